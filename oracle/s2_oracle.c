@@ -1,0 +1,779 @@
+/*
+ * Plain FP64 CPU oracle of the STREAmS-2 right-hand side and its
+ * low-storage RK3 update.  TEST INFRASTRUCTURE ONLY: it is called by the
+ * tests, by the smoke check and by the benchmark's CPU-baseline leg, never by
+ * the product path, and it shares no code, header or table with the CUDA
+ * library.
+ *
+ * What it computes (paper Sec. 2, "Numerical Methods"): the compressible
+ * Navier-Stokes equations for a calorically perfect ideal gas on a Cartesian
+ * grid (stretched in y), finite differences, with
+ *   - a hybrid convective discretisation: the energy-preserving split
+ *     ("skew-symmetric") form of the convective terms written as numerical
+ *     fluxes (Pirozzoli, J. Comput. Phys. 2010), switched at interfaces
+ *     flagged by a modified Ducros shock sensor to a WENO reconstruction of
+ *     characteristic fluxes (Lax-Friedrichs splitting), projected back on
+ *     the right eigenvectors of the Euler equations (Jiang & Shu 1996 WENO5,
+ *     Balsara & Shu 2000 WENO7);
+ *   - viscous terms expanded in Laplacian form, 6th-order central formulae;
+ *   - a third-order low-storage Runge-Kutta scheme (Wray's coefficients);
+ *   - the update "w += fln" of the flux register (Sec. 3.2, Listing 4), the
+ *     forcing reduction force_rhs_1 and the CFL reduction compute_dt of
+ *     Table 2.
+ * The paper prints no formula; where it is silent the choices below are
+ * readings of the cited published methods (listed as such in the design
+ * notes).  Everything is written in the most direct form: interface fluxes
+ * by their double sums, eigenvector matrices built explicitly, WENO weights
+ * by their definition, derivatives by their stencils.  No blocking, fusion
+ * or reordering.
+ *
+ * Layout of a state w: five fields (rho, rho u, rho v, rho w, rho E), each
+ * nz*ny*nx doubles with i (x) fastest: w[f][k][j][i].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NV 5
+#define GH 4 /* ghost width of the padded work arrays (WENO7 needs 4) */
+
+/* 6th-order central first derivative: f' = sum_l a_l (f_{i+l} - f_{i-l}) */
+static const double A1[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
+/* 6th-order central second derivative: f'' = b_0 f_i + sum_l b_l (f_{i+l} + f_{i-l}) */
+static const double B2[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+
+/* Wray's low-storage RK3: w_k = w_{k-1} + dt (gamma_k R_{k-1} + rho_k R_{k-2}) */
+static const double RK_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+static const double RK_RHO[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+/* Problem description.  x and z are periodic; y is periodic or bounded by
+ * isothermal no-slip walls at y = -ly/2 and y = +ly/2 (nodes strictly
+ * inside, the walls lying half way between the outermost node and its
+ * mirror image). */
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz;
+  const double *y;      /* ny node ordinates, or NULL for uniform nodes */
+  double gamma, prandtl, mach, re, visc_exp, t_ref;
+  int bc_y;             /* 0 periodic, 1 isothermal no-slip walls */
+  double t_wall;
+  int force;            /* 1: uniform x body force keeping the bulk rho*u constant */
+  int weno_order;       /* 0 (central everywhere), 5 or 7 */
+  double threshold;     /* interface is WENO iff max sensor over its stencil > threshold */
+} or_cfg;
+
+/* Which terms or_rhs evaluates. */
+#define OR_CONV 1
+#define OR_VISC 2
+#define OR_FORCE 4
+
+typedef struct {
+  const or_cfg *c;
+  int nx, ny, nz, px, py, pz;
+  size_t np, n;
+  double R, cv, cp, dx, dz, eps_sensor;
+  int viscous;
+  double *eta_y, *eta_yy; /* ny */
+  double *rho, *u, *v, *w, *T, *p, *H, *cs, *sens, *div;
+} ws_t;
+
+#define PI(s, i, j, k) \
+  ((((size_t)((k) + GH)) * (size_t)(s)->py + (size_t)((j) + GH)) * (size_t)(s)->px + (size_t)((i) + GH))
+#define WI(s, i, j, k) ((((size_t)(k)) * (size_t)(s)->ny + (size_t)(j)) * (size_t)(s)->nx + (size_t)(i))
+
+static int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+/* ---------------------------------------------------------------- grid ---
+ * Grid metrics of the stretched y direction (paper Sec. 3.1: the Grid
+ * object evaluates the metrics).  The flux is computed in the uniform index
+ * eta; d/dy = eta_y d/deta with y_eta from the 6th-order stencil applied to
+ * the node ordinates extended into the ghosts (periodic shift, or mirror
+ * about the walls), eta_yy = -y_etaeta / y_eta^3. */
+static double node_y(const or_cfg *c, int j) {
+  if (c->y) return c->y[j];
+  return -0.5 * c->ly + (j + 0.5) * c->ly / c->ny;
+}
+
+static double ext_y(const or_cfg *c, int j) {
+  int ny = c->ny;
+  if (j >= 0 && j < ny) return node_y(c, j);
+  if (c->bc_y == 0) {
+    int jm = imod(j, ny);
+    int shift = (j - jm) / ny;
+    return node_y(c, jm) + shift * c->ly;
+  }
+  if (j < 0) return 2.0 * (-0.5 * c->ly) - node_y(c, -1 - j);
+  return 2.0 * (0.5 * c->ly) - node_y(c, 2 * ny - 1 - j);
+}
+
+void or_metric(const or_cfg *c, double *eta_y, double *eta_yy) {
+  for (int j = 0; j < c->ny; ++j) {
+    double d1 = 0.0, d2 = B2[0] * ext_y(c, j);
+    for (int l = 1; l <= 3; ++l) {
+      d1 += A1[l] * (ext_y(c, j + l) - ext_y(c, j - l));
+      d2 += B2[l] * (ext_y(c, j + l) + ext_y(c, j - l));
+    }
+    eta_y[j] = 1.0 / d1;
+    eta_yy[j] = -d2 / (d1 * d1 * d1);
+  }
+}
+
+/* ------------------------------------------------------------ workspace --- */
+static int ws_init(ws_t *s, const or_cfg *c) {
+  memset(s, 0, sizeof(*s));
+  s->c = c;
+  s->nx = c->nx; s->ny = c->ny; s->nz = c->nz;
+  s->px = c->nx + 2 * GH; s->py = c->ny + 2 * GH; s->pz = c->nz + 2 * GH;
+  s->np = (size_t)s->px * s->py * s->pz;
+  s->n = (size_t)c->nx * c->ny * c->nz;
+  /* Non-dimensional gas (reference density, velocity, temperature, length
+   * all 1): R = 1/(gamma M^2), so p = rho R T and c = sqrt(gamma R T). */
+  s->R = 1.0 / (c->gamma * c->mach * c->mach);
+  s->cv = s->R / (c->gamma - 1.0);
+  s->cp = c->gamma * s->cv;
+  s->dx = c->lx / c->nx;
+  s->dz = c->lz / c->nz;
+  s->eps_sensor = 1.0; /* (U0/L0)^2 in reference units */
+  s->viscous = c->re > 0.0;
+  s->eta_y = (double *)malloc(sizeof(double) * c->ny);
+  s->eta_yy = (double *)malloc(sizeof(double) * c->ny);
+  double **f[] = {&s->rho, &s->u, &s->v, &s->w, &s->T, &s->p, &s->H, &s->cs, &s->sens, &s->div};
+  for (size_t q = 0; q < sizeof(f) / sizeof(f[0]); ++q) {
+    *f[q] = (double *)calloc(s->np, sizeof(double));
+    if (!*f[q]) return -1;
+  }
+  if (!s->eta_y || !s->eta_yy) return -1;
+  or_metric(c, s->eta_y, s->eta_yy);
+  return 0;
+}
+
+static void ws_free(ws_t *s) {
+  double *f[] = {s->rho, s->u, s->v, s->w, s->T, s->p, s->H, s->cs, s->sens, s->div};
+  for (size_t q = 0; q < sizeof(f) / sizeof(f[0]); ++q) free(f[q]);
+  free(s->eta_y); free(s->eta_yy);
+}
+
+/* ------------------------------------------------------------ primitives ---
+ * Primitive recovery: rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v,
+ * p = rho R T; then the ghost faces; then H = c_p T + |u|^2/2 and
+ * c = sqrt(gamma R T) on interior and ghost faces. */
+static void fill_ghost_prims(ws_t *s) {
+  const or_cfg *c = s->c;
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+  double *fl[] = {s->rho, s->u, s->v, s->w, s->T, s->p};
+  /* x faces (periodic) */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int g = 1; g <= GH; ++g)
+        for (int q = 0; q < 6; ++q) {
+          fl[q][PI(s, -g, j, k)] = fl[q][PI(s, nx - g, j, k)];
+          fl[q][PI(s, nx - 1 + g, j, k)] = fl[q][PI(s, g - 1, j, k)];
+        }
+  /* z faces (periodic) */
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int g = 1; g <= GH; ++g)
+        for (int q = 0; q < 6; ++q) {
+          fl[q][PI(s, i, j, -g)] = fl[q][PI(s, i, j, nz - g)];
+          fl[q][PI(s, i, j, nz - 1 + g)] = fl[q][PI(s, i, j, g - 1)];
+        }
+  /* y faces */
+  for (int k = 0; k < nz; ++k)
+    for (int i = 0; i < nx; ++i)
+      for (int g = 1; g <= GH; ++g) {
+        if (c->bc_y == 0) {
+          for (int q = 0; q < 6; ++q) {
+            fl[q][PI(s, i, -g, k)] = fl[q][PI(s, i, ny - g, k)];
+            fl[q][PI(s, i, ny - 1 + g, k)] = fl[q][PI(s, i, g - 1, k)];
+          }
+        } else {
+          /* mirror about the wall: ghost -g <-> node g-1 (bottom),
+           * ghost ny-1+g <-> node ny-g (top).  No slip: velocity odd;
+           * isothermal: T_ghost = 2 T_wall - T; pressure even; density
+           * from the equation of state. */
+          int gj[2] = {-g, ny - 1 + g}, mj[2] = {g - 1, ny - g};
+          for (int side = 0; side < 2; ++side) {
+            size_t a = PI(s, i, gj[side], k), b = PI(s, i, mj[side], k);
+            s->u[a] = -s->u[b];
+            s->v[a] = -s->v[b];
+            s->w[a] = -s->w[b];
+            s->T[a] = 2.0 * c->t_wall - s->T[b];
+            s->p[a] = s->p[b];
+            s->rho[a] = s->p[a] / (s->R * s->T[a]);
+          }
+        }
+      }
+}
+
+static void prims(ws_t *s, const double *w) {
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+  size_t n = s->n;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t q = WI(s, i, j, k), a = PI(s, i, j, k);
+        double rho = w[q];
+        double u = w[n + q] / rho, v = w[2 * n + q] / rho, ww = w[3 * n + q] / rho;
+        double e = w[4 * n + q] / rho - 0.5 * (u * u + v * v + ww * ww);
+        double T = e / s->cv;
+        s->rho[a] = rho; s->u[a] = u; s->v[a] = v; s->w[a] = ww;
+        s->T[a] = T; s->p[a] = rho * s->R * T;
+      }
+  fill_ghost_prims(s);
+  /* H and c everywhere the primitives are defined (edges/corners stay 0) */
+#pragma omp parallel for schedule(static)
+  for (int kk = 0; kk < s->pz; ++kk)
+    for (int jj = 0; jj < s->py; ++jj)
+      for (int ii = 0; ii < s->px; ++ii) {
+        size_t a = ((size_t)kk * s->py + jj) * s->px + ii;
+        double T = s->T[a];
+        double q2 = s->u[a] * s->u[a] + s->v[a] * s->v[a] + s->w[a] * s->w[a];
+        s->H[a] = s->cp * T + 0.5 * q2;
+        s->cs[a] = T > 0.0 ? sqrt(s->c->gamma * s->R * T) : 0.0;
+      }
+}
+
+/* ---------------------------------------------------------- derivatives --- */
+static double d1(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  double r = 0.0;
+  for (int l = 1; l <= 3; ++l) {
+    if (dir == 0) r += A1[l] * (f[PI(s, i + l, j, k)] - f[PI(s, i - l, j, k)]);
+    else if (dir == 1) r += A1[l] * (f[PI(s, i, j + l, k)] - f[PI(s, i, j - l, k)]);
+    else r += A1[l] * (f[PI(s, i, j, k + l)] - f[PI(s, i, j, k - l)]);
+  }
+  if (dir == 0) return r / s->dx;
+  if (dir == 1) return r * s->eta_y[j];
+  return r / s->dz;
+}
+
+/* derivative in index space (no metric) */
+static double d1_idx(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  double r = 0.0;
+  for (int l = 1; l <= 3; ++l) {
+    if (dir == 0) r += A1[l] * (f[PI(s, i + l, j, k)] - f[PI(s, i - l, j, k)]);
+    else if (dir == 1) r += A1[l] * (f[PI(s, i, j + l, k)] - f[PI(s, i, j - l, k)]);
+    else r += A1[l] * (f[PI(s, i, j, k + l)] - f[PI(s, i, j, k - l)]);
+  }
+  return r;
+}
+
+static double d2(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  double r = B2[0] * f[PI(s, i, j, k)];
+  for (int l = 1; l <= 3; ++l) {
+    if (dir == 0) r += B2[l] * (f[PI(s, i + l, j, k)] + f[PI(s, i - l, j, k)]);
+    else if (dir == 1) r += B2[l] * (f[PI(s, i, j + l, k)] + f[PI(s, i, j - l, k)]);
+    else r += B2[l] * (f[PI(s, i, j, k + l)] + f[PI(s, i, j, k - l)]);
+  }
+  if (dir == 0) return r / (s->dx * s->dx);
+  if (dir == 2) return r / (s->dz * s->dz);
+  /* d2f/dy2 = eta_y^2 f_etaeta + eta_yy f_eta */
+  double ey = s->eta_y[j];
+  return ey * ey * r + s->eta_yy[j] * d1_idx(s, f, i, j, k, 1);
+}
+
+/* --------------------------------------------------------------- sensor ---
+ * Modified Ducros sensor (paper Sec. 2): theta = div u, omega = curl u,
+ * sensor = max(-theta / sqrt(theta^2 + |omega|^2 + eps), 0), eps = (U0/L0)^2.
+ * It also stores theta, whose derivatives the viscous terms use.  Ghost
+ * values: periodic copy, or at a wall the mirror value of the sensor and
+ * the divergence of the mirrored velocity field (-u_x + v_y - w_z at the
+ * mirror node, since u, w are odd in y with even x/z derivatives and v is
+ * odd with an even y derivative). */
+static void sensor(ws_t *s) {
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        double ux = d1(s, s->u, i, j, k, 0), uy = d1(s, s->u, i, j, k, 1), uz = d1(s, s->u, i, j, k, 2);
+        double vx = d1(s, s->v, i, j, k, 0), vy = d1(s, s->v, i, j, k, 1), vz = d1(s, s->v, i, j, k, 2);
+        double wx = d1(s, s->w, i, j, k, 0), wy = d1(s, s->w, i, j, k, 1), wz = d1(s, s->w, i, j, k, 2);
+        double th = ux + vy + wz;
+        double o1 = wy - vz, o2 = uz - wx, o3 = vx - uy;
+        double om2 = o1 * o1 + o2 * o2 + o3 * o3;
+        double sv = -th / sqrt(th * th + om2 + s->eps_sensor);
+        size_t a = PI(s, i, j, k);
+        s->sens[a] = sv > 0.0 ? sv : 0.0;
+        s->div[a] = th;
+      }
+  double *fl[] = {s->sens, s->div};
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int g = 1; g <= GH; ++g)
+        for (int q = 0; q < 2; ++q) {
+          fl[q][PI(s, -g, j, k)] = fl[q][PI(s, nx - g, j, k)];
+          fl[q][PI(s, nx - 1 + g, j, k)] = fl[q][PI(s, g - 1, j, k)];
+        }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int g = 1; g <= GH; ++g)
+        for (int q = 0; q < 2; ++q) {
+          fl[q][PI(s, i, j, -g)] = fl[q][PI(s, i, j, nz - g)];
+          fl[q][PI(s, i, j, nz - 1 + g)] = fl[q][PI(s, i, j, g - 1)];
+        }
+  for (int k = 0; k < nz; ++k)
+    for (int i = 0; i < nx; ++i)
+      for (int g = 1; g <= GH; ++g) {
+        if (s->c->bc_y == 0) {
+          for (int q = 0; q < 2; ++q) {
+            fl[q][PI(s, i, -g, k)] = fl[q][PI(s, i, ny - g, k)];
+            fl[q][PI(s, i, ny - 1 + g, k)] = fl[q][PI(s, i, g - 1, k)];
+          }
+        } else {
+          int gj[2] = {-g, ny - 1 + g}, mj[2] = {g - 1, ny - g};
+          for (int side = 0; side < 2; ++side) {
+            int m = mj[side];
+            if (m < 0 || m >= ny) continue;
+            double ux = d1(s, s->u, i, m, k, 0), vy = d1(s, s->v, i, m, k, 1), wz = d1(s, s->w, i, m, k, 2);
+            s->sens[PI(s, i, gj[side], k)] = s->sens[PI(s, i, m, k)];
+            s->div[PI(s, i, gj[side], k)] = -ux + vy - wz;
+          }
+        }
+      }
+}
+
+/* ------------------------------------------------------------------ WENO ---
+ * Left-biased WENO reconstruction at x_{i+1/2} from the 2r-1 values
+ * f[0..2r-2] centred on f[r-1] = f_i.  r = 3: Jiang & Shu (1996) WENO5;
+ * r = 4: Balsara & Shu (2000) WENO7.  Weights alpha_k = d_k/(eps+beta_k)^2,
+ * eps = 1e-6. */
+#define WENO_EPS 1e-6
+
+/* Candidate values q_k and smoothness indicators beta_k of the r
+ * substencils; returns r (0 for an unsupported order). */
+int or_weno_parts(int order, const double *g, double *q, double *b) {
+  if (order == 5) { /* g[0..4] = f_{i-2} .. f_{i+2} */
+    q[0] = (2.0 * g[0] - 7.0 * g[1] + 11.0 * g[2]) / 6.0;
+    q[1] = (-g[1] + 5.0 * g[2] + 2.0 * g[3]) / 6.0;
+    q[2] = (2.0 * g[2] + 5.0 * g[3] - g[4]) / 6.0;
+    double t;
+    t = g[0] - 2.0 * g[1] + g[2]; b[0] = 13.0 / 12.0 * t * t;
+    t = g[0] - 4.0 * g[1] + 3.0 * g[2]; b[0] += 0.25 * t * t;
+    t = g[1] - 2.0 * g[2] + g[3]; b[1] = 13.0 / 12.0 * t * t;
+    t = g[1] - g[3]; b[1] += 0.25 * t * t;
+    t = g[2] - 2.0 * g[3] + g[4]; b[2] = 13.0 / 12.0 * t * t;
+    t = 3.0 * g[2] - 4.0 * g[3] + g[4]; b[2] += 0.25 * t * t;
+    return 3;
+  }
+  if (order == 7) { /* g[0..6] = f_{i-3} .. f_{i+3} */
+    q[0] = (-3.0 * g[0] + 13.0 * g[1] - 23.0 * g[2] + 25.0 * g[3]) / 12.0;
+    q[1] = (g[1] - 5.0 * g[2] + 13.0 * g[3] + 3.0 * g[4]) / 12.0;
+    q[2] = (-g[2] + 7.0 * g[3] + 7.0 * g[4] - g[5]) / 12.0;
+    q[3] = (3.0 * g[3] + 13.0 * g[4] - 5.0 * g[5] + g[6]) / 12.0;
+    b[0] = g[0] * (547.0 * g[0] - 3882.0 * g[1] + 4642.0 * g[2] - 1854.0 * g[3]) +
+           g[1] * (7043.0 * g[1] - 17246.0 * g[2] + 7042.0 * g[3]) +
+           g[2] * (11003.0 * g[2] - 9402.0 * g[3]) + 2107.0 * g[3] * g[3];
+    b[1] = g[1] * (267.0 * g[1] - 1642.0 * g[2] + 1602.0 * g[3] - 494.0 * g[4]) +
+           g[2] * (2843.0 * g[2] - 5966.0 * g[3] + 1922.0 * g[4]) +
+           g[3] * (3443.0 * g[3] - 2522.0 * g[4]) + 547.0 * g[4] * g[4];
+    b[2] = g[2] * (547.0 * g[2] - 2522.0 * g[3] + 1922.0 * g[4] - 494.0 * g[5]) +
+           g[3] * (3443.0 * g[3] - 5966.0 * g[4] + 1602.0 * g[5]) +
+           g[4] * (2843.0 * g[4] - 1642.0 * g[5]) + 267.0 * g[5] * g[5];
+    b[3] = g[3] * (2107.0 * g[3] - 9402.0 * g[4] + 7042.0 * g[5] - 1854.0 * g[6]) +
+           g[4] * (11003.0 * g[4] - 17246.0 * g[5] + 4642.0 * g[6]) +
+           g[5] * (7043.0 * g[5] - 3882.0 * g[6]) + 547.0 * g[6] * g[6];
+    return 4;
+  }
+  return 0;
+}
+
+/* Optimal (linear) weights d_k. */
+static const double WENO5_D[3] = {0.1, 0.6, 0.3};
+static const double WENO7_D[4] = {1.0 / 35.0, 12.0 / 35.0, 18.0 / 35.0, 4.0 / 35.0};
+
+double or_weno_rec(int order, const double *f) {
+  double q[4], b[4];
+  int r = or_weno_parts(order, f, q, b);
+  if (!r) return NAN;
+  const double *d = r == 3 ? WENO5_D : WENO7_D;
+  double a[4], sa = 0.0;
+  for (int k = 0; k < r; ++k) { a[k] = d[k] / ((WENO_EPS + b[k]) * (WENO_EPS + b[k])); sa += a[k]; }
+  double res = 0.0;
+  for (int k = 0; k < r; ++k) res += a[k] / sa * q[k];
+  return res;
+}
+
+/* Eigenvector matrices of the Euler flux Jacobian along direction dir at
+ * the state (velocity uv[3], total enthalpy H): columns of Rm are the right
+ * eigenvectors for the eigenvalues (u_n - c, u_n, u_n, u_n, u_n + c), rows of
+ * Lm the left eigenvectors, Lm = Rm^-1.  Row-major 5x5.  Returns c. */
+double or_eigvec(double gamma, int dir, const double *uv, double H, double *Lm, double *Rm) {
+  double b = gamma - 1.0;
+  double q2 = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+  double c2 = b * (H - 0.5 * q2);
+  double c = sqrt(c2);
+  double n[3] = {0.0, 0.0, 0.0};
+  n[dir] = 1.0;
+  int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3; /* tangential axes */
+  double un = uv[dir];
+  for (int q = 0; q < 25; ++q) { Lm[q] = 0.0; Rm[q] = 0.0; }
+  /* right eigenvectors (columns) */
+  Rm[0 * 5 + 0] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 0] = uv[a] - c * n[a];
+  Rm[4 * 5 + 0] = H - un * c;
+  Rm[0 * 5 + 1] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 1] = uv[a];
+  Rm[4 * 5 + 1] = 0.5 * q2;
+  Rm[(1 + t1) * 5 + 2] = 1.0;
+  Rm[4 * 5 + 2] = uv[t1];
+  Rm[(1 + t2) * 5 + 3] = 1.0;
+  Rm[4 * 5 + 3] = uv[t2];
+  Rm[0 * 5 + 4] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 4] = uv[a] + c * n[a];
+  Rm[4 * 5 + 4] = H + un * c;
+  /* left eigenvectors (rows) */
+  double h2 = 0.5 / c2;
+  Lm[0 * 5 + 0] = h2 * (0.5 * b * q2 + un * c);
+  for (int a = 0; a < 3; ++a) Lm[0 * 5 + 1 + a] = h2 * (-b * uv[a] - c * n[a]);
+  Lm[0 * 5 + 4] = h2 * b;
+  Lm[1 * 5 + 0] = 1.0 - b * q2 / (2.0 * c2);
+  for (int a = 0; a < 3; ++a) Lm[1 * 5 + 1 + a] = b * uv[a] / c2;
+  Lm[1 * 5 + 4] = -b / c2;
+  Lm[2 * 5 + 0] = -uv[t1];
+  Lm[2 * 5 + 1 + t1] = 1.0;
+  Lm[3 * 5 + 0] = -uv[t2];
+  Lm[3 * 5 + 1 + t2] = 1.0;
+  Lm[4 * 5 + 0] = h2 * (0.5 * b * q2 - un * c);
+  for (int a = 0; a < 3; ++a) Lm[4 * 5 + 1 + a] = h2 * (-b * uv[a] + c * n[a]);
+  Lm[4 * 5 + 4] = h2 * b;
+  return c;
+}
+
+/* value of field f at position "pos" along direction dir of the pencil
+ * through (i,j,k) */
+static inline size_t at(const ws_t *s, int dir, int pos, int i, int j, int k) {
+  if (dir == 0) return PI(s, pos, j, k);
+  if (dir == 1) return PI(s, i, pos, k);
+  return PI(s, i, j, pos);
+}
+
+/* WENO flux of order 2r-1 at interface pos+1/2 (characteristic variables,
+ * local Lax-Friedrichs splitting with one dissipation per characteristic
+ * field: the largest |eigenvalue| over the stencil points; Roe-averaged
+ * eigenvectors). */
+static void weno_flux(const ws_t *s, int dir, int pos, int i, int j, int k, double *F) {
+  const double gam = s->c->gamma;
+  int r = (s->c->weno_order + 1) / 2;
+  int np = 2 * r; /* stencil points pos-r+1 .. pos+r */
+  size_t a = at(s, dir, pos, i, j, k), bq = at(s, dir, pos + 1, i, j, k);
+  /* Roe average of the states at pos and pos+1 */
+  double ra = sqrt(s->rho[a]), rb = sqrt(s->rho[bq]);
+  double uv[3], H;
+  uv[0] = (ra * s->u[a] + rb * s->u[bq]) / (ra + rb);
+  uv[1] = (ra * s->v[a] + rb * s->v[bq]) / (ra + rb);
+  uv[2] = (ra * s->w[a] + rb * s->w[bq]) / (ra + rb);
+  H = (ra * s->H[a] + rb * s->H[bq]) / (ra + rb);
+  double Lm[25], Rm[25];
+  or_eigvec(gam, dir, uv, H, Lm, Rm);
+  double V[8][5], G[8][5], lam[8][5];
+  for (int m = 0; m < np; ++m) {
+    size_t q = at(s, dir, pos - r + 1 + m, i, j, k);
+    double rho = s->rho[q], vel[3] = {s->u[q], s->v[q], s->w[q]};
+    double p = s->p[q], Hq = s->H[q], un = vel[dir];
+    double W[5] = {rho, rho * vel[0], rho * vel[1], rho * vel[2], rho * Hq - p};
+    double Fp[5] = {rho * un, rho * un * vel[0], rho * un * vel[1], rho * un * vel[2], rho * un * Hq};
+    Fp[1 + dir] += p;
+    for (int e = 0; e < 5; ++e) {
+      double sv = 0.0, sg = 0.0;
+      for (int f = 0; f < 5; ++f) { sv += Lm[e * 5 + f] * W[f]; sg += Lm[e * 5 + f] * Fp[f]; }
+      V[m][e] = sv; G[m][e] = sg;
+    }
+    lam[m][0] = un - s->cs[q];
+    lam[m][1] = un; lam[m][2] = un; lam[m][3] = un;
+    lam[m][4] = un + s->cs[q];
+  }
+  double gh[5];
+  for (int e = 0; e < 5; ++e) {
+    double alpha = 0.0;
+    for (int m = 0; m < np; ++m) alpha = fmax(alpha, fabs(lam[m][e]));
+    double fp[7], fm[7];
+    /* plus flux: left-biased, points pos-r+1 .. pos+r-1 */
+    for (int m = 0; m < 2 * r - 1; ++m) fp[m] = 0.5 * (G[m][e] + alpha * V[m][e]);
+    /* minus flux: right-biased, mirrored so pos+r .. pos-r+2 */
+    for (int m = 0; m < 2 * r - 1; ++m) {
+      int mm = np - 1 - m;
+      fm[m] = 0.5 * (G[mm][e] - alpha * V[mm][e]);
+    }
+    gh[e] = or_weno_rec(s->c->weno_order, fp) + or_weno_rec(s->c->weno_order, fm);
+  }
+  for (int f = 0; f < 5; ++f) {
+    double sum = 0.0;
+    for (int e = 0; e < 5; ++e) sum += Rm[f * 5 + e] * gh[e];
+    F[f] = sum;
+  }
+}
+
+/* Split-form central flux at interface pos+1/2 (Pirozzoli 2010):
+ * F = 2 sum_l a_l sum_{m<l} (rho)(u_n)(phi) over the pairs (pos-m, pos-m+l),
+ * (g) the arithmetic mean of the pair, phi = (1, u, v, w, H); the pressure
+ * enters the normal momentum as sum_l a_l sum_{m<l} (p_a + p_b). */
+static void central_flux(const ws_t *s, int dir, int pos, int i, int j, int k, double *F) {
+  const double *un = dir == 0 ? s->u : (dir == 1 ? s->v : s->w);
+  for (int f = 0; f < 5; ++f) F[f] = 0.0;
+  double fp = 0.0;
+  for (int l = 1; l <= 3; ++l) {
+    double acc[5] = {0, 0, 0, 0, 0}, pp = 0.0;
+    for (int m = 0; m < l; ++m) {
+      size_t a = at(s, dir, pos - m, i, j, k), b = at(s, dir, pos - m + l, i, j, k);
+      double rr = 0.5 * (s->rho[a] + s->rho[b]);
+      double uu = 0.5 * (un[a] + un[b]);
+      double phi[5] = {1.0, 0.5 * (s->u[a] + s->u[b]), 0.5 * (s->v[a] + s->v[b]),
+                       0.5 * (s->w[a] + s->w[b]), 0.5 * (s->H[a] + s->H[b])};
+      for (int f = 0; f < 5; ++f) acc[f] += rr * uu * phi[f];
+      pp += s->p[a] + s->p[b];
+    }
+    for (int f = 0; f < 5; ++f) F[f] += 2.0 * A1[l] * acc[f];
+    fp += A1[l] * pp;
+  }
+  F[1 + dir] += fp;
+}
+
+static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags) {
+  int nx = s->nx, ny = s->ny, nz = s->nz, n = dir == 0 ? nx : (dir == 1 ? ny : nz);
+  int r = (s->c->weno_order + 1) / 2;
+  int na = dir == 0 ? ny : nx, nb = dir == 2 ? ny : nz; /* transverse extents */
+#pragma omp parallel for schedule(static) collapse(2)
+  for (int tb = 0; tb < nb; ++tb)
+    for (int ta = 0; ta < na; ++ta) {
+      int i = 0, j = 0, k = 0;
+      if (dir == 0) { j = ta; k = tb; }
+      else if (dir == 1) { i = ta; k = tb; }
+      else { i = ta; j = tb; }
+      double *Fh = (double *)malloc(sizeof(double) * 5 * (size_t)(n + 1));
+      for (int pos = -1; pos < n; ++pos) {
+        int fl = 0;
+        if (s->c->weno_order > 0) {
+          double mx = 0.0;
+          for (int m = pos - r + 1; m <= pos + r; ++m) mx = fmax(mx, s->sens[at(s, dir, m, i, j, k)]);
+          fl = mx > s->c->threshold;
+        }
+        if (flags) {
+          /* per-direction interface flags, n+1 per pencil, interface pos+1/2 at slot pos+1 */
+          size_t slot;
+          if (dir == 0) slot = ((size_t)k * ny + j) * (nx + 1) + (pos + 1);
+          else if (dir == 1) slot = ((size_t)k * (ny + 1) + (pos + 1)) * nx + i;
+          else slot = ((size_t)(pos + 1) * ny + j) * nx + i;
+          flags[slot] = (unsigned char)fl;
+        }
+        if (fl) weno_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+        else central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+      }
+      for (int pos = 0; pos < n; ++pos) {
+        int ii = dir == 0 ? pos : i, jj = dir == 1 ? pos : j, kk = dir == 2 ? pos : k;
+        double sc = dir == 0 ? 1.0 / s->dx : (dir == 1 ? s->eta_y[jj] : 1.0 / s->dz);
+        size_t q = WI(s, ii, jj, kk);
+        for (int f = 0; f < 5; ++f)
+          rhs[f * s->n + q] -= sc * (Fh[5 * (pos + 1) + f] - Fh[5 * pos + f]);
+      }
+      free(Fh);
+    }
+}
+
+/* ---------------------------------------------------------------- viscous ---
+ * Viscous and heat-flux terms in Laplacian form (paper Sec. 2):
+ *   momentum_i: mu (lap u_i + (1/3) d_i theta) + d_j mu (d_j u_i + d_i u_j)
+ *               - (2/3) theta d_i mu
+ *   energy:     u_i * momentum_i + tau_ij d_j u_i + k lap T + grad k . grad T
+ * with mu = (T/T_ref)^omega / Re, grad mu = (omega mu / T) grad T,
+ * k = mu c_p / Pr, tau_ij = mu (d_j u_i + d_i u_j - (2/3) theta delta_ij),
+ * theta the stored divergence (its gradient by the same stencil). */
+static void viscous(ws_t *s, double *rhs) {
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+  const or_cfg *c = s->c;
+  size_t n = s->n;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const double *vel[3] = {s->u, s->v, s->w};
+        double g[3][3], lap[3], gT[3], gth[3];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) g[a][b] = d1(s, vel[a], i, j, k, b); /* d u_a / d x_b */
+        for (int a = 0; a < 3; ++a) lap[a] = d2(s, vel[a], i, j, k, 0) + d2(s, vel[a], i, j, k, 1) + d2(s, vel[a], i, j, k, 2);
+        for (int b = 0; b < 3; ++b) { gT[b] = d1(s, s->T, i, j, k, b); gth[b] = d1(s, s->div, i, j, k, b); }
+        double lapT = d2(s, s->T, i, j, k, 0) + d2(s, s->T, i, j, k, 1) + d2(s, s->T, i, j, k, 2);
+        size_t pa = PI(s, i, j, k);
+        double T = s->T[pa];
+        double mu = pow(T / c->t_ref, c->visc_exp) / c->re;
+        double mut = c->visc_exp * mu / T;
+        double kc = mu * s->cp / c->prandtl;
+        double gmu[3], gk[3];
+        for (int b = 0; b < 3; ++b) { gmu[b] = mut * gT[b]; gk[b] = s->cp / c->prandtl * gmu[b]; }
+        double th = s->div[pa];
+        double uvec[3] = {s->u[pa], s->v[pa], s->w[pa]};
+        double mom[3], en = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          double m = mu * (lap[a] + gth[a] / 3.0);
+          for (int b = 0; b < 3; ++b) m += gmu[b] * (g[a][b] + g[b][a]);
+          m -= 2.0 / 3.0 * th * gmu[a];
+          mom[a] = m;
+        }
+        for (int a = 0; a < 3; ++a) {
+          en += uvec[a] * mom[a];
+          for (int b = 0; b < 3; ++b) {
+            double tau = mu * (g[a][b] + g[b][a] - (a == b ? 2.0 / 3.0 * th : 0.0));
+            en += tau * g[a][b];
+          }
+        }
+        en += kc * lapT;
+        for (int b = 0; b < 3; ++b) en += gk[b] * gT[b];
+        size_t q = WI(s, i, j, k);
+        for (int a = 0; a < 3; ++a) rhs[(1 + a) * n + q] += mom[a];
+        rhs[4 * n + q] += en;
+      }
+}
+
+/* ----------------------------------------------------------------- forcing ---
+ * Constant-mass-flow forcing (force_rhs_1 of Table 2): a uniform x body
+ * force f = -(sum R_rhou dV)/(sum dV), dV proportional to dy/deta, added to
+ * R_rhou and, times u, to R_rhoE; the bulk rho u then stays constant. */
+static double forcing(ws_t *s, double *rhs) {
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+  size_t n = s->n;
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j) {
+      double dv = 1.0 / s->eta_y[j];
+      for (int i = 0; i < nx; ++i) num += rhs[n + WI(s, i, j, k)] * dv;
+      den += dv * nx;
+    }
+  double f = -num / den;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t q = WI(s, i, j, k);
+        rhs[n + q] += f;
+        rhs[4 * n + q] += f * s->u[PI(s, i, j, k)];
+      }
+  return f;
+}
+
+/* --------------------------------------------------------------------- RHS ---
+ * R(w): primitives, sensor, convective fluxes in x, y, z, viscous terms,
+ * forcing.  flags{x,y,z} (may be NULL) receive the per-interface WENO flags,
+ * (n_dir + 1) per pencil. */
+static int rhs_ws(ws_t *s, const double *w, double *rhs, unsigned char *fx, unsigned char *fy,
+                  unsigned char *fz, int terms, double *force_out) {
+  memset(rhs, 0, sizeof(double) * NV * s->n);
+  prims(s, w);
+  sensor(s);
+  if (terms & OR_CONV) {
+    convective(s, 0, rhs, fx);
+    convective(s, 1, rhs, fy);
+    convective(s, 2, rhs, fz);
+  }
+  if ((terms & OR_VISC) && s->viscous) viscous(s, rhs);
+  double f = 0.0;
+  if ((terms & OR_FORCE) && s->c->force) f = forcing(s, rhs);
+  if (force_out) *force_out = f;
+  return 0;
+}
+
+int or_rhs(const or_cfg *c, const double *w, double *rhs, unsigned char *fx, unsigned char *fy,
+           unsigned char *fz, int terms, double *force_out) {
+  ws_t s;
+  if (ws_init(&s, c)) { ws_free(&s); return -1; }
+  rhs_ws(&s, w, rhs, fx, fy, fz, terms, force_out);
+  ws_free(&s);
+  return 0;
+}
+
+/* Sensor and divergence at interior points, for checks. */
+int or_sensor(const or_cfg *c, const double *w, double *sens, double *div) {
+  ws_t s;
+  if (ws_init(&s, c)) { ws_free(&s); return -1; }
+  prims(&s, w);
+  sensor(&s);
+  for (int k = 0; k < c->nz; ++k)
+    for (int j = 0; j < c->ny; ++j)
+      for (int i = 0; i < c->nx; ++i) {
+        sens[WI(&s, i, j, k)] = s.sens[PI(&s, i, j, k)];
+        div[WI(&s, i, j, k)] = s.div[PI(&s, i, j, k)];
+      }
+  ws_free(&s);
+  return 0;
+}
+
+/* -------------------------------------------------------------------- dt ---
+ * compute_dt of Table 2: dt = cfl / max over the interior of
+ *   (|u|+c)/dx + (|v|+c) eta_y + (|w|+c)/dz
+ *   + gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2)   (viscous runs). */
+static double dt_ws(ws_t *s, const double *w, double cfl) {
+  int nx = s->nx, ny = s->ny, nz = s->nz;
+  const or_cfg *c = s->c;
+  prims(s, w);
+  double mx = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t a = PI(s, i, j, k);
+        double cs = s->cs[a], ey = s->eta_y[j];
+        double sr = (fabs(s->u[a]) + cs) / s->dx + (fabs(s->v[a]) + cs) * ey + (fabs(s->w[a]) + cs) / s->dz;
+        if (s->viscous) {
+          double mu = pow(s->T[a] / c->t_ref, c->visc_exp) / c->re;
+          sr += c->gamma * mu / (c->prandtl * s->rho[a]) *
+                (1.0 / (s->dx * s->dx) + ey * ey + 1.0 / (s->dz * s->dz));
+        }
+        mx = fmax(mx, sr);
+      }
+  return cfl / mx;
+}
+
+double or_dt(const or_cfg *c, const double *w, double cfl) {
+  ws_t s;
+  if (ws_init(&s, c)) { ws_free(&s); return -1.0; }
+  double dt = dt_ws(&s, w, cfl);
+  ws_free(&s);
+  return dt;
+}
+
+/* ------------------------------------------------------------------- RK3 ---
+ * n low-storage RK3 steps of w (in place).  dt: when cfl > 0 it is
+ * recomputed at the start of every step whose counter is a multiple of
+ * dt_every and frozen within the step; otherwise dt_fixed.  *step_io and
+ * *dt_io carry the step counter and the current dt across calls. */
+int or_step(const or_cfg *c, double *w, int nsteps, double cfl, double dt_fixed, int dt_every,
+            long long *step_io, double *dt_io) {
+  ws_t s;
+  if (ws_init(&s, c)) { ws_free(&s); return -1; }
+  size_t tot = NV * s.n;
+  double *R = (double *)malloc(sizeof(double) * tot);
+  double *Rp = (double *)calloc(tot, sizeof(double));
+  if (!R || !Rp) { free(R); free(Rp); ws_free(&s); return -1; }
+  long long step = step_io ? *step_io : 0;
+  double dt = dt_io ? *dt_io : dt_fixed;
+  if (dt_every < 1) dt_every = 1;
+  for (int it = 0; it < nsteps; ++it, ++step) {
+    if (cfl > 0.0) {
+      if (step % dt_every == 0 || dt <= 0.0) dt = dt_ws(&s, w, cfl);
+    } else {
+      dt = dt_fixed;
+    }
+    for (int st = 0; st < 3; ++st) {
+      rhs_ws(&s, w, R, NULL, NULL, NULL, OR_CONV | OR_VISC | OR_FORCE, NULL);
+      for (size_t q = 0; q < tot; ++q) w[q] += dt * (RK_GAMMA[st] * R[q] + RK_RHO[st] * Rp[q]);
+      double *t = Rp; Rp = R; R = t;
+    }
+  }
+  if (step_io) *step_io = step;
+  if (dt_io) *dt_io = dt;
+  free(R); free(Rp);
+  ws_free(&s);
+  return 0;
+}
+
+/* RK3 on the scalar ODE y' = lambda y with the same coefficient table. */
+double or_rk3_scalar(double lambda, double y0, double dt, int nsteps) {
+  double y = y0, rp = 0.0;
+  for (int it = 0; it < nsteps; ++it) {
+    rp = 0.0;
+    for (int st = 0; st < 3; ++st) {
+      double r = lambda * y;
+      y += dt * (RK_GAMMA[st] * r + RK_RHO[st] * rp);
+      rp = r;
+    }
+  }
+  return y;
+}

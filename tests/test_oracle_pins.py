@@ -1,0 +1,579 @@
+"""Pins of the CPU oracle against facts fixed by mathematics and published
+methods (closed forms, invariants, exact solutions, convergence orders).
+
+None of these recomputes an oracle formula the same way; each checks a
+property that a dropped term, a wrong sign, index or coefficient breaks.
+"""
+import numpy as np
+import pytest
+import sympy as sp
+
+from oracle import oracle as O
+from paper_2304_05494_gb300 import workloads as W
+from tests import exact_riemann as ER
+
+A1 = (0.75, -0.15, 1.0 / 60.0)
+
+
+def mod_wavenumber(k, h):
+    """Closed form of the 6th-order central first derivative on exp(ikx)."""
+    return 2.0 * sum(a * np.sin((l + 1) * k * h) for l, a in enumerate(A1)) / h
+
+
+def _prob(nx, ny, nz, L=2 * np.pi, **kw):
+    return O.Problem(nx, ny, nz, L, L, L, **kw)
+
+
+# ------------------------------------------------------------------ WENO ---
+def _cell_avg_poly(coefs, j):
+    """Cell average over [j-1/2, j+1/2] of sum c_n x^n."""
+    x = sp.Symbol("x")
+    P = sum(c * x ** n for n, c in enumerate(coefs))
+    return float(sp.integrate(P, (x, j - sp.Rational(1, 2), j + sp.Rational(1, 2))))
+
+
+@pytest.mark.parametrize("order,deg", [(5, 2), (7, 3)])
+def test_weno_exact_on_polynomials(order, deg):
+    """Every substencil reconstructs a polynomial of degree r-1 exactly from
+    its cell averages, so any convex weighting returns P(x_{i+1/2})."""
+    rng = np.random.default_rng(7)
+    r = (order + 1) // 2
+    for _ in range(5):
+        c = rng.normal(size=deg + 1)
+        f = np.array([_cell_avg_poly(c, j) for j in range(-(r - 1), r)])
+        exact = sum(cn * 0.5 ** n for n, cn in enumerate(c))
+        assert abs(O.weno_rec(order, f) - exact) < 1e-12 * (1 + abs(exact))
+        q, _ = O.weno_parts(order, f)
+        assert np.allclose(q, exact, atol=1e-12, rtol=0)
+
+
+def _jiang_shu_reference(order):
+    """q_k, beta_k (Jiang-Shu integral definition) and the optimal weights
+    derived symbolically from polynomial reconstruction."""
+    r = (order + 1) // 2
+    x = sp.Symbol("x")
+    fs = sp.symbols("f0:%d" % order)
+    pts = list(range(-(r - 1), r))
+    qs, bs = [], []
+    for k in range(r):
+        st = pts[k:k + r]
+        cs = sp.symbols("c0:%d" % r)
+        P = sum(cs[n] * x ** n for n in range(r))
+        eqs = [sp.integrate(P, (x, j - sp.Rational(1, 2), j + sp.Rational(1, 2))) - fs[pts.index(j)] for j in st]
+        sol = sp.solve(eqs, cs)
+        Pk = P.subs(sol)
+        qs.append(sp.expand(Pk.subs(x, sp.Rational(1, 2))))
+        beta = sum(sp.integrate(sp.diff(Pk, x, l) ** 2, (x, -sp.Rational(1, 2), sp.Rational(1, 2)))
+                   for l in range(1, r))
+        bs.append(sp.expand(beta))
+    # big stencil polynomial -> optimal weights
+    cs = sp.symbols("C0:%d" % order)
+    P = sum(cs[n] * x ** n for n in range(order))
+    eqs = [sp.integrate(P, (x, j - sp.Rational(1, 2), j + sp.Rational(1, 2))) - fs[pts.index(j)] for j in pts]
+    big = sp.expand(P.subs(sp.solve(eqs, cs)).subs(x, sp.Rational(1, 2)))
+    ds = sp.symbols("d0:%d" % r)
+    comb = sp.expand(sum(ds[k] * qs[k] for k in range(r)) - big)
+    dsol = sp.solve([comb.coeff(f) for f in fs], ds)
+    return fs, qs, bs, [dsol[d] for d in ds]
+
+
+@pytest.mark.parametrize("order", [5, 7])
+def test_weno_smoothness_indicators_and_weights(order):
+    """beta_k equal the Jiang-Shu integral definition; q_k the substencil
+    polynomials; optimal weights reproduce the full-stencil reconstruction
+    and give the classic upwind-5 formula (2,-13,47,27,-3)/60 for WENO5."""
+    fs, qs, bs, d = _jiang_shu_reference(order)
+    if order == 5:
+        assert [sp.nsimplify(v) for v in d] == [sp.Rational(1, 10), sp.Rational(3, 5), sp.Rational(3, 10)]
+        lin = sp.expand(sum(d[k] * qs[k] for k in range(3)))
+        assert [lin.coeff(f) for f in fs] == [sp.Rational(c, 60) for c in (2, -13, 47, 27, -3)]
+    else:
+        assert [sp.nsimplify(v) for v in d] == [sp.Rational(1, 35), sp.Rational(12, 35),
+                                                 sp.Rational(18, 35), sp.Rational(4, 35)]
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        f = rng.normal(size=order)
+        sub = dict(zip(fs, f))
+        q, b = O.weno_parts(order, f)
+        qref = np.array([float(e.subs(sub)) for e in qs])
+        # the Balsara-Shu WENO7 indicators are the integrals scaled by 240
+        scale = 1.0 if order == 5 else 240.0
+        bref = np.array([float(e.subs(sub)) for e in bs]) * scale
+        assert np.allclose(q, qref, rtol=1e-12, atol=1e-12)
+        assert np.allclose(b, bref, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("order,min_rate", [(5, 4.5), (7, 6.0)])
+def test_weno_convergence_smooth(order, min_rate):
+    """On cell averages of a smooth function away from critical points the
+    reconstruction converges at the design order."""
+    errs = []
+    for h in (0.1, 0.05):
+        x0 = 0.3  # interface position; sin has no critical point near it
+        r = (order + 1) // 2
+        centres = x0 - 0.5 * h + h * np.arange(-(r - 1), r)
+        f = (np.cos(centres - 0.5 * h) - np.cos(centres + 0.5 * h)) / h  # averages of sin
+        errs.append(abs(O.weno_rec(order, f) - np.sin(x0)))
+    assert np.log2(errs[0] / errs[1]) > min_rate
+
+
+def test_weno_non_oscillatory_at_step():
+    """At a discontinuity the stencils that cross it get vanishing weight:
+    the result stays within the smooth side's range (ENO property)."""
+    f = np.array([1.0, 1.0, 1.0, 0.0, 0.0])  # jump between i and i+1
+    v = O.weno_rec(5, f)
+    assert abs(v - 1.0) < 1e-6
+    f7 = np.array([1.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    assert abs(O.weno_rec(7, f7) - 1.0) < 1e-6
+
+
+# ------------------------------------------------------- eigenvectors ---
+def _euler_flux(U, d, g):
+    rho, m, E = U[0], U[1:4], U[4]
+    u = m / rho
+    p = (g - 1.0) * (E - 0.5 * rho * np.dot(u, u))
+    F = np.empty(5, dtype=U.dtype)
+    F[0] = m[d]
+    F[1:4] = m[d] * u
+    F[1 + d] += p
+    F[4] = (E + p) * u[d]
+    return F
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_eigenvectors_diagonalise_jacobian(d):
+    """L R = I and L A R = diag(u-c, u, u, u, u+c), A = dF/dU by complex step
+    of the Euler flux."""
+    g = 1.4
+    rng = np.random.default_rng(11 + d)
+    for _ in range(3):
+        rho = rng.uniform(0.5, 2)
+        u = rng.normal(size=3)
+        p = rng.uniform(0.5, 2)
+        E = p / (g - 1) + 0.5 * rho * np.dot(u, u)
+        H = (E + p) / rho
+        L, R, c = O.eigvec(g, d, u, H)
+        assert np.allclose(L @ R, np.eye(5), atol=1e-12)
+        U = np.array([rho, *(rho * u), E])
+        A = np.zeros((5, 5))
+        hh = 1e-30
+        for k in range(5):
+            Uc = U.astype(complex)
+            Uc[k] += 1j * hh
+            A[:, k] = _euler_flux(Uc, d, g).imag / hh
+        lam = L @ A @ R
+        expect = np.diag([u[d] - c, u[d], u[d], u[d], u[d] + c])
+        assert np.allclose(lam, expect, atol=1e-11)
+        assert abs(c - np.sqrt(g * p / rho)) < 1e-13
+
+
+# --------------------------------------------------------------- RK3 ---
+def test_rk3_third_order_and_consistency():
+    e = [abs(O.rk3_scalar(-1.0, 1.0, 1.0 / n, n) - np.exp(-1.0)) for n in (20, 40, 80)]
+    r1, r2 = np.log2(e[0] / e[1]), np.log2(e[1] / e[2])
+    assert 2.8 < r1 < 3.2 and 2.8 < r2 < 3.2
+    # one step of y' = lambda y reproduces the cubic Taylor polynomial
+    z = 0.1
+    assert abs(O.rk3_scalar(1.0, 1.0, z, 1) - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+
+
+# ------------------------------------------------------------- metric ---
+def test_metric_uniform_and_periodic_stretched():
+    p = _prob(8, 16, 8)
+    ey, eyy = O.metric(p)
+    assert np.allclose(ey, 16 / (2 * np.pi), rtol=1e-13) and np.allclose(eyy, 0, atol=1e-9)
+    errs = []
+    for ny in (16, 32):
+        xi = np.arange(ny) * 2 * np.pi / ny
+        A = 0.3
+        y = xi + A * np.sin(xi)
+        p = _prob(4, ny, 4, y=y)
+        ey, eyy = O.metric(p)
+        h = 2 * np.pi / ny
+        yx = 1 + A * np.cos(xi)      # dy/dxi
+        yxx = -A * np.sin(xi)
+        ey_ex = 1.0 / (yx * h)       # deta/dy with eta = xi/h
+        eyy_ex = -(yxx * h * h) / (yx * h) ** 3
+        errs.append((np.max(np.abs(ey / ey_ex - 1)), np.max(np.abs(eyy - eyy_ex) / np.max(np.abs(eyy_ex)))))
+    assert np.log2(errs[0][0] / errs[1][0]) > 5.5
+    assert np.log2(errs[0][1] / errs[1][1]) > 5.5
+
+
+def test_metric_wall_mirror_interior_order():
+    """With walls, nodes at least 3 away from the walls see only true nodes
+    and converge at 6th order to the analytic tanh map."""
+    out = []
+    for ny in (32, 64):
+        beta = 1.8
+        y = W.tanh_nodes(ny, beta)
+        p = O.Problem(4, ny, 4, 1.0, 2.0, 1.0, y=y, wall_y=True)
+        ey, _ = O.metric(p)
+        xi = -1 + (np.arange(ny) + 0.5) * 2 / ny
+        h = 2.0 / ny
+        yx = beta / np.cosh(beta * xi) ** 2 / np.tanh(beta)
+        j = np.arange(3, ny - 3)
+        xs = xi[j]
+        sel = np.abs(xs) < 0.5  # same physical region at both resolutions
+        out.append(np.max(np.abs(ey[j][sel] * yx[j][sel] * h - 1)))
+    assert np.log2(out[0] / out[1]) > 5.5
+
+
+# ------------------------------------------------- discrete properties ---
+@pytest.mark.parametrize("weno", [0, 5, 7])
+def test_free_stream_exact(weno):
+    """A uniform state has R = 0 exactly, uniform and stretched y, central
+    and WENO-forced, viscous."""
+    for stretched in (False, True):
+        y = None
+        if stretched:
+            xi = np.arange(12) * 2 * np.pi / 12
+            y = xi + 0.3 * np.sin(xi)
+        p = _prob(10, 12, 9, y=y, mach=0.4, re=50.0, weno_order=weno, threshold=-1.0)
+        one = np.ones((9, 12, 10))
+        w = W.conserved(1.2 * one, 0.3 * one, -0.2 * one, 0.1 * one, 1.1 * one, 1.4, 0.4)
+        # the inviscid fluxes cancel exactly; the second-derivative stencil of
+        # a constant is zero only up to the rounding of its coefficients
+        assert np.max(np.abs(O.rhs(p, w, terms=O.CONV))) == 0.0
+        assert np.max(np.abs(O.rhs(p, w))) < 1e-13
+
+
+def test_quiescent_walls_fixed_point():
+    y = W.tanh_nodes(16, 1.5)
+    p = O.Problem(8, 16, 6, 3.0, 2.0, 2.0, y=y, wall_y=True, t_wall=1.0, mach=1.5, re=300.0,
+                  weno_order=5, threshold=-1.0, force=True)
+    one = np.ones((6, 16, 8))
+    w = W.conserved(one, 0 * one, 0 * one, 0 * one, one, 1.4, 1.5)
+    assert np.max(np.abs(O.rhs(p, w, terms=O.CONV))) == 0.0
+    assert np.max(np.abs(O.rhs(p, w))) < 1e-12
+
+
+@pytest.mark.parametrize("weno", [0, 5, 7])
+def test_discrete_conservation_periodic(weno):
+    """Flux form: sum over a periodic box of every inviscid R is round-off,
+    with stretched y weighted by the cell volume 1/eta_y; with constant
+    viscosity mass and momentum stay conserved."""
+    xi = np.arange(14) * 2 * np.pi / 14
+    y = xi + 0.25 * np.sin(xi)
+    p = _prob(12, 14, 10, y=y, mach=0.6, re=-1.0, weno_order=weno, threshold=0.3)
+    w = W.smooth_periodic(12, 14, 10, seed=5, mach=0.6, amp_u=0.8, amp_s=0.3)
+    r, flags = O.rhs(p, w, flags=True)
+    if weno:
+        frac = np.mean(np.concatenate([f.ravel() for f in flags]))
+        assert 0.05 < frac < 0.95  # both branches active
+    ey, _ = O.metric(p)
+    dv = (1.0 / ey)[None, None, :, None]
+    tot = np.sum(r * dv, axis=(1, 2, 3))
+    scale = np.sum(np.abs(r) * dv, axis=(1, 2, 3))
+    assert np.all(np.abs(tot) < 1e-13 * scale)
+    # constant viscosity: mass and momentum
+    p2 = _prob(12, 14, 10, mach=0.6, re=20.0, visc_exp=0.0, weno_order=0)
+    r2 = O.rhs(p2, w, terms=O.VISC)
+    tot2 = np.sum(r2, axis=(1, 2, 3))
+    sc2 = np.sum(np.abs(r2), axis=(1, 2, 3))
+    assert np.all(np.abs(tot2[1:4]) < 1e-13 * sc2[1:4])
+
+
+def _d1_periodic(f, axis, h):
+    out = np.zeros_like(f)
+    for l, a in enumerate(A1, start=1):
+        out += a * (np.roll(f, -l, axis=axis) - np.roll(f, l, axis=axis))
+    return out / h
+
+
+def test_kinetic_energy_preservation():
+    """Inviscid split form: sum(u.R_mom - |u|^2/2 R_rho) equals the pressure
+    work sum(p div_h u) exactly (the convective part conserves kinetic
+    energy), on random smooth periodic fields."""
+    n = (14, 12, 10)
+    p = _prob(n[0], n[1], n[2], mach=0.5, re=-1.0, weno_order=0)
+    w = W.smooth_periodic(*n, seed=21, mach=0.5, amp_u=0.7, amp_s=0.3)
+    r = O.rhs(p, w, terms=O.CONV)
+    rho = w[0]
+    u, v, ww = w[1] / rho, w[2] / rho, w[3] / rho
+    R = 1 / (1.4 * 0.25)
+    T = (w[4] / rho - 0.5 * (u * u + v * v + ww * ww)) / (R / 0.4)
+    pr = rho * R * T
+    h = [2 * np.pi / m for m in n]
+    lhs = np.sum(u * r[1] + v * r[2] + ww * r[3] - 0.5 * (u * u + v * v + ww * ww) * r[0])
+    div = _d1_periodic(u, 2, h[0]) + _d1_periodic(v, 1, h[1]) + _d1_periodic(ww, 0, h[2])
+    rhs_ = np.sum(pr * div)
+    scale = np.sum(np.abs(u * r[1])) + np.sum(np.abs(pr * div))
+    assert abs(lhs - rhs_) < 1e-13 * scale
+    # and the identity is not trivially satisfied
+    assert abs(rhs_) > 1e-6 * scale
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_modified_wavenumber_entropy_wave(axis):
+    """Density wave at uniform velocity and pressure: R_rho is exactly
+    -U eps cos(k x) times the closed-form modified wavenumber."""
+    n = 16
+    k = 3
+    h = 2 * np.pi / n
+    x = np.arange(n) * h
+    eps, U = 0.1, 0.7
+    shape = (n, n, n)
+    X = np.meshgrid(x, x, x, indexing="ij")[2 - axis]  # coordinate along `axis` (x is last)
+    rho = 1.0 + eps * np.sin(k * X)
+    vel = [np.zeros(shape)] * 3
+    vel = [np.zeros(shape), np.zeros(shape), np.zeros(shape)]
+    vel[axis] = U * np.ones(shape)
+    R = 1 / (1.4 * 0.3 ** 2)
+    T = 1.0 / rho  # p = R uniform
+    w = W.conserved(rho, vel[0], vel[1], vel[2], T, 1.4, 0.3)
+    p = _prob(n, n, n, mach=0.3, re=-1.0)
+    r = O.rhs(p, w, terms=O.CONV)
+    exact = -U * eps * np.cos(k * X) * mod_wavenumber(k, h)
+    assert np.max(np.abs(r[0] - exact)) < 1e-12
+    assert np.max(np.abs(r[1 + axis] - U * exact)) < 1e-12
+
+
+# ----------------------------------------------------------------- sensor ---
+def test_sensor_closed_forms():
+    n = 16
+    h = 2 * np.pi / n
+    x = np.arange(n) * h
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    A = 0.8
+    one = np.ones_like(X)
+    # 1-D compression/expansion: u = -A sin x  -> theta = -A k' cos x, omega = 0
+    w = W.conserved(one, -A * np.sin(X), 0 * one, 0 * one, one, 1.4, 0.5)
+    s, d = O.sensor(_prob(n, n, n, mach=0.5), w)
+    kp = mod_wavenumber(1, h)
+    th = -A * kp * np.cos(X)
+    assert np.allclose(d, th, atol=1e-13)
+    assert np.allclose(s, np.maximum(-th / np.sqrt(th * th + 1.0), 0.0), atol=1e-14)
+    # solenoidal Taylor-Green velocity: theta = 0 to round-off, sensor 0
+    c = W.taylor_green(n)
+    s2, d2 = O.sensor(_prob(n, n, n, mach=c.mach), c.w0)
+    assert np.max(np.abs(d2)) < 1e-12 and np.max(s2) < 1e-12
+
+
+# ----------------------------------------------------- manufactured RHS ---
+def _ns_rhs_exact(fields, mach, re, pr, gamma, visc_exp):
+    """Analytic compressible Navier-Stokes RHS (divergence form) of the
+    closed-form fields (rho, u, v, w, T) of x, y, z."""
+    x, y, z = sp.symbols("x y z")
+    rho, u, v, w, T = fields
+    R = 1 / (gamma * mach ** 2)
+    cp = gamma * R / (gamma - 1)
+    p = rho * R * T
+    H = cp * T + (u * u + v * v + w * w) / 2
+    U = [u, v, w]
+    X = [x, y, z]
+    mu = T ** visc_exp / re
+    kc = mu * cp / pr
+    th = sum(sp.diff(U[a], X[a]) for a in range(3))
+    tau = [[mu * (sp.diff(U[a], X[b]) + sp.diff(U[b], X[a]) - (sp.Rational(2, 3) * th if a == b else 0))
+            for b in range(3)] for a in range(3)]
+    out = [-sum(sp.diff(rho * U[j], X[j]) for j in range(3))]
+    for i in range(3):
+        out.append(-sum(sp.diff(rho * U[i] * U[j] + (p if i == j else 0), X[j]) for j in range(3))
+                   + sum(sp.diff(tau[i][j], X[j]) for j in range(3)))
+    out.append(-sum(sp.diff(rho * U[j] * H, X[j]) for j in range(3))
+               + sum(sp.diff(sum(U[i] * tau[i][j] for i in range(3)) + kc * sp.diff(T, X[j]), X[j])
+                     for j in range(3)))
+    f = [sp.lambdify((x, y, z), e, "numpy") for e in fields]
+    r = [sp.lambdify((x, y, z), e, "numpy") for e in out]
+    return f, r
+
+
+def _mms_exact(mach, re, pr, gamma, visc_exp):
+    x, y, z = sp.symbols("x y z")
+    rho = 1 + sp.Rational(1, 5) * sp.sin(x + sp.Rational(3, 10)) * sp.cos(y) + sp.sin(z) / 10
+    u = sp.sin(y + z) / 2 + sp.cos(x) / 5
+    v = sp.Rational(2, 5) * sp.cos(x + z) - sp.sin(y) / 10
+    w = sp.Rational(3, 10) * sp.sin(x - y) + sp.cos(z) / 5
+    T = 1 + sp.cos(x) * sp.sin(y + z) / 10
+    return _ns_rhs_exact((rho, u, v, w, T), mach, re, pr, gamma, visc_exp)
+
+
+@pytest.fixture(scope="module")
+def mms():
+    return _mms_exact(0.5, 100.0, 0.72, 1.4, 0.76)
+
+
+@pytest.mark.parametrize("stretched", [False, True])
+def test_design_order_manufactured(mms, stretched):
+    """R_h(w*) - R(w*) falls as h^6 for convective (split form) plus
+    viscous (Laplacian form) terms, uniform and stretched y."""
+    fields, rhs = mms
+    errs = []
+    for n in (16, 32):
+        xi = np.arange(n) * 2 * np.pi / n
+        yv = xi + 0.3 * np.sin(xi) if stretched else xi
+        Z, Y, X = np.meshgrid(xi, yv, xi, indexing="ij")
+        vals = [f(X, Y, Z) * np.ones_like(X) for f in fields]
+        w = W.conserved(*vals, 1.4, 0.5)
+        p = _prob(n, n, n, y=yv if stretched else None, mach=0.5, re=100.0, prandtl=0.72,
+                  visc_exp=0.76, weno_order=0)
+        r = O.rhs(p, w)
+        ex = np.stack([g(X, Y, Z) * np.ones_like(X) for g in rhs])
+        errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(rates > 5.4), rates
+
+
+@pytest.mark.parametrize("order,min_rate", [(5, 4.0), (7, 5.5)])
+def test_weno_forced_order_entropy_wave(order, min_rate):
+    """WENO everywhere on a smooth entropy wave: the mass RHS converges to
+    -U drho/dx at (nearly) the design order."""
+    errs = []
+    for n in (32, 64):
+        h = 2 * np.pi / n
+        x = np.arange(n) * h
+        X = x[None, None, :] * np.ones((1, 1, n))
+        rho = 1.0 + 0.2 * np.sin(X)
+        one = np.ones_like(X)
+        w = W.conserved(rho, 0.6 * one, 0 * one, 0 * one, 1.0 / rho, 1.4, 0.5)
+        p = O.Problem(n, 1, 1, 2 * np.pi, 1.0, 1.0, mach=0.5, re=-1.0, weno_order=order, threshold=-1.0)
+        r = O.rhs(p, w, terms=O.CONV)
+        ex = -0.6 * 0.2 * np.cos(X)
+        errs.append(np.mean(np.abs(r[0] - ex)))
+    assert np.log2(errs[0] / errs[1]) > min_rate
+
+
+# ----------------------------------------------------------- wall / forcing ---
+def test_channel_reflection_symmetry():
+    """A state even in y (rho, T, u, w) with odd v on the symmetric tanh grid
+    gives an RHS with the same symmetry: both walls use consistent
+    mirror maps."""
+    ny = 16
+    y = W.tanh_nodes(ny, 1.6)
+    nx, nz = 8, 6
+    rng = np.random.default_rng(2)
+    x = np.arange(nx) * 2 * np.pi / nx
+    z = np.arange(nz) * 2 * np.pi / nz
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    ph = rng.uniform(0, 6, 4)
+    rho = 1 + 0.1 * np.cos(X + ph[0]) * (1 - Y ** 2)
+    T = 1 + 0.2 * (1 - Y ** 4) + 0.05 * np.sin(Z + ph[1])
+    u = 1.5 * (1 - Y ** 2) * (1 + 0.1 * np.sin(X + Z))
+    v = 0.1 * Y * (1 - Y ** 2) * np.cos(X + ph[2])
+    ww = 0.1 * (1 - Y ** 2) * np.sin(Z + ph[3])
+    w = W.conserved(rho, u, v, ww, T, 1.4, 1.5)
+    p = O.Problem(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, y=y, wall_y=True, mach=1.5, re=300.0,
+                  weno_order=5, threshold=0.05, force=True)
+    r = O.rhs(p, w)
+    par = np.array([1, 1, -1, 1, 1])
+    flipped = r[:, :, ::-1, :] * par[:, None, None, None]
+    scale = np.max(np.abs(r), axis=(1, 2, 3))[:, None, None, None]
+    assert np.max(np.abs(flipped - r) / scale) < 1e-12
+
+
+def test_forcing_keeps_bulk_momentum():
+    c = W.channel(16, 16, 8, seed=99)
+    p = O.Problem(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, y=c.y, wall_y=True, mach=c.mach, re=c.re,
+                  force=True, weno_order=5)
+    ey, _ = O.metric(p)
+    dv = (1.0 / ey)[None, :, None]
+    b0 = np.sum(c.w0[1] * dv)
+    w, _, _ = O.step(p, c.w0, 3, dt_fixed=2e-3)
+    assert abs(np.sum(w[1] * dv) - b0) < 1e-13 * abs(b0)
+    r = O.rhs(p, w)
+    assert abs(np.sum(r[1] * dv)) < 1e-12 * np.sum(np.abs(r[1]) * dv)
+
+
+def test_dt_closed_form_uniform():
+    p = _prob(8, 8, 8, mach=0.5, re=200.0, prandtl=0.7)
+    one = np.ones((8, 8, 8))
+    w = W.conserved(1.3 * one, 0.4 * one, -0.3 * one, 0.2 * one, 1.2 * one, 1.4, 0.5)
+    R = 1 / (1.4 * 0.25)
+    c = np.sqrt(1.4 * R * 1.2)
+    h = 2 * np.pi / 8
+    conv = (0.4 + c + 0.3 + c + 0.2 + c) / h
+    visc = 1.4 * (1.2 ** 0.76 / 200.0) / (0.7 * 1.3) * 3 / h ** 2
+    assert abs(O.dt(p, w, 0.8) - 0.8 / (conv + visc)) < 1e-14
+
+
+# --------------------------------------------------------- exact solutions ---
+def test_riemann_solver_textbook_values():
+    """Star state of Sod's problem as tabulated by Toro (Table 4.3)."""
+    ps, us = ER.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+    assert abs(ps - 0.30313) < 5e-5 and abs(us - 0.92745) < 5e-5
+
+
+def test_sod_exact_solution():
+    """Double Sod problem, WENO5 everywhere, t = 0.2: density close to the
+    exact solution in L1 and first-order convergence."""
+    errs = []
+    for n in (200, 400):
+        w0, x, mach = W.double_sod(n)
+        p = O.Problem(n, 1, 1, 2.0, 1.0, 1.0, mach=mach, re=-1.0, weno_order=5, threshold=-1.0)
+        dtv = 0.2 / (n // 2)
+        w, _, _ = O.step(p, w0, n // 2, dt_fixed=dtv)
+        rho = w[0, 0, 0]
+        # right-moving Sod at x = 1.5 and its mirror at x = 0.5
+        ex = np.where(x >= 1.0,
+                      ER.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (x - 1.5) / 0.2)[0],
+                      ER.sample((0.125, 0.0, 0.1), (1.0, 0.0, 1.0), (x - 0.5) / 0.2)[0])
+        errs.append(np.mean(np.abs(rho - ex)) * 2.0)
+        assert np.all(np.isfinite(w))
+        # mirror symmetry about x = 1
+        assert np.max(np.abs(rho - rho[::-1])) < 1e-10
+    assert errs[1] < 0.012
+    assert errs[0] / errs[1] > 1.5
+
+
+def test_isentropic_vortex_translation():
+    """Shu's vortex is carried unchanged by the uniform stream: after one
+    period the density matches the initial field, converging with h."""
+    errs = []
+    for n in (24, 48):
+        w0, mach = W.isentropic_vortex(n)
+        p = O.Problem(n, n, 1, 10.0, 10.0, 1.0, mach=mach, re=-1.0, weno_order=0)
+        nsteps = 4 * n
+        w, _, _ = O.step(p, w0, nsteps, dt_fixed=10.0 / nsteps)
+        errs.append(np.max(np.abs(w[0] - w0[0])))
+    assert errs[1] < 2e-3
+    assert np.log2(errs[0] / errs[1]) > 2.8
+
+
+def test_design_order_manufactured_walls():
+    """Isothermal no-slip walls: fields whose mirror continuation is analytic
+    (velocity and T - T_w odd about each wall, pressure even) make the whole
+    RHS, wall rows included, converge at 6th order.  This pins the ghost
+    rules of velocity, temperature, density and the stored divergence."""
+    x, y, z = sp.symbols("x y z")
+    mach, tw = 0.8, 1.0
+    R = 1 / (1.4 * mach ** 2)
+    cy, sy = sp.cos(sp.pi * y / 2), sp.sin(sp.pi * y)
+    u = (sp.Rational(3, 2) + sp.sin(x + z) / 5) * cy
+    v = sp.Rational(3, 10) * sy * sp.cos(x)
+    w = sp.Rational(2, 5) * cy * sp.sin(z)
+    T = tw + sp.Rational(3, 10) * cy * (1 + sp.cos(x) / 10)
+    p = R * (1 + sp.cos(sp.pi * y) * sp.cos(z) / 10)
+    rho = p / (R * T)
+    fields, rhs = _ns_rhs_exact((rho, u, v, w, T), mach, 50.0, 0.72, 1.4, 0.76)
+    errs = []
+    for ny in (16, 32):
+        nx = nz = ny // 2
+        xs = np.arange(nx) * 2 * np.pi / nx
+        zs = np.arange(nz) * 2 * np.pi / nz
+        ys = -1.0 + (np.arange(ny) + 0.5) * 2.0 / ny
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        vals = [f(X, Y, Z) * np.ones_like(X) for f in fields]
+        wv = W.conserved(*vals, 1.4, mach)
+        pr = O.Problem(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, wall_y=True, t_wall=tw, mach=mach,
+                       re=50.0, weno_order=0)
+        r = O.rhs(pr, wv)
+        ex = np.stack([g(X, Y, Z) * np.ones_like(X) for g in rhs])
+        errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(rates > 5.0), rates
+
+
+def test_forcing_is_body_force_with_its_power():
+    """The forcing adds a uniform x force f to the x momentum and its power
+    f u to the energy, nothing else, with f closing the volume balance."""
+    c = W.channel(12, 16, 8, seed=5)
+    p = O.Problem(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, y=c.y, wall_y=True, mach=c.mach, re=c.re,
+                  force=True, weno_order=5)
+    full = O.rhs(p, c.w0)
+    base = O.rhs(p, c.w0, terms=O.CONV | O.VISC)
+    d = full - base
+    f = d[1].ravel()[0]
+    assert abs(f) > 0
+    assert np.allclose(d[1], f, rtol=1e-12, atol=0)
+    assert np.max(np.abs(d[[0, 2, 3]])) == 0.0
+    assert np.allclose(d[4], f * c.w0[1] / c.w0[0], rtol=1e-12, atol=1e-15)
