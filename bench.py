@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point RK3 steps per second of the FP64 solver.
+
+Workload: the compressible turbulent channel, bulk Mach 1.5, Re_tau ~ 220,
+256 x 128 x 128 points (6 pi h x 2h x 2 pi h, tanh-stretched y, isothermal
+walls, constant mass flow), hybrid central-6 / WENO5 where the sensor
+exceeds 0.2, 6th-order viscous terms, dt from CFL 0.8 every 10 steps.
+Synthetic seeded initial state (laminar Poiseuille profile plus 10 %
+smooth random velocity perturbations).
+
+One step = one full RK3 step (3 RHS stages) of the whole grid.  The state
+(168 MB) and the working set (~1.2 GB) are larger than the 129 MB L2, so no
+L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun as independent replicas (the solver does not
+shard across GPUs); value = all ranks' point-steps / the slowest rank's time.
+The reference arm times the plain CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK3 steps/s"
+UNIT = "point-steps/s"
+
+# Algorithmic FP64 flops per interior point of one launch (FMA = 2), counted
+# from the kernel arithmetic; WENO adds WENO5_FLOPS per flagged interface.
+ALG_FLOPS = {"prims": 25, "grad": 92, "flux_x": 95, "flux_y": 95, "flux_z": 95, "visc": 280, "update": 23}
+WENO5_FLOPS = 2000
+# FP64 peak: 152 SMs x 2 DFMA/clk (4 flop) x 2070 MHz maximum SM clock.
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2304_05494_gb300 import workloads as W
+    return W.channel()
+
+
+def config_of(case):
+    return {"workload": "compressible channel %dx%dx%d (6pi x 2 x 2pi, tanh y, M_b=1.5, Re_tau~220), "
+                        "FP64 hybrid central-6/WENO5 (sensor>0.2), viscous-6, RK3, CFL 0.8 dt every 10"
+                        % (case.nx, case.ny, case.nz),
+            "points": case.points, "grid": [case.nx, case.ny, case.nz], "seed": 1235,
+            "l2": "inputs larger than L2 (state 168 MB, working set ~1.2 GB > 129 MB L2); no flush"}
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(case, budget_s: float = 15.0):
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    import numpy as np  # noqa: F401
+    from oracle import oracle as O
+    O.build()
+    pr = O.Problem(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, y=case.y, mach=case.mach, re=case.re,
+                   visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
+                   force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+    t0 = time.perf_counter()
+    O.step(pr, case.w0, 1, cfl=case.cfl, dt_every=case.dt_every)
+    one = time.perf_counter() - t0
+    steps = max(1, min(10, int(budget_s / max(one, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    O.step(pr, case.w0, steps, cfl=case.cfl, dt_every=case.dt_every)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": case.points * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK3 step(s) of the full %dx%dx%d channel after 1 untimed step (%.1f s)"
+                      % (steps, case.nx, case.ny, case.nz, el)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    import numpy as np
+    case = workload()
+    O.build()
+    # bounded sample: a z-slab of the channel sized so one step is ~2 s here
+    nz = case.nz
+    pr_full = None
+    del pr_full
+    t_target = 2.0
+    sub = max(4, nz // 8)
+    w = np.ascontiguousarray(case.w0[:, :sub])
+    lz = case.lz * sub / nz
+    pr = O.Problem(case.nx, case.ny, sub, case.lx, case.ly, lz, y=case.y, mach=case.mach, re=case.re,
+                   visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
+                   force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+    t0 = time.perf_counter()
+    w, st, dt = O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every)
+    one = time.perf_counter() - t0
+    if one > 0 and one * 1.2 < t_target:
+        pass
+    for _ in range(args.warmup):
+        w, st, dt = O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every, step0=st, dt0=dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        w, st, dt = O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every, step0=st, dt0=dt)
+    el = time.perf_counter() - t0
+    pts = case.nx * case.ny * sub
+    value = pts * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%d-plane z-slab (%dx%dx%d, same spacing) of the channel, one RK3 step per bench step" % (
+        sub, case.nx, case.ny, sub)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(case),
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value, "unit": UNIT},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def our_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2304_05494_gb300 import s2
+
+    case = workload()
+    stream = torch.cuda.Stream()
+    sv = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local)
+    sv.set_state(case.w0)
+    # warm-up (graph capture happens here)
+    sv.step(args.warmup)
+    sv.sync()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = sv.stats()["launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sv.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    st = sv.stats()
+    launches = st["launches"] - launches0
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = case.points * args.steps * world / (t_max * 1e-3)
+
+    # per-kernel device times (CUDA events on the solver's stream)
+    prof = sv.profile(args.profile_steps)
+    st2 = sv.stats()
+    weno_frac = st2["weno_frac"]
+    dom = max(((k, v) for k, v in prof.items() if k in ALG_FLOPS), key=lambda kv: kv[1][0])
+    name, (kms, kl) = dom
+    per_launch_ms = kms / max(kl, 1)
+    flops = ALG_FLOPS[name] * case.points
+    if name.startswith("flux_"):
+        flops += WENO5_FLOPS * weno_frac * case.points
+    achieved = flops / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": name,
+                "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2070 MHz (measured FMA loop: 1204 GFLOP/s)",
+                "per_launch_ms": per_launch_ms,
+                "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1]}}
+
+    # end to end through the C ABI with host buffers: H2D of the step's
+    # input state, one step, D2H of the result, every step
+    pinned_in = torch.from_numpy(case.w0).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    win = pinned_in.numpy()
+    wout = pinned_out.numpy()
+    sv.set_state(win)
+    sv.step(1)
+    sv.get_state(wout)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sv.set_state(win)
+        sv.step(1)
+        sv.get_state(wout)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    nbytes = case.w0.nbytes
+    e2e = {"value": case.points * args.e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+    finite = bool(np.isfinite(wout).all())
+    sv.close()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
+               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "weno_frac": weno_frac, "state_finite": finite}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(case)
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

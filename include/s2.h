@@ -1,0 +1,210 @@
+/*
+ * s2.h -- C ABI of the GB300 STREAmS-2 solver (libs2.so).
+ *
+ * The library advances the 3-D compressible Navier-Stokes equations of a
+ * calorically perfect ideal gas on a Cartesian grid, stretched in y, with
+ * the method of the paper's Sec. 2 ("Numerical Methods"): hybrid
+ * convective discretisation (energy-preserving split-form central flux of
+ * 6th order; at interfaces flagged by a modified Ducros shock sensor, a
+ * WENO5/WENO7 reconstruction of characteristic fluxes with Lax-Friedrichs
+ * splitting, projected on the right eigenvectors), 6th-order viscous terms
+ * in Laplacian form, and a third-order low-storage Runge-Kutta scheme.
+ * The call sequence follows the program flow of Sec. 3.1 (create grid,
+ * metrics, gas, boundaries -> initialise -> time loop) and the single
+ * host-to-device copy of the initial field before the loop (Sec. 3.2,
+ * Listing 3); afterwards the state stays resident on the GPU.
+ *
+ * Units: reference density, velocity, temperature and length are 1; the
+ * gas constant is R = 1/(gamma mach_ref^2), p = rho R T,
+ * E = c_v T + |u|^2/2, c_v = R/(gamma-1), mu = (T/t_ref)^visc_exp / re_ref.
+ *
+ * State layout across the ABI: w[v][k][j][i], v = 0..4 = (rho, rho u,
+ * rho v, rho w, rho E), interior points only, i (x) fastest: 5*nx*ny*nz
+ * doubles, the order of the paper's (x, y, z, v) device array (Sec. 3.2,
+ * Listing 2) without its ghost layers.
+ *
+ * Errors: every int-returning call returns S2_OK (0) or a negative code;
+ * s2_strerror names it.  Handles are not thread-safe; each solver issues
+ * all its work on one CUDA stream.  No call allocates device memory except
+ * s2_create (which allocates everything up front).
+ */
+#ifndef S2_H
+#define S2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define S2_OK 0
+#define S2_EINVAL -1      /* bad argument or unsupported configuration */
+#define S2_ENOMEM -2      /* device or host allocation failed */
+#define S2_ECUDA -3       /* a CUDA runtime call failed */
+#define S2_ENONFINITE -4  /* non-positive density/temperature or NaN met */
+#define S2_ETIMEOUT -5    /* a bounded device wait gave up */
+#define S2_EBUSY -6       /* solver busy (reserved) */
+
+#define S2_BC_PERIODIC 0
+#define S2_BC_ISOTHERMAL_WALL 1
+
+#define S2_HOST 0
+#define S2_DEVICE 1
+
+#define S2_FP64 0
+
+typedef struct s2_solver s2_solver; /* opaque; owned by the library */
+
+/* Interior points and box size.  x in [0, lx), z in [0, lz) are periodic;
+ * y spans ly (periodic, or walls at y = -ly/2 and +ly/2). */
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz;
+} s2_grid;
+
+/* Node ordinates in y (Sec. 3.1: the Grid object evaluates the metrics).
+ * y: host pointer to ny increasing values, read during s2_create only;
+ * NULL = uniform nodes y_j = -ly/2 + (j + 1/2) ly/ny.  With walls the
+ * nodes lie strictly inside (-ly/2, ly/2) and the walls sit half way
+ * between the outermost node and its mirror image.  The library derives
+ * eta_y = 1/y_eta and eta_yy from the 6th-order stencil. */
+typedef struct {
+  const double *y;
+} s2_metrics;
+
+/* Gas (Sec. 2: ideal gas; calorically perfect).  re_ref <= 0 = inviscid. */
+typedef struct {
+  double gamma, prandtl, mach_ref, re_ref, visc_exp, t_ref;
+} s2_gas;
+
+/* Boundaries: x and z must be S2_BC_PERIODIC; y periodic or isothermal
+ * no-slip walls at temperature t_wall.  force_mass_flow = 1 adds the
+ * uniform x body force that keeps the bulk rho*u constant (force_rhs_1 of
+ * Table 2). */
+typedef struct {
+  int x, y, z;
+  double t_wall;
+  int force_mass_flow;
+} s2_bcs;
+
+/* Scheme.  central_order and visc_order: 6.  weno_order: 0 (central
+ * everywhere), 5 or 7.  An interface is WENO iff the sensor's maximum over
+ * its stencil exceeds sensor_threshold (strictly).  precision: S2_FP64.
+ * dt: if cfl > 0 it is recomputed from the CFL condition (compute_dt of
+ * Table 2) at every step whose counter is a multiple of dt_every and
+ * frozen within a step; otherwise dt_fixed is used. */
+typedef struct {
+  int central_order, weno_order, visc_order;
+  double sensor_threshold;
+  int precision;
+  double cfl, dt_fixed;
+  int dt_every;
+} s2_scheme;
+
+/* Device options.  alloc/free: optional allocator callbacks (device
+ * memory), both NULL = cudaMalloc/cudaFree.  stream: a cudaStream_t or
+ * NULL for the legacy default stream.  device: CUDA ordinal, or -1 for
+ * the current device. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *ctx);
+  void (*free)(void *ptr, void *ctx);
+  void *ctx;
+  void *stream;
+  int device;
+} s2_device;
+
+/* Monitoring (paper Sec. 3.2 residual, Listings 7-8; Table 2 reductions).
+ * Volume integrals use dV = dx dz / eta_y. */
+typedef struct {
+  double t;             /* simulated time */
+  long long step;       /* completed RK3 steps */
+  double dt;            /* current time step */
+  double mass;          /* integral of rho */
+  double mom[3];        /* integrals of rho u, rho v, rho w */
+  double energy;        /* integral of rho E */
+  double kinetic;       /* integral of rho |u|^2 / 2 */
+  double residual_rhou; /* sqrt(mean(R_rhou^2)) of the last RHS evaluation */
+  double weno_frac;     /* flagged interfaces / (3 N) in the last RHS evaluation */
+  double forcing;       /* body force of the last RHS evaluation */
+  long long launches;   /* kernels launched by s2_step so far (all graph nodes that are kernels) */
+  int status;           /* S2_OK or the first error met on the device */
+} s2_stats_t;
+
+/* Create a solver; allocates all device memory (state, RK register, RHS,
+ * primitive and auxiliary fields with ghost layers) and computes the
+ * metrics.  dev may be NULL.  On success *out owns the solver; release it
+ * with s2_destroy.  S2_EINVAL for unsupported settings. */
+int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas, const s2_bcs *bcs,
+              const s2_scheme *scheme, const s2_device *dev, s2_solver **out);
+
+/* Copy a state in (layout above).  where = S2_HOST: w is host memory
+ * (pageable or pinned); S2_DEVICE: w is device memory on the solver's
+ * device.  The caller keeps ownership; the copy is complete when the call
+ * returns.  The clock (t, step, dt) is left unchanged. */
+int s2_set_state(s2_solver *s, const double *w, int where);
+
+/* Copy the state out; synchronises the solver's stream first.  Returns
+ * S2_ENONFINITE if the device recorded an invalid state. */
+int s2_get_state(s2_solver *s, double *w, int where);
+
+/* Advance n full RK3 steps (3 stages each).  Asynchronous on the solver's
+ * stream: the call enqueues the work (a captured CUDA graph per step) and
+ * returns; an invalid state met on the device is reported by the next
+ * synchronising call (s2_get_state, s2_stats, s2_sync). */
+int s2_step(s2_solver *s, int n);
+
+/* Wait for the solver's stream; returns the device status. */
+int s2_sync(s2_solver *s);
+
+/* Restore the clock (for a restart from a saved state). */
+int s2_set_clock(s2_solver *s, double t, long long step, double dt);
+
+/* Reductions over the current state; synchronises. */
+int s2_stats(s2_solver *s, s2_stats_t *out);
+
+/* Diagnostics: evaluate the right-hand side R(w) of the current state
+ * (all terms, forcing included) into rhs (same layout as the state; host
+ * or device pointer per where).  Synchronises.  The state is unchanged. */
+int s2_rhs(s2_solver *s, double *rhs, int where);
+
+/* Diagnostics: per-interface WENO flags of the last s2_rhs call, as bytes
+ * 0/1, host pointers: fx (nz, ny, nx+1), fy (nz, ny+1, nx), fz (nz+1, ny,
+ * nx); slot p along the direction is the interface between points p-1 and
+ * p.  Any pointer may be NULL. */
+int s2_get_flags(s2_solver *s, unsigned char *fx, unsigned char *fy, unsigned char *fz);
+
+/* Tracing: kernel classes timed by s2_profile. */
+#define S2_PROF_PRIMS 0     /* primitive recovery (+ CFL partials) */
+#define S2_PROF_DT 1        /* CFL max reduction, compute_dt of Table 2 */
+#define S2_PROF_GHOST 2     /* ghost faces of the primitives */
+#define S2_PROF_GRAD 3      /* velocity gradients, divergence, shock sensor */
+#define S2_PROF_GHOST_AUX 4 /* ghost faces of divergence and sensor */
+#define S2_PROF_FLUX_X 5    /* euler_x (central + WENO) */
+#define S2_PROF_FLUX_Y 6    /* euler_y */
+#define S2_PROF_FLUX_Z 7    /* euler_z */
+#define S2_PROF_VISC 8      /* visflx */
+#define S2_PROF_FORCE 9     /* force_rhs_1 (two kernels) */
+#define S2_PROF_UPDATE 10   /* RK3 update */
+#define S2_PROF_KINDS 11
+
+/* Advance n steps launching every kernel directly (no graph) with CUDA
+ * events around each class on the solver's stream; ms[k] receives the
+ * summed device time of class k over the n steps and launches[k] its
+ * kernel count (arrays of S2_PROF_KINDS, host memory; either may be NULL).
+ * The state advances exactly as with s2_step.  Synchronises. */
+int s2_profile(s2_solver *s, int n, double *ms, long long *launches);
+
+/* Name of a kernel class ("prims", "flux_y", ...); NULL if out of range. */
+const char *s2_profile_name(int kind);
+
+/* Release everything; NULL is accepted. */
+void s2_destroy(s2_solver *s);
+
+/* Static description of an error code. */
+const char *s2_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S2_H */

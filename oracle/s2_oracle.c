@@ -362,18 +362,22 @@ int or_weno_parts(int order, const double *g, double *q, double *b) {
     q[1] = (g[1] - 5.0 * g[2] + 13.0 * g[3] + 3.0 * g[4]) / 12.0;
     q[2] = (-g[2] + 7.0 * g[3] + 7.0 * g[4] - g[5]) / 12.0;
     q[3] = (3.0 * g[3] + 13.0 * g[4] - 5.0 * g[5] + g[6]) / 12.0;
-    b[0] = g[0] * (547.0 * g[0] - 3882.0 * g[1] + 4642.0 * g[2] - 1854.0 * g[3]) +
-           g[1] * (7043.0 * g[1] - 17246.0 * g[2] + 7042.0 * g[3]) +
-           g[2] * (11003.0 * g[2] - 9402.0 * g[3]) + 2107.0 * g[3] * g[3];
-    b[1] = g[1] * (267.0 * g[1] - 1642.0 * g[2] + 1602.0 * g[3] - 494.0 * g[4]) +
-           g[2] * (2843.0 * g[2] - 5966.0 * g[3] + 1922.0 * g[4]) +
-           g[3] * (3443.0 * g[3] - 2522.0 * g[4]) + 547.0 * g[4] * g[4];
-    b[2] = g[2] * (547.0 * g[2] - 2522.0 * g[3] + 1922.0 * g[4] - 494.0 * g[5]) +
-           g[3] * (3443.0 * g[3] - 5966.0 * g[4] + 1602.0 * g[5]) +
-           g[4] * (2843.0 * g[4] - 1642.0 * g[5]) + 267.0 * g[5] * g[5];
-    b[3] = g[3] * (2107.0 * g[3] - 9402.0 * g[4] + 7042.0 * g[5] - 1854.0 * g[6]) +
-           g[4] * (11003.0 * g[4] - 17246.0 * g[5] + 4642.0 * g[6]) +
-           g[5] * (7043.0 * g[5] - 3882.0 * g[6]) + 547.0 * g[6] * g[6];
+    /* Balsara & Shu's indicators (240 x the Jiang-Shu measure
+     * sum_l int (d^l p_k/dx^l)^2) written as sums of squares of the
+     * undivided differences e1, e2, e3 of each substencil, which keeps
+     * them free of the cancellation of the expanded quadratic form. */
+    static const double c1[4][2] = {{5.0 / 2.0, 11.0 / 6.0}, {3.0 / 2.0, 1.0 / 3.0},
+                                    {1.0 / 2.0, -1.0 / 6.0}, {-1.0 / 2.0, 1.0 / 3.0}};
+    static const double c2[4] = {2.0, 1.0, 0.0, -1.0};
+    for (int k = 0; k < 4; ++k) {
+      const double *h = g + k; /* substencil f_{i-3+k} .. f_{i+k} */
+      double e1 = h[1] - h[0];
+      double e2 = h[2] - 2.0 * h[1] + h[0];
+      double e3 = h[3] - 3.0 * h[2] + 3.0 * h[1] - h[0];
+      double s1 = e1 + c1[k][0] * e2 + c1[k][1] * e3;
+      double s2 = e2 + c2[k] * e3;
+      b[k] = 240.0 * s1 * s1 + 260.0 * s2 * s2 + 781.0 / 3.0 * e3 * e3;
+    }
     return 4;
   }
   return 0;

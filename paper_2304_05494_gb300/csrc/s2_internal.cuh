@@ -1,0 +1,69 @@
+// Internal declarations shared by the translation units of libs2.so.
+// Not part of the public ABI (include/s2.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace s2 {
+
+// Ghost width of every padded field (WENO7 needs 4; central-6, WENO5 and
+// the 6th-order derivatives need 3).
+constexpr int GH = 4;
+constexpr int NV = 5;
+
+// Device-side scalars of one solver.
+struct Scal {
+  double dt;              // current time step
+  double t;               // simulated time
+  double force;           // body force of the last RHS evaluation
+  double dt_max_rate;     // last max spectral radius
+  unsigned long long wcount;  // flagged interfaces of the last RHS evaluation
+  int status;             // 0 or the first error code met
+  int pad;
+  double red[8];          // results of the last stats reduction
+};
+
+// Error bits written by kernels (mapped to S2_ENONFINITE on the host).
+constexpr int ERR_NONFINITE = 1;
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  int nx, ny, nz;
+  int px, py, pz;          // padded extents (x pitch rounded up)
+  long long sy, sz;        // padded strides
+  long long off0;          // padded offset of interior point (0,0,0)
+  long long n;             // nx*ny*nz
+  double dx, dz, idx, idz;  // spacings and their inverses
+  double ax[4], az[4];     // a_l/dx, a_l/dz (first derivative, l = 1..3)
+  double bx[4], bz[4];     // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..3)
+  double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
+  double thr;              // sensor threshold
+  double cfl;
+  double vol_inv;          // 1 / sum(dV) / (dx dz) for the forcing
+  int viscous, wall_y, weno, force;
+  // state and registers (interior layout [v][k][j][i])
+  double *w, *fl, *fln;
+  // primitives with ghosts
+  double *rho, *u, *v, *ww, *T, *p, *H, *c;
+  // auxiliary fields
+  double *mu;              // interior
+  double *g;               // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
+  double *div, *sens;      // padded
+  // metrics (length ny)
+  const double *eta_y, *ay, *by, *ry, *dvy;  // eta_y; a_l eta_y (3/j); b_l eta_y^2 (4/j); eta_yy/eta_y; 1/eta_y
+  Scal *scal;
+  double *part;            // reduction partials
+  unsigned char *flagrec[3];  // optional per-interface flag record
+};
+
+__host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
+  return d.off0 + (long long)k * d.sz + (long long)j * d.sy + i;
+}
+
+// Launch helpers (defined in the kernel translation units).
+cudaError_t launch_flux(const Dev &d, int dir, int accumulate, int record, cudaStream_t st);
+cudaError_t launch_grad(const Dev &d, cudaStream_t st);
+cudaError_t launch_visc(const Dev &d, cudaStream_t st);
+cudaError_t flux_set_attributes();
+
+}  // namespace s2

@@ -105,18 +105,23 @@ def tanh_beta_for(ny: int, dy_wall: float) -> float:
     return 0.5 * (lo + hi)
 
 
-def _smooth_noise(rng, shape_xyz, kmax_xz: int, kmax_y: int, X, Y, Z, lx, lz):
-    """Sum of random-amplitude, random-phase Fourier modes, max-normalised."""
-    g = np.zeros(shape_xyz)
+def _smooth_noise(rng, kmax_xz: int, kmax_y: int, x, y, z, lx, lz):
+    """Sum of random-amplitude, random-phase separable Fourier modes
+    cos(kx x + a) sin(ky pi (y+1)/2 + b) cos(kz z + c), max-normalised;
+    returned with shape (nz, ny, nx)."""
+    cx, sy, cz, amp = [], [], [], []
     for kx in range(0, kmax_xz + 1):
         for kz in range(0, kmax_xz + 1):
             if kx == 0 and kz == 0:
                 continue
             for ky in range(1, kmax_y + 1):
-                a = rng.normal()
+                amp.append(rng.normal())
                 ph = rng.uniform(0, 2 * np.pi, size=3)
-                g += a * (np.cos(2 * np.pi * kx * X / lx + ph[0]) * np.cos(2 * np.pi * kz * Z / lz + ph[1])
-                          * np.sin(0.5 * np.pi * ky * (Y + 1.0) + ph[2]))
+                cx.append(np.cos(2 * np.pi * kx * x / lx + ph[0]))
+                cz.append(np.cos(2 * np.pi * kz * z / lz + ph[1]))
+                sy.append(np.sin(0.5 * np.pi * ky * (y + 1.0) + ph[2]))
+    a = np.asarray(amp)[:, None] * np.asarray(cz)
+    g = np.einsum("mk,mj,mi->kji", a, np.asarray(sy), np.asarray(cx), optimize=True)
     return g / np.max(np.abs(g))
 
 
@@ -135,12 +140,11 @@ def channel(nx: int = 256, ny: int = 128, nz: int = 128, mach_b: float = 1.5, re
     yn = tanh_nodes(ny, beta)
     x = np.arange(nx) * (lx / nx)
     z = np.arange(nz) * (lz / nz)
-    Z, Y, X = np.meshgrid(z, yn, x, indexing="ij")
     rng = np.random.default_rng(seed)
-    damp = 1.0 - Y * Y
-    u = 1.5 * damp + amp * damp * _smooth_noise(rng, X.shape, kmax_xz, kmax_y, X, Y, Z, lx, lz)
-    v = amp * damp * _smooth_noise(rng, X.shape, kmax_xz, kmax_y, X, Y, Z, lx, lz)
-    w = amp * damp * _smooth_noise(rng, X.shape, kmax_xz, kmax_y, X, Y, Z, lx, lz)
+    damp = (1.0 - yn * yn)[None, :, None]
+    u = 1.5 * damp + amp * damp * _smooth_noise(rng, kmax_xz, kmax_y, x, yn, z, lx, lz)
+    v = amp * damp * _smooth_noise(rng, kmax_xz, kmax_y, x, yn, z, lx, lz)
+    w = amp * damp * _smooth_noise(rng, kmax_xz, kmax_y, x, yn, z, lx, lz)
     rho = np.ones_like(u)
     T = np.ones_like(u)
     w0 = conserved(rho, u, v, w, T, 1.4, mach_b)
