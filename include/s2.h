@@ -167,7 +167,8 @@ int s2_stats(s2_solver *s, s2_stats_t *out);
  * or device pointer per where).  Synchronises.  The state is unchanged. */
 int s2_rhs(s2_solver *s, double *rhs, int where);
 
-/* Diagnostics: per-interface WENO flags of the last s2_rhs call, as bytes
+/* Diagnostics: per-interface WENO flags of the last RHS evaluation (the
+ * last stage of s2_step, or s2_rhs), as bytes
  * 0/1, host pointers: fx (nz, ny, nx+1), fy (nz, ny+1, nx), fz (nz+1, ny,
  * nx); slot p along the direction is the interface between points p-1 and
  * p.  Any pointer may be NULL. */
@@ -185,7 +186,9 @@ int s2_get_flags(s2_solver *s, unsigned char *fx, unsigned char *fy, unsigned ch
 #define S2_PROF_VISC 8      /* visflx */
 #define S2_PROF_FORCE 9     /* force_rhs_1 (two kernels) */
 #define S2_PROF_UPDATE 10   /* RK3 update */
-#define S2_PROF_KINDS 11
+#define S2_PROF_WENO 11     /* WENO flux corrections at flagged interfaces (3 kernels) */
+#define S2_PROF_APPLY 12    /* adding the WENO corrections (inviscid runs; fused into visc otherwise) */
+#define S2_PROF_KINDS 13
 
 /* Advance n steps launching every kernel directly (no graph) with CUDA
  * events around each class on the solver's stream; ms[k] receives the

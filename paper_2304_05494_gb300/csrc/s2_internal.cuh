@@ -18,6 +18,7 @@ struct Scal {
   double force;           // body force of the last RHS evaluation
   double dt_max_rate;     // last max spectral radius
   unsigned long long wcount;  // flagged interfaces of the last RHS evaluation
+  unsigned int nlist[4];  // per-direction lengths of the flagged-interface lists
   int status;             // 0 or the first error code met
   int pad;
   double red[8];          // results of the last stats reduction
@@ -37,6 +38,8 @@ struct Dev {
   double ax[4], az[4];     // a_l/dx, a_l/dz (first derivative, l = 1..3)
   double bx[4], bz[4];     // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..3)
   double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
+  double gR;               // gamma R (c^2 = gamma R T)
+  int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
   double thr;              // sensor threshold
   double cfl;
   double vol_inv;          // 1 / sum(dV) / (dx dz) for the forcing
@@ -44,7 +47,7 @@ struct Dev {
   // state and registers (interior layout [v][k][j][i])
   double *w, *fl, *fln;
   // primitives with ghosts
-  double *rho, *u, *v, *ww, *T, *p, *H, *c;
+  double *rho, *u, *v, *ww, *T, *p, *H;
   // auxiliary fields
   double *mu;              // interior
   double *g;               // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
@@ -53,17 +56,33 @@ struct Dev {
   const double *eta_y, *ay, *by, *ry, *dvy;  // eta_y; a_l eta_y (3/j); b_l eta_y^2 (4/j); eta_yy/eta_y; 1/eta_y
   Scal *scal;
   double *part;            // reduction partials
-  unsigned char *flagrec[3];  // optional per-interface flag record
+  // hybrid scheme, per direction: interface flags (n_d + 1 slots per
+  // pencil), the compacted list of flagged slots and F_weno - F_central at
+  // every listed slot (5 values, slot-major per component)
+  unsigned char *flag[3];
+  unsigned int *wlist[3];
+  double *dF[3];
+  long long nslot[3];
 };
 
 __host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
   return d.off0 + (long long)k * d.sz + (long long)j * d.sy + i;
 }
 
+// Slot of the interface between points s and s+1 (s = -1 .. n_d - 1) of
+// the pencil through (i, j, k) along direction dir: n_d + 1 slots per pencil.
+__host__ __device__ inline long long islot(const Dev &d, int dir, int s, int i, int j, int k) {
+  if (dir == 0) return ((long long)k * d.ny + j) * (d.nx + 1) + (s + 1);
+  if (dir == 1) return ((long long)k * (d.ny + 1) + (s + 1)) * d.nx + i;
+  return ((long long)(s + 1) * d.ny + j) * d.nx + i;
+}
+
 // Launch helpers (defined in the kernel translation units).
-cudaError_t launch_flux(const Dev &d, int dir, int accumulate, int record, cudaStream_t st);
+cudaError_t launch_flux(const Dev &d, int dir, int accumulate, cudaStream_t st);
+cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st);
 cudaError_t launch_grad(const Dev &d, cudaStream_t st);
 cudaError_t launch_visc(const Dev &d, cudaStream_t st);
+cudaError_t launch_apply(const Dev &d, cudaStream_t st);
 cudaError_t flux_set_attributes();
 
 }  // namespace s2

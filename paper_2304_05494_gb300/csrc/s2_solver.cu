@@ -115,9 +115,39 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
 }
 
 // ------------------------------------------------------------- primitives
+// Integer power by repeated squaring (e >= 0).
+__device__ __forceinline__ double ipow(double x, int e) {
+  double r = 1.0;
+  while (e) {
+    if (e & 1) r *= x;
+    x *= x;
+    e >>= 1;
+  }
+  return r;
+}
+
+// mu = (T/T_ref)^omega / Re.  For omega = p/q with small p >= 0, q (0.76 =
+// 19/25) the root y of y^q = x^p is found from a single-precision seed by
+// one Halley step, y <- y ((q-1) y^q + (q+1) a) / ((q+1) y^q + (q-1) a),
+// a = x^p, whose cubic convergence takes the ~1e-7 seed to double
+// precision; otherwise the library pow.
+__device__ __forceinline__ double viscosity(const Dev &d, double T) {
+  double x = T * d.inv_t_ref;
+  double y;
+  if (d.mu_q > 0) {
+    y = (double)powf((float)x, (float)d.visc_exp);
+    double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
+    double q = (double)d.mu_q;
+    y = y * ((q - 1.0) * yq + (q + 1.0) * a) / ((q + 1.0) * yq + (q - 1.0) * a);
+  } else {
+    y = pow(x, d.visc_exp);
+  }
+  return y / d.re;
+}
+
 // rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v, p = rho R T,
-// H = c_p T + |u|^2/2, c = sqrt(gamma R T), mu = (T/T_ref)^omega/Re.
-// With want_dt, also the CFL spectral radius max into part[block].
+// H = c_p T + |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the
+// CFL spectral radius max into part[block] (c = sqrt(gamma R T)).
 __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   double sr = 0.0;
@@ -139,17 +169,16 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
     d.T[p] = T;
     d.p[p] = pr;
     d.H[p] = d.cp * T + 0.5 * q2;
-    double cs = sqrt(d.gamma * d.R * T);
-    d.c[p] = cs;
     double mu = 0.0;
     if (d.viscous) {
-      mu = pow(T * d.inv_t_ref, d.visc_exp) / d.re;
+      mu = viscosity(d, T);
       d.mu[q] = mu;
     }
     if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
     if (want_dt) {
       double ey = d.eta_y[j];
+      double cs = sqrt(d.gamma * d.R * T);
       sr = (fabs(u) + cs) / d.dx + (fabs(v) + cs) * ey + (fabs(ww) + cs) / d.dz;  // as compute_dt
       if (d.viscous)
         sr += d.gamma * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
@@ -190,7 +219,7 @@ __global__ void k_dt_final(Dev d, int nparts) {
 // Face ghosts (GH deep) of the primitive fields.  x and z periodic; y
 // periodic or isothermal no-slip wall mirrored about the face between the
 // outermost node and its ghost: u -> -u, T -> 2 T_w - T, p -> p,
-// rho = p/(R T), H and c from T and |u|.
+// rho = p/(R T), H from T and |u|.
 __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
   long long nxf = 2LL * GH * d.ny * d.nz, nyf = 2LL * GH * d.nx * d.nz, nzf = 2LL * GH * d.nx * d.ny;
   long long t = (long long)blockIdx.x * NT + threadIdx.x;
@@ -237,7 +266,6 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
     d.T[dp] = d.T[sp];
     d.p[dp] = d.p[sp];
     d.H[dp] = d.H[sp];
-    d.c[dp] = d.c[sp];
   } else {
     double u = -d.u[sp], v = -d.v[sp], ww = -d.ww[sp];
     double T = 2.0 * d.t_wall - d.T[sp];
@@ -249,12 +277,7 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
     d.p[dp] = pr;
     d.rho[dp] = pr / (d.R * T);
     d.H[dp] = d.cp * T + 0.5 * (u * u + v * v + ww * ww);
-    if (!(T > 0.0)) {
-      atomicOr(&d.scal->status, ERR_NONFINITE);
-      d.c[dp] = 0.0;
-    } else {
-      d.c[dp] = sqrt(d.gamma * d.R * T);
-    }
+    if (!(T > 0.0)) atomicOr(&d.scal->status, ERR_NONFINITE);
   }
 }
 
@@ -504,7 +527,7 @@ cudaError_t run(Trace *tr, cudaStream_t st, int kind, int nkernels, F f) {
 }
 
 // One RHS evaluation (all terms up to the forcing reduction).
-cudaError_t enqueue_rhs(s2_solver *s, int want_dt, int record, Trace *tr) {
+cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
   const Dev &d = s->d;
   cudaStream_t st = s->stream;
   cudaError_t e;
@@ -538,14 +561,28 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, int record, Trace *tr) {
     if (e != cudaSuccess) return e;
   }
   if (d.weno) {
-    if ((e = cudaMemsetAsync(&d.scal->wcount, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    // wcount and the three list lengths are adjacent
+    if ((e = cudaMemsetAsync(&d.scal->wcount, 0, sizeof(unsigned long long) + 4 * sizeof(unsigned), st)) !=
+        cudaSuccess)
+      return e;
   }
   for (int dir = 0; dir < 3; ++dir) {
-    e = run(tr, st, S2_PROF_FLUX_X + dir, 1, [&] { return launch_flux(d, dir, dir > 0, record, st); });
+    e = run(tr, st, S2_PROF_FLUX_X + dir, 1, [&] { return launch_flux(d, dir, dir > 0, st); });
+    if (e != cudaSuccess) return e;
+  }
+  if (d.weno) {
+    e = run(tr, st, S2_PROF_WENO, 3, [&] {
+      cudaError_t r = cudaSuccess;
+      for (int dir = 0; dir < 3 && r == cudaSuccess; ++dir) r = launch_weno(d, dir, st);
+      return r;
+    });
     if (e != cudaSuccess) return e;
   }
   if (d.viscous) {
     e = run(tr, st, S2_PROF_VISC, 1, [&] { return launch_visc(d, st); });
+    if (e != cudaSuccess) return e;
+  } else if (d.weno) {
+    e = run(tr, st, S2_PROF_APPLY, 1, [&] { return launch_apply(d, st); });
     if (e != cudaSuccess) return e;
   }
   if (d.force) {
@@ -564,7 +601,7 @@ cudaError_t enqueue_step(s2_solver *s, int want_dt, Trace *tr) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
   cudaError_t e;
   for (int st = 0; st < 3; ++st) {
-    if ((e = enqueue_rhs(s, st == 0 ? want_dt : 0, 0, tr)) != cudaSuccess) return e;
+    if ((e = enqueue_rhs(s, st == 0 ? want_dt : 0, tr)) != cudaSuccess) return e;
     e = run(tr, s->stream, S2_PROF_UPDATE, 1, [&] {
       k_update<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
       return cudaGetLastError();
@@ -660,6 +697,9 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   if (n > (1LL << 40)) return S2_EINVAL;
+  // interface slots of a direction are listed as 32-bit indices
+  if (scheme->weno_order && (long long)(grid->nx + 1) * (grid->ny + 1) * (long long)(grid->nz + 1) > 0xffffffffLL)
+    return S2_EINVAL;
   if (metrics && metrics->y) {
     for (int j = 1; j < grid->ny; ++j)
       if (!(metrics->y[j] > metrics->y[j - 1])) return S2_EINVAL;
@@ -735,6 +775,19 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   }
   d.gamma = gas->gamma;
   d.R = 1.0 / (gas->gamma * gas->mach_ref * gas->mach_ref);
+  d.gR = gas->gamma * d.R;
+  // viscosity exponent as a ratio of small integers when it is one
+  d.mu_p = 0;
+  d.mu_q = 0;
+  for (int q = 1; q <= 64 && gas->visc_exp >= 0.0; ++q) {
+    double pq = gas->visc_exp * q;
+    double r = floor(pq + 0.5);
+    if (fabs(pq - r) <= 1e-12 * q && r <= 64.0) {
+      d.mu_p = (int)r;
+      d.mu_q = q;
+      break;
+    }
+  }
   d.cv = d.R / (gas->gamma - 1.0);
   d.icv = 1.0 / d.cv;
   d.cp = gas->gamma * d.cv;
@@ -763,7 +816,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.fl = A(NV * nn);
   d.fln = A(NV * nn);
   d.rho = A(np); d.u = A(np); d.v = A(np); d.ww = A(np);
-  d.T = A(np); d.p = A(np); d.H = A(np); d.c = A(np);
+  d.T = A(np); d.p = A(np); d.H = A(np);
   d.div = A(np); d.sens = A(np);
   d.mu = A(nn);
   d.g = A(9 * nn);
@@ -777,8 +830,12 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   s->flag_bytes[1] = (size_t)grid->nz * (grid->ny + 1) * grid->nx;
   s->flag_bytes[2] = (size_t)(grid->nz + 1) * grid->ny * grid->nx;
   for (int a = 0; a < 3; ++a) {
-    d.flagrec[a] = (unsigned char *)dalloc(s, s->flag_bytes[a]);
-    if (!d.flagrec[a]) ok = false;
+    d.nslot[a] = (long long)s->flag_bytes[a];
+    d.flag[a] = (unsigned char *)dalloc(s, s->flag_bytes[a]);
+    size_t nl = scheme->weno_order ? s->flag_bytes[a] : 1;
+    d.wlist[a] = (unsigned *)dalloc(s, nl * sizeof(unsigned));
+    d.dF[a] = (double *)dalloc(s, NV * nl * sizeof(double));
+    if (!d.flag[a] || !d.wlist[a] || !d.dF[a]) ok = false;
   }
   if (!ok) {
     release(s);
@@ -792,7 +849,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.dvy = dvy;
 
   cudaError_t e = cudaSuccess;
-  double *pads[] = {d.rho, d.u, d.v, d.ww, d.T, d.p, d.H, d.c, d.div, d.sens};
+  double *pads[] = {d.rho, d.u, d.v, d.ww, d.T, d.p, d.H, d.div, d.sens};
   for (double *p : pads)
     if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, np * sizeof(double), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.w, 0, NV * nn * sizeof(double), s->stream);
@@ -800,7 +857,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (e == cudaSuccess) e = cudaMemsetAsync(d.fln, 0, NV * nn * sizeof(double), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.scal, 0, sizeof(Scal), s->stream);
   for (int a = 0; a < 3 && e == cudaSuccess; ++a)
-    e = cudaMemsetAsync(d.flagrec[a], 0, s->flag_bytes[a], s->stream);
+    e = cudaMemsetAsync(d.flag[a], 0, s->flag_bytes[a], s->stream);
   // y nodes -> device, metric kernel
   std::vector<double> yn(grid->ny);
   for (int j = 0; j < grid->ny; ++j)
@@ -911,7 +968,7 @@ int s2_set_clock(s2_solver *s, double t, long long step, double dt) {
 int s2_rhs(s2_solver *s, double *rhs, int where) {
   if (!s || !rhs || (where != S2_HOST && where != S2_DEVICE)) return S2_EINVAL;
   DeviceGuard guard(s->device);
-  cudaError_t e = enqueue_rhs(s, 0, 1, nullptr);
+  cudaError_t e = enqueue_rhs(s, 0, nullptr);
   if (e != cudaSuccess) return S2_ECUDA;
   unsigned nb = (unsigned)((s->d.n + NT - 1) / NT);
   size_t bytes = NV * (size_t)s->d.n * sizeof(double);
@@ -934,7 +991,7 @@ int s2_get_flags(s2_solver *s, unsigned char *fx, unsigned char *fy, unsigned ch
   unsigned char *o[3] = {fx, fy, fz};
   for (int a = 0; a < 3; ++a)
     if (o[a] &&
-        cudaMemcpyAsync(o[a], s->d.flagrec[a], s->flag_bytes[a], cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+        cudaMemcpyAsync(o[a], s->d.flag[a], s->flag_bytes[a], cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
       return S2_ECUDA;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
   return S2_OK;
@@ -997,8 +1054,8 @@ int s2_profile(s2_solver *s, int n, double *ms, long long *launches) {
 }
 
 const char *s2_profile_name(int kind) {
-  static const char *names[S2_PROF_KINDS] = {"prims", "dt", "ghost", "grad", "ghost_aux", "flux_x",
-                                             "flux_y", "flux_z", "visc", "force", "update"};
+  static const char *names[S2_PROF_KINDS] = {"prims", "dt", "ghost", "grad", "ghost_aux", "flux_x", "flux_y",
+                                             "flux_z", "visc", "force", "update", "weno", "apply"};
   return (kind >= 0 && kind < S2_PROF_KINDS) ? names[kind] : nullptr;
 }
 

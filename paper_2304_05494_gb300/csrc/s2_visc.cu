@@ -14,7 +14,10 @@
 //               - (2/3) theta d_a mu
 //   energy:     u_a momentum_a + tau_ab d_b u_a + k lap T + grad k . grad T
 // with grad mu = (omega mu / T) grad T (power law), k = mu c_p / Pr,
-// d2/dy2 = eta_y^2 d2/deta2 + eta_yy d/deta.
+// d2/dy2 = eta_y^2 d2/deta2 + eta_yy d/deta.  The same pass adds the WENO
+// corrections of the hybrid convective flux (k_apply does it alone for
+// inviscid runs): per direction -scale (dF_{i+1/2} - dF_{i-1/2}) over the
+// flagged interfaces, in a fixed order.
 #include "s2_internal.cuh"
 
 namespace s2 {
@@ -46,6 +49,40 @@ __device__ __forceinline__ double d2(const double *__restrict__ f, long long p, 
          c.c2 * (__ldg(f + p + 2 * s) + __ldg(f + p - 2 * s)) + c.c3 * (__ldg(f + p + 3 * s) + __ldg(f + p - 3 * s));
 }
 
+// Hybrid-scheme correction of point (i, j, k): R -= scale_d (dF_hi - dF_lo)
+// summed over the directions whose interfaces around the point are flagged.
+__device__ __forceinline__ void weno_correction(const Dev &d, int i, int j, int k, double *R) {
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    int pos = dir == 0 ? i : (dir == 1 ? j : k);
+    long long lo = islot(d, dir, pos - 1, i, j, k), hi = islot(d, dir, pos, i, j, k);
+    bool fl = d.flag[dir][lo], fh = d.flag[dir][hi];
+    if (fl || fh) {
+      double scale = dir == 0 ? d.idx : (dir == 1 ? __ldg(d.eta_y + j) : d.idz);
+      const long long ns = d.nslot[dir];
+      const double *dF = d.dF[dir];
+#pragma unroll
+      for (int f = 0; f < NV; ++f) {
+        double c = (fh ? dF[f * ns + hi] : 0.0) - (fl ? dF[f * ns + lo] : 0.0);
+        R[f] = fma(-scale, c, R[f]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_apply(Dev d) {
+  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  if (q >= d.n) return;
+  int i, j, k;
+  point_of(d, q, i, j, k);
+  double R[NV];
+#pragma unroll
+  for (int f = 0; f < NV; ++f) R[f] = d.fl[f * d.n + q];
+  weno_correction(d, i, j, k, R);
+#pragma unroll
+  for (int f = 0; f < NV; ++f) d.fl[f * d.n + q] = R[f];
+}
+
 __global__ void __launch_bounds__(NT) k_grad(Dev d) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   if (q >= d.n) return;
@@ -67,11 +104,13 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) d.g[(3 * a + b) * d.n + q] = g[a][b];
   double th = g[0][0] + g[1][1] + g[2][2];
-  double o1 = g[2][1] - g[1][2], o2 = g[0][2] - g[2][0], o3 = g[1][0] - g[0][1];
-  double om2 = o1 * o1 + o2 * o2 + o3 * o3;
-  double sv = -th / sqrt(th * th + om2 + 1.0);
   d.div[p] = th;
-  d.sens[p] = sv > 0.0 ? sv : 0.0;
+  if (d.weno) {
+    double o1 = g[2][1] - g[1][2], o2 = g[0][2] - g[2][0], o3 = g[1][0] - g[0][1];
+    double om2 = o1 * o1 + o2 * o2 + o3 * o3;
+    double sv = -th / sqrt(th * th + om2 + 1.0);
+    d.sens[p] = sv > 0.0 ? sv : 0.0;
+  }
 }
 
 __global__ void __launch_bounds__(NT) k_visc(Dev d) {
@@ -132,9 +171,15 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   en += mu * tg;
   en += kc * lapT;
   en += d.cp_over_pr * (gmu[0] * gT[0] + gmu[1] * gT[1] + gmu[2] * gT[2]);
+  double R[NV];
+  R[0] = d.fl[q];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) d.fl[(1 + a) * d.n + q] += mom[a];
-  d.fl[4 * d.n + q] += en;
+  for (int a = 0; a < 3; ++a) R[1 + a] = d.fl[(1 + a) * d.n + q] + mom[a];
+  R[4] = d.fl[4 * d.n + q] + en;
+  if (d.weno) weno_correction(d, i, j, k, R);
+  if (d.weno) d.fl[q] = R[0];
+#pragma unroll
+  for (int f = 1; f < NV; ++f) d.fl[f * d.n + q] = R[f];
 }
 
 }  // namespace
@@ -142,6 +187,12 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
 cudaError_t launch_grad(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
   k_grad<<<nb, NT, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Dev &d, cudaStream_t st) {
+  unsigned nb = (unsigned)((d.n + NT - 1) / NT);
+  k_apply<<<nb, NT, 0, st>>>(d);
   return cudaGetLastError();
 }
 

@@ -71,7 +71,7 @@ class s2_stats_t(C.Structure):
                 ("launches", C.c_longlong), ("status", C.c_int)]
 
 
-S2_PROF_KINDS = 11
+S2_PROF_KINDS = 13
 
 
 def _load():
