@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/s2.h"
+
 namespace s2 {
 
 // Ghost width of every padded field (WENO7 needs 4; central-6, WENO5 and
@@ -69,6 +71,47 @@ __host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
   return d.off0 + (long long)k * d.sz + (long long)j * d.sy + i;
 }
 
+// Integer power by repeated squaring (e >= 0).
+__device__ __forceinline__ double ipow(double x, int e) {
+  double r = 1.0;
+  while (e) {
+    if (e & 1) r *= x;
+    x *= x;
+    e >>= 1;
+  }
+  return r;
+}
+
+// mu = (T/T_ref)^omega / Re.  For omega = p/q with small p >= 0, q (0.76 =
+// 19/25) the root y of y^q = x^p is found from a single-precision seed by
+// one Halley step, y <- y ((q-1) y^q + (q+1) a) / ((q+1) y^q + (q-1) a),
+// a = x^p, whose cubic convergence takes the ~1e-7 seed to double
+// precision; otherwise the library pow.
+__device__ __forceinline__ double viscosity(const Dev &d, double T) {
+  double x = T * d.inv_t_ref;
+  double y;
+  if (d.mu_q > 0) {
+    y = (double)powf((float)x, (float)d.visc_exp);
+    double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
+    double q = (double)d.mu_q;
+    y = y * ((q - 1.0) * yq + (q + 1.0) * a) / ((q + 1.0) * yq + (q - 1.0) * a);
+  } else {
+    y = pow(x, d.visc_exp);
+  }
+  return y / d.re;
+}
+
+// CFL spectral radius of one point (compute_dt of Table 2):
+// (|u|+c)/dx + (|v|+c) eta_y + (|w|+c)/dz, plus for viscous runs
+// gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2), c = sqrt(gamma R T).
+__device__ __forceinline__ double spectral_radius(const Dev &d, double rho, double u, double v, double ww, double T,
+                                                  double mu, double ey) {
+  double cs = sqrt(d.gamma * d.R * T);
+  double sr = (fabs(u) + cs) / d.dx + (fabs(v) + cs) * ey + (fabs(ww) + cs) / d.dz;
+  if (d.viscous) sr += d.gamma * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
+  return sr;
+}
+
 // Slot of the interface between points s and s+1 (s = -1 .. n_d - 1) of
 // the pencil through (i, j, k) along direction dir: n_d + 1 slots per pencil.
 __host__ __device__ inline long long islot(const Dev &d, int dir, int s, int i, int j, int k) {
@@ -84,5 +127,8 @@ cudaError_t launch_grad(const Dev &d, cudaStream_t st);
 cudaError_t launch_visc(const Dev &d, cudaStream_t st);
 cudaError_t launch_apply(const Dev &d, cudaStream_t st);
 cudaError_t flux_set_attributes();
+
+// Gas constants (R, c_v, c_p, viscosity law) of a Dev from s2_gas.
+void set_gas(Dev &d, const s2_gas *gas);
 
 }  // namespace s2

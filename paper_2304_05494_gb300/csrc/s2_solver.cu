@@ -115,36 +115,6 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
 }
 
 // ------------------------------------------------------------- primitives
-// Integer power by repeated squaring (e >= 0).
-__device__ __forceinline__ double ipow(double x, int e) {
-  double r = 1.0;
-  while (e) {
-    if (e & 1) r *= x;
-    x *= x;
-    e >>= 1;
-  }
-  return r;
-}
-
-// mu = (T/T_ref)^omega / Re.  For omega = p/q with small p >= 0, q (0.76 =
-// 19/25) the root y of y^q = x^p is found from a single-precision seed by
-// one Halley step, y <- y ((q-1) y^q + (q+1) a) / ((q+1) y^q + (q-1) a),
-// a = x^p, whose cubic convergence takes the ~1e-7 seed to double
-// precision; otherwise the library pow.
-__device__ __forceinline__ double viscosity(const Dev &d, double T) {
-  double x = T * d.inv_t_ref;
-  double y;
-  if (d.mu_q > 0) {
-    y = (double)powf((float)x, (float)d.visc_exp);
-    double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
-    double q = (double)d.mu_q;
-    y = y * ((q - 1.0) * yq + (q + 1.0) * a) / ((q + 1.0) * yq + (q - 1.0) * a);
-  } else {
-    y = pow(x, d.visc_exp);
-  }
-  return y / d.re;
-}
-
 // rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v, p = rho R T,
 // H = c_p T + |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the
 // CFL spectral radius max into part[block] (c = sqrt(gamma R T)).
@@ -176,13 +146,7 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
     }
     if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
-    if (want_dt) {
-      double ey = d.eta_y[j];
-      double cs = sqrt(d.gamma * d.R * T);
-      sr = (fabs(u) + cs) / d.dx + (fabs(v) + cs) * ey + (fabs(ww) + cs) / d.dz;  // as compute_dt
-      if (d.viscous)
-        sr += d.gamma * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
-    }
+    if (want_dt) sr = spectral_radius(d, rho, u, v, ww, T, mu, d.eta_y[j]);
   }
   if (want_dt) {
     __shared__ double red[NT / 32];
@@ -666,6 +630,34 @@ struct DeviceGuard {
 
 }  // namespace
 
+// Gas constants of a Dev from the public description (reference units).
+void s2::set_gas(Dev &d, const s2_gas *gas) {
+  d.gamma = gas->gamma;
+  d.R = 1.0 / (gas->gamma * gas->mach_ref * gas->mach_ref);
+  d.gR = gas->gamma * d.R;
+  // viscosity exponent as a ratio of small integers when it is one
+  d.mu_p = 0;
+  d.mu_q = 0;
+  for (int q = 1; q <= 64 && gas->visc_exp >= 0.0; ++q) {
+    double pq = gas->visc_exp * q;
+    double r = floor(pq + 0.5);
+    if (fabs(pq - r) <= 1e-12 * q && r <= 64.0) {
+      d.mu_p = (int)r;
+      d.mu_q = q;
+      break;
+    }
+  }
+  d.cv = d.R / (gas->gamma - 1.0);
+  d.icv = 1.0 / d.cv;
+  d.cp = gas->gamma * d.cv;
+  d.prandtl = gas->prandtl;
+  d.re = gas->re_ref;
+  d.visc_exp = gas->visc_exp;
+  d.inv_t_ref = 1.0 / gas->t_ref;
+  d.cp_over_pr = d.cp / gas->prandtl;
+  d.viscous = gas->re_ref > 0.0;
+}
+
 extern "C" {
 
 const char *s2_strerror(int code) {
@@ -773,33 +765,10 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     d.bx[l] = B2[l] / (d.dx * d.dx);
     d.bz[l] = B2[l] / (d.dz * d.dz);
   }
-  d.gamma = gas->gamma;
-  d.R = 1.0 / (gas->gamma * gas->mach_ref * gas->mach_ref);
-  d.gR = gas->gamma * d.R;
-  // viscosity exponent as a ratio of small integers when it is one
-  d.mu_p = 0;
-  d.mu_q = 0;
-  for (int q = 1; q <= 64 && gas->visc_exp >= 0.0; ++q) {
-    double pq = gas->visc_exp * q;
-    double r = floor(pq + 0.5);
-    if (fabs(pq - r) <= 1e-12 * q && r <= 64.0) {
-      d.mu_p = (int)r;
-      d.mu_q = q;
-      break;
-    }
-  }
-  d.cv = d.R / (gas->gamma - 1.0);
-  d.icv = 1.0 / d.cv;
-  d.cp = gas->gamma * d.cv;
-  d.prandtl = gas->prandtl;
-  d.re = gas->re_ref;
-  d.visc_exp = gas->visc_exp;
-  d.inv_t_ref = 1.0 / gas->t_ref;
-  d.cp_over_pr = d.cp / gas->prandtl;
+  set_gas(d, gas);
   d.t_wall = bcs->t_wall;
   d.thr = scheme->sensor_threshold;
   d.cfl = scheme->cfl;
-  d.viscous = gas->re_ref > 0.0;
   d.wall_y = bcs->y == S2_BC_ISOTHERMAL_WALL;
   d.weno = scheme->weno_order;
   d.force = bcs->force_mass_flow ? 1 : 0;
