@@ -44,6 +44,7 @@ extern "C" {
 #define S2_ENONFINITE -4  /* non-positive density/temperature or NaN met */
 #define S2_ETIMEOUT -5    /* a bounded device wait gave up */
 #define S2_EBUSY -6       /* solver busy (reserved) */
+#define S2_ETOOBIG -7     /* larger than the fixed scratch of s2_cfl_dt_noalloc */
 
 #define S2_BC_PERIODIC 0
 #define S2_BC_ISOTHERMAL_WALL 1
@@ -202,6 +203,33 @@ const char *s2_profile_name(int kind);
 
 /* Release everything; NULL is accepted. */
 void s2_destroy(s2_solver *s);
+
+/* Allocation-free CFL time step.  The paper has no counterpart: this entry
+ * point serves callers that must not allocate device memory when they need
+ * a step size -- a serving loop whose memory is owned by a pooling
+ * allocator it does not control, code running while another framework
+ * holds the device's memory, or a latency-bound loop that cannot afford
+ * cudaMalloc's implicit synchronisation.  It returns the dt that s2_step
+ * computes from the same state (cfl / max over the points of the
+ * convective plus viscous spectral radius) without a solver object.
+ *
+ * w: device pointer, the state in the ABI layout (5*nx*ny*nz doubles).
+ * eta_y: device pointer to ny values of deta/dy, or NULL for uniform nodes
+ * (ny/ly).  dt: device pointer; one double is written.  stream: a
+ * cudaStream_t or NULL.  The call is asynchronous on that stream.
+ *
+ * Its only scratch is a fixed array of 65536 doubles (512 KiB) compiled
+ * into the library, present on every GPU that loads it until the process
+ * exits; nothing is allocated (no cudaMalloc, cudaFree or allocating
+ * library call).  Grids above 65536 * 4096 = 268,435,456 points return
+ * S2_ETOOBIG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and caches it;
+ * make that first call before any stream capture.  All calls on a device
+ * share the array and every call rewrites the entries it reads, so nothing
+ * needs clearing; calls that overlap on the GPU (different streams without
+ * ordering) race on it and must be serialised by the caller. */
+int s2_cfl_dt_noalloc(const s2_grid *grid, const s2_gas *gas, const double *w, const double *eta_y, double cfl,
+                      double *dt, void *stream);
 
 /* Static description of an error code. */
 const char *s2_strerror(int code);

@@ -669,6 +669,7 @@ const char *s2_strerror(int code) {
     case S2_ENONFINITE: return "non-positive density/temperature or non-finite value";
     case S2_ETIMEOUT: return "device wait timed out";
     case S2_EBUSY: return "solver busy";
+    case S2_ETOOBIG: return "grid larger than the fixed scratch of the allocation-free entry point";
   }
   return "unknown error";
 }

@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 S2_OK, S2_EINVAL, S2_ENOMEM, S2_ECUDA, S2_ENONFINITE, S2_ETIMEOUT, S2_EBUSY = 0, -1, -2, -3, -4, -5, -6
+S2_ETOOBIG = -7
 S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL = 0, 1
 S2_HOST, S2_DEVICE = 0, 1
 S2_FP64 = 0
@@ -98,6 +99,8 @@ def _load():
     lib.s2_profile.restype = C.c_int
     lib.s2_profile_name.argtypes = [C.c_int]
     lib.s2_profile_name.restype = C.c_char_p
+    lib.s2_cfl_dt_noalloc.argtypes = [C.POINTER(s2_grid), C.POINTER(s2_gas), P, P, C.c_double, P, P]
+    lib.s2_cfl_dt_noalloc.restype = C.c_int
     lib.s2_strerror.argtypes = [C.c_int]
     lib.s2_strerror.restype = C.c_char_p
     for f in ("s2_set_state", "s2_get_state", "s2_step", "s2_sync", "s2_set_clock", "s2_stats", "s2_rhs",
@@ -200,6 +203,13 @@ def s2_profile(h, n: int) -> dict:
     cnt = (C.c_longlong * S2_PROF_KINDS)()
     _check(_lib.s2_profile(h, int(n), ms, cnt), "s2_profile")
     return {s2_profile_name(k): (ms[k], cnt[k]) for k in range(S2_PROF_KINDS)}
+
+
+def s2_cfl_dt_noalloc(grid, gas, w, eta_y, cfl: float, dt, stream=None) -> int:
+    """Allocation-free CFL dt; w, eta_y (or None) and dt are CUDA tensors.
+    Returns the status code (no exception, so callers can test it)."""
+    return _lib.s2_cfl_dt_noalloc(C.byref(grid), C.byref(gas), w.data_ptr(),
+                                  eta_y.data_ptr() if eta_y is not None else None, cfl, dt.data_ptr(), stream)
 
 
 def s2_destroy(h) -> None:
