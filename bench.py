@@ -41,6 +41,18 @@ ALG_FLOPS = {"prims": 25, "grad": 92, "flux_x": 95, "flux_y": 95, "flux_z": 95, 
 WENO5_FLOPS = 2000
 # FP64 peak: 152 SMs x 2 DFMA/clk (4 flop) x 2070 MHz maximum SM clock.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+# Mixed path: algorithmic HBM bytes per interior point of one launch
+# (single-precision primitives and RHS, double-precision state).
+MIXED_BYTES = {"prims": 72, "grad": 56, "flux_x": 52, "flux_y": 72, "flux_z": 72, "visc": 100, "update": 144}
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def parse():
@@ -52,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -243,6 +256,51 @@ def our_arm(args):
                 "per_launch_ms": per_launch_ms,
                 "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1]}}
 
+    # mixed precision: same workload, single-precision flux arithmetic
+    mixed = None
+    if not args.no_mixed:
+        sm = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local, precision="mixed")
+        sm.set_state(case.w0)
+        sm.step(args.warmup)
+        sm.sync()
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sm.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_m = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms_m], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_m = float(t.item())
+        prof_m = sm.profile(args.profile_steps)
+        domm = max(((k, v) for k, v in prof_m.items() if k in MIXED_BYTES), key=lambda kv: kv[1][0])
+        mname, (mms, ml) = domm
+        per_launch = mms / max(ml, 1)
+        peak, src = hbm_peak_gbs()
+        ach = MIXED_BYTES[mname] * case.points / (per_launch * 1e-3) / 1e9
+        # error of the mixed path against the FP64 path after 10 steps from w0
+        sm.set_state(case.w0)
+        sm.set_clock(0.0, 0, 0.0)
+        sm.step(10)
+        wm = sm.get_state()
+        sm.close()
+        with s2.Solver.from_case(case, stream=stream.cuda_stream, device=local) as sd:
+            sd.set_state(case.w0)
+            sd.step(10)
+            wd = sd.get_state()
+        scale = np.max(np.abs(wd), axis=(1, 2, 3))
+        err = (np.max(np.abs(wm - wd), axis=(1, 2, 3)) / scale).tolist()
+        mixed = {"value": case.points * args.steps * world / (ms_m * 1e-3), "unit": UNIT,
+                 "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state",
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "traffic": None, "kernel": mname, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+                              "per_launch_ms": per_launch,
+                              "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_m.items() if v[1]}},
+                 "err_vs_fp64_after_10_steps": err}
+
     # end to end through the C ABI with host buffers: H2D of the step's
     # input state, one step, D2H of the result, every step
     pinned_in = torch.from_numpy(case.w0).pin_memory()
@@ -274,7 +332,7 @@ def our_arm(args):
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
-               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "mixed": mixed,
                "weno_frac": weno_frac, "state_finite": finite}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(case)

@@ -52,7 +52,9 @@ extern "C" {
 #define S2_HOST 0
 #define S2_DEVICE 1
 
-#define S2_FP64 0
+#define S2_FP64 0   /* all arithmetic and storage in double precision */
+#define S2_MIXED 1  /* single-precision primitives, flux, WENO and viscous arithmetic;
+                       double-precision state, RK accumulation and E -> T recovery */
 
 typedef struct s2_solver s2_solver; /* opaque; owned by the library */
 
@@ -90,7 +92,8 @@ typedef struct {
 
 /* Scheme.  central_order and visc_order: 6.  weno_order: 0 (central
  * everywhere), 5 or 7.  An interface is WENO iff the sensor's maximum over
- * its stencil exceeds sensor_threshold (strictly).  precision: S2_FP64.
+ * its stencil exceeds sensor_threshold (strictly).  precision: S2_FP64 or
+ * S2_MIXED (the sensor then decides in single precision).
  * dt: if cfl > 0 it is recomputed from the CFL condition (compute_dt of
  * Table 2) at every step whose counter is a multiple of dt_every and
  * frozen within a step; otherwise dt_fixed is used. */

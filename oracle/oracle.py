@@ -62,6 +62,8 @@ def lib():
         bp = C.POINTER(C.c_ubyte)
         _lib.or_rhs.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int, dp]
         _lib.or_rhs.restype = C.c_int
+        _lib.or_rhs_given_flags.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int]
+        _lib.or_rhs_given_flags.restype = C.c_int
         _lib.or_sensor.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
         _lib.or_sensor.restype = C.c_int
         _lib.or_dt.argtypes = [C.POINTER(_Cfg), dp, C.c_double]
@@ -164,6 +166,20 @@ def rhs(p: Problem, w: np.ndarray, terms: int = CONV | VISC | FORCE, flags: bool
         raise MemoryError("oracle rhs failed")
     if flags:
         return out, (fx, fy, fz)
+    return out
+
+
+def rhs_given_flags(p: Problem, w: np.ndarray, flags, terms: int = CONV | VISC | FORCE):
+    """R(w) with the interface flags (fx, fy, fz) imposed instead of decided
+    by the sensor (same layout as rhs(..., flags=True) returns)."""
+    w = _state(p, w)
+    out = np.zeros_like(w)
+    cfg = p.cfg()
+    fx, fy, fz = [np.ascontiguousarray(f, dtype=np.uint8) for f in flags]
+    assert fx.shape == (p.nz, p.ny, p.nx + 1) and fy.shape == (p.nz, p.ny + 1, p.nx)
+    assert fz.shape == (p.nz + 1, p.ny, p.nx)
+    if lib().or_rhs_given_flags(C.byref(cfg), _dp(w), _dp(out), _bp(fx), _bp(fy), _bp(fz), terms):
+        raise MemoryError("oracle rhs failed")
     return out
 
 

@@ -534,7 +534,9 @@ static void central_flux(const ws_t *s, int dir, int pos, int i, int j, int k, d
   F[1 + dir] += fp;
 }
 
-static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags) {
+/* flags: where the per-interface WENO flags are written, or (given != 0)
+ * read from: a caller-supplied decision replaces the sensor test. */
+static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags, int given) {
   int nx = s->nx, ny = s->ny, nz = s->nz, n = dir == 0 ? nx : (dir == 1 ? ny : nz);
   int r = (s->c->weno_order + 1) / 2;
   int na = dir == 0 ? ny : nx, nb = dir == 2 ? ny : nz; /* transverse extents */
@@ -548,18 +550,22 @@ static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags) {
       double *Fh = (double *)malloc(sizeof(double) * 5 * (size_t)(n + 1));
       for (int pos = -1; pos < n; ++pos) {
         int fl = 0;
-        if (s->c->weno_order > 0) {
-          double mx = 0.0;
-          for (int m = pos - r + 1; m <= pos + r; ++m) mx = fmax(mx, s->sens[at(s, dir, m, i, j, k)]);
-          fl = mx > s->c->threshold;
-        }
+        size_t slot = 0;
         if (flags) {
           /* per-direction interface flags, n+1 per pencil, interface pos+1/2 at slot pos+1 */
-          size_t slot;
           if (dir == 0) slot = ((size_t)k * ny + j) * (nx + 1) + (pos + 1);
           else if (dir == 1) slot = ((size_t)k * (ny + 1) + (pos + 1)) * nx + i;
           else slot = ((size_t)(pos + 1) * ny + j) * nx + i;
-          flags[slot] = (unsigned char)fl;
+        }
+        if (given) {
+          fl = s->c->weno_order > 0 && flags[slot];
+        } else {
+          if (s->c->weno_order > 0) {
+            double mx = 0.0;
+            for (int m = pos - r + 1; m <= pos + r; ++m) mx = fmax(mx, s->sens[at(s, dir, m, i, j, k)]);
+            fl = mx > s->c->threshold;
+          }
+          if (flags) flags[slot] = (unsigned char)fl;
         }
         if (fl) weno_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
         else central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
@@ -659,14 +665,14 @@ static double forcing(ws_t *s, double *rhs) {
  * forcing.  flags{x,y,z} (may be NULL) receive the per-interface WENO flags,
  * (n_dir + 1) per pencil. */
 static int rhs_ws(ws_t *s, const double *w, double *rhs, unsigned char *fx, unsigned char *fy,
-                  unsigned char *fz, int terms, double *force_out) {
+                  unsigned char *fz, int terms, double *force_out, int given) {
   memset(rhs, 0, sizeof(double) * NV * s->n);
   prims(s, w);
   sensor(s);
   if (terms & OR_CONV) {
-    convective(s, 0, rhs, fx);
-    convective(s, 1, rhs, fy);
-    convective(s, 2, rhs, fz);
+    convective(s, 0, rhs, fx, given);
+    convective(s, 1, rhs, fy, given);
+    convective(s, 2, rhs, fz, given);
   }
   if ((terms & OR_VISC) && s->viscous) viscous(s, rhs);
   double f = 0.0;
@@ -679,7 +685,20 @@ int or_rhs(const or_cfg *c, const double *w, double *rhs, unsigned char *fx, uns
            unsigned char *fz, int terms, double *force_out) {
   ws_t s;
   if (ws_init(&s, c)) { ws_free(&s); return -1; }
-  rhs_ws(&s, w, rhs, fx, fy, fz, terms, force_out);
+  rhs_ws(&s, w, rhs, fx, fy, fz, terms, force_out, 0);
+  ws_free(&s);
+  return 0;
+}
+
+/* R(w) with the interface WENO flags supplied by the caller (layout as
+ * or_rhs writes them) instead of decided by the sensor: isolates the
+ * arithmetic of another implementation from its flag decisions. */
+int or_rhs_given_flags(const or_cfg *c, const double *w, double *rhs, unsigned char *fx, unsigned char *fy,
+                       unsigned char *fz, int terms) {
+  if (!fx || !fy || !fz) return -1;
+  ws_t s;
+  if (ws_init(&s, c)) { ws_free(&s); return -1; }
+  rhs_ws(&s, w, rhs, fx, fy, fz, terms, NULL, 1);
   ws_free(&s);
   return 0;
 }
@@ -756,7 +775,7 @@ int or_step(const or_cfg *c, double *w, int nsteps, double cfl, double dt_fixed,
       dt = dt_fixed;
     }
     for (int st = 0; st < 3; ++st) {
-      rhs_ws(&s, w, R, NULL, NULL, NULL, OR_CONV | OR_VISC | OR_FORCE, NULL);
+      rhs_ws(&s, w, R, NULL, NULL, NULL, OR_CONV | OR_VISC | OR_FORCE, NULL, 0);
       for (size_t q = 0; q < tot; ++q) w[q] += dt * (RK_GAMMA[st] * R[q] + RK_RHO[st] * Rp[q]);
       double *t = Rp; Rp = R; R = t;
     }

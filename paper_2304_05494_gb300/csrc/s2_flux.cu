@@ -23,13 +23,18 @@
 //   here): F_weno - F_central at the interface.
 // The corrections are added per point, in a fixed order, by the viscous
 // kernel (or k_apply when inviscid): deterministic, no atomics on the RHS.
+// Every kernel is instantiated for R = double (FP64 path) and R = float
+// (arithmetic of the mixed path).
 #include "s2_internal.cuh"
 
 namespace s2 {
 namespace {
 
-// 6th-order central coefficients a_l (first derivative).
-__device__ __constant__ double kA[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
+// 6th-order central coefficients a_l (first derivative), l = 1..3.
+template <class R>
+__device__ __forceinline__ constexpr R ka(int l) {
+  return l == 1 ? R(3.0 / 4.0) : (l == 2 ? R(-3.0 / 20.0) : R(1.0 / 60.0));
+}
 
 template <int DIR>
 struct Tile;
@@ -49,7 +54,7 @@ struct Tile<2> {  // z: 32 along z, 8 columns (x)
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
-template <int DIR, int WR>
+template <int DIR, int WR, class R>
 __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
   constexpr int LE = L + 2 * GH;       // extended positions per pencil
@@ -57,9 +62,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int LT = L + 3;            // pair-flux positions a = -3 .. L-1
   constexpr int ST = LT * W;           // doubles per pair-flux slot
   constexpr int NFLD = WR > 0 ? NF : F_S;  // the sensor is staged only for WENO
-  extern __shared__ double smem[];
-  double *S = smem;                    // [NF][LE][W]
-  double *TP = smem + NF * SF;         // [3][5][LT][W]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *S = (R *)smem_raw;                // [NF][LE][W]
+  R *TP = S + NF * SF;                 // [3][5][LT][W]
+  const View<R> V = view<R>(d);
+  const Consts<R> &K = consts<R>(d);
 
   const int tid = threadIdx.x;
   const int n = DIR == 0 ? d.nx : (DIR == 1 ? d.ny : d.nz);
@@ -71,7 +78,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   const int nac = DIR == 0 ? d.ny : d.nx;   // extent across
   const int c0 = DIR == 0 ? y0 : x0;
 
-  const double *src[NF] = {d.rho, d.u, d.v, d.ww, d.H, d.p, d.sens};
+  const R *src[NF] = {V.rho, V.u, V.v, V.ww, V.H, V.p, V.sens};
 
   // ---- 1. stage the tile (positions s0-GH .. s0+L+GH-1) ----
   for (int idx = tid; idx < SF; idx += NTHREADS) {
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
       else g = pidx(d, x0 + cc, y0, s);
     }
 #pragma unroll
-    for (int f = 0; f < NFLD; ++f) S[f * SF + a * W + cc] = ok ? __ldg(src[f] + g) : 1.0;
+    for (int f = 0; f < NFLD; ++f) S[f * SF + a * W + cc] = ok ? __ldg(src[f] + g) : R(1);
   }
   __syncthreads();
 
@@ -95,17 +102,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   for (int idx = tid; idx < ST; idx += NTHREADS) {
     int a = idx / W, cc = idx % W;        // a in 0..LT-1 <-> position a-3
     int ae = a - 3 + GH;                  // extended index of the position
-    const double *Sr = S + F_RHO * SF, *Su = S + F_U * SF, *Sv = S + F_V * SF, *Sw = S + F_W * SF,
-                 *Sh = S + F_H * SF;
+    const R *Sr = S + F_RHO * SF, *Su = S + F_U * SF, *Sv = S + F_V * SF, *Sw = S + F_W * SF, *Sh = S + F_H * SF;
     int q0 = ae * W + cc;
-    double r0 = Sr[q0], u0 = Su[q0], v0 = Sv[q0], w0 = Sw[q0], h0 = Sh[q0];
+    R r0 = Sr[q0], u0 = Su[q0], v0 = Sv[q0], w0 = Sw[q0], h0 = Sh[q0];
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
       int q1 = q0 + l * W;
-      double su = u0 + Su[q1], sv = v0 + Sv[q1], sw = w0 + Sw[q1];
-      double sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
-      double m = (r0 + Sr[q1]) * sun;
-      double *T = TP + ((l - 1) * 5) * ST + idx;
+      R su = u0 + Su[q1], sv = v0 + Sv[q1], sw = w0 + Sw[q1];
+      R sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
+      R m = (r0 + Sr[q1]) * sun;
+      R *T = TP + ((l - 1) * 5) * ST + idx;
       T[0] = m;
       T[ST] = m * su;
       T[2 * ST] = m * sv;
@@ -119,8 +125,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   // pencil also the one before its first point (a = -1): every interface
   // slot 0..n of a pencil is owned exactly once.
   if constexpr (WR > 0) {
-    const double *Ss = S + F_S * SF;
-    const long long thr_bits = __double_as_longlong(d.thr);
+    const R *Ss = S + F_S * SF;
+    const auto thr_bits = order_bits(K.thr);
     constexpr int NI = (L + 1) * W;
     unsigned long long mycount = 0;
     for (int base = 0; base < NI; base += NTHREADS) {
@@ -134,13 +140,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
         if (own) {
           // the sensor is >= 0, so its IEEE bit patterns order like the
           // values: max and comparison run on the integer pipe
-          long long mx = 0;
+          decltype(order_bits(R(0))) mx = 0;
 #pragma unroll
           for (int m = -WR + 1; m <= WR; ++m) {
-            long long b = __double_as_longlong(Ss[(a + m + GH) * W + cc]);
+            auto b = order_bits(Ss[(a + m + GH) * W + cc]);
             mx = b > mx ? b : mx;
           }
-          flag = d.thr < 0.0 || mx > thr_bits;
+          flag = K.thr < R(0) || mx > thr_bits;
           if (flag && a >= 0) mycount++;
           int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
           slot = islot(d, DIR, s, i, j, k);
@@ -167,35 +173,35 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   if (DIR == 0) { a = tid % L; cc = tid / L; }
   else { cc = tid % W; a = tid / W; }
   if ((c0 + cc < nac) && (s0 + a < n)) {
-    const double c1[4] = {0.0, 0.5 * 0.75, 0.5 * -0.15, 0.5 * (1.0 / 60.0)};
-    const double c2[4] = {0.0, 0.25 * 0.75, 0.25 * -0.15, 0.25 * (1.0 / 60.0)};
-    double D[5];
+    const R c1[4] = {R(0), R(0.5 * 0.75), R(0.5 * -0.15), R(0.5 * (1.0 / 60.0))};
+    const R c2[4] = {R(0), R(0.25 * 0.75), R(0.25 * -0.15), R(0.25 * (1.0 / 60.0))};
+    R D[5];
     int at = (a + 3) * W + cc;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      double acc = 0.0;
+      R acc = R(0);
 #pragma unroll
       for (int l = 1; l <= 3; ++l) {
-        const double *T = TP + ((l - 1) * 5 + f) * ST;
+        const R *T = TP + ((l - 1) * 5 + f) * ST;
         acc = fma(f == 0 ? c1[l] : c2[l], T[at] - T[at - l * W], acc);
       }
       D[f] = acc;
     }
-    const double *Sp = S + F_P * SF;
+    const R *Sp = S + F_P * SF;
     int ap = (a + GH) * W + cc;
-    double dp = 0.0;
+    R dp = R(0);
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) dp = fma(kA[l], Sp[ap + l * W] - Sp[ap - l * W], dp);
+    for (int l = 1; l <= 3; ++l) dp = fma(ka<R>(l), Sp[ap + l * W] - Sp[ap - l * W], dp);
     D[1 + DIR] += dp;
     int i = DIR == 0 ? x0 + a : x0 + cc;
     int j = DIR == 0 ? y0 + cc : (DIR == 1 ? y0 + a : y0);
     int k = DIR == 2 ? z0 + a : z0;
-    double scale = DIR == 0 ? d.idx : (DIR == 1 ? __ldg(d.eta_y + j) : d.idz);
+    R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + j) : K.idz);
     long long q = ((long long)k * d.ny + j) * d.nx + i;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
-      double *o = d.fl + f * d.n + q;
-      double prev = accumulate ? *o : 0.0;
+      R *o = V.fl + f * d.n + q;
+      R prev = accumulate ? *o : R(0);
       *o = fma(-scale, D[f], prev);
     }
   }
@@ -206,57 +212,59 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
 // Jiang & Shu (r=3), Balsara & Shu (r=4), alpha_k = d_k/(eps+beta_k)^2;
 // the normalisation sum alpha_k q_k / sum alpha_k is evaluated with one
 // division by multiplying through by prod_k (eps+beta_k)^2.
-__device__ __forceinline__ double weno5(const double *g) {
-  const double eps = 1e-6;
-  double q0 = (2.0 * g[0] - 7.0 * g[1] + 11.0 * g[2]) * (1.0 / 6.0);
-  double q1 = (-g[1] + 5.0 * g[2] + 2.0 * g[3]) * (1.0 / 6.0);
-  double q2 = (2.0 * g[2] + 5.0 * g[3] - g[4]) * (1.0 / 6.0);
-  double t, b0, b1, b2;
-  t = g[0] - 2.0 * g[1] + g[2]; b0 = (13.0 / 12.0) * t * t;
-  t = g[0] - 4.0 * g[1] + 3.0 * g[2]; b0 += 0.25 * t * t;
-  t = g[1] - 2.0 * g[2] + g[3]; b1 = (13.0 / 12.0) * t * t;
-  t = g[1] - g[3]; b1 += 0.25 * t * t;
-  t = g[2] - 2.0 * g[3] + g[4]; b2 = (13.0 / 12.0) * t * t;
-  t = 3.0 * g[2] - 4.0 * g[3] + g[4]; b2 += 0.25 * t * t;
-  double s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
+template <class R>
+__device__ __forceinline__ R weno5(const R *g) {
+  const R eps = R(1e-6);
+  R q0 = (R(2) * g[0] - R(7) * g[1] + R(11) * g[2]) * R(1.0 / 6.0);
+  R q1 = (-g[1] + R(5) * g[2] + R(2) * g[3]) * R(1.0 / 6.0);
+  R q2 = (R(2) * g[2] + R(5) * g[3] - g[4]) * R(1.0 / 6.0);
+  R t, b0, b1, b2;
+  t = g[0] - R(2) * g[1] + g[2]; b0 = R(13.0 / 12.0) * t * t;
+  t = g[0] - R(4) * g[1] + R(3) * g[2]; b0 += R(0.25) * t * t;
+  t = g[1] - R(2) * g[2] + g[3]; b1 = R(13.0 / 12.0) * t * t;
+  t = g[1] - g[3]; b1 += R(0.25) * t * t;
+  t = g[2] - R(2) * g[3] + g[4]; b2 = R(13.0 / 12.0) * t * t;
+  t = R(3) * g[2] - R(4) * g[3] + g[4]; b2 += R(0.25) * t * t;
+  R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
   s0 *= s0; s1 *= s1; s2 *= s2;
-  double a0 = 0.1 * s1 * s2, a1 = 0.6 * s0 * s2, a2 = 0.3 * s0 * s1;
+  R a0 = R(0.1) * s1 * s2, a1 = R(0.6) * s0 * s2, a2 = R(0.3) * s0 * s1;
   return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
 }
 
-__device__ __forceinline__ double weno7(const double *g) {
-  const double eps = 1e-6;
-  double q0 = (-3.0 * g[0] + 13.0 * g[1] - 23.0 * g[2] + 25.0 * g[3]) * (1.0 / 12.0);
-  double q1 = (g[1] - 5.0 * g[2] + 13.0 * g[3] + 3.0 * g[4]) * (1.0 / 12.0);
-  double q2 = (-g[2] + 7.0 * g[3] + 7.0 * g[4] - g[5]) * (1.0 / 12.0);
-  double q3 = (3.0 * g[3] + 13.0 * g[4] - 5.0 * g[5] + g[6]) * (1.0 / 12.0);
+template <class R>
+__device__ __forceinline__ R weno7(const R *g) {
+  const R eps = R(1e-6);
+  R q0 = (R(-3) * g[0] + R(13) * g[1] - R(23) * g[2] + R(25) * g[3]) * R(1.0 / 12.0);
+  R q1 = (g[1] - R(5) * g[2] + R(13) * g[3] + R(3) * g[4]) * R(1.0 / 12.0);
+  R q2 = (-g[2] + R(7) * g[3] + R(7) * g[4] - g[5]) * R(1.0 / 12.0);
+  R q3 = (R(3) * g[3] + R(13) * g[4] - R(5) * g[5] + g[6]) * R(1.0 / 12.0);
   // smoothness indicators: 240 x the Jiang-Shu measure as sums of squares
   // of the undivided differences of each 4-point substencil
-  double bk[4];
-  const double c10[4] = {5.0 / 2.0, 3.0 / 2.0, 1.0 / 2.0, -1.0 / 2.0};
-  const double c11[4] = {11.0 / 6.0, 1.0 / 3.0, -1.0 / 6.0, 1.0 / 3.0};
-  const double c2[4] = {2.0, 1.0, 0.0, -1.0};
+  R bk[4];
+  const R c10[4] = {R(5.0 / 2.0), R(3.0 / 2.0), R(1.0 / 2.0), R(-1.0 / 2.0)};
+  const R c11[4] = {R(11.0 / 6.0), R(1.0 / 3.0), R(-1.0 / 6.0), R(1.0 / 3.0)};
+  const R c2[4] = {R(2), R(1), R(0), R(-1)};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    double e1 = g[k + 1] - g[k];
-    double e2 = g[k + 2] - 2.0 * g[k + 1] + g[k];
-    double e3 = g[k + 3] - 3.0 * g[k + 2] + 3.0 * g[k + 1] - g[k];
-    double t1 = e1 + c10[k] * e2 + c11[k] * e3;
-    double t2 = e2 + c2[k] * e3;
-    bk[k] = 240.0 * t1 * t1 + 260.0 * t2 * t2 + (781.0 / 3.0) * e3 * e3;
+    R e1 = g[k + 1] - g[k];
+    R e2 = g[k + 2] - R(2) * g[k + 1] + g[k];
+    R e3 = g[k + 3] - R(3) * g[k + 2] + R(3) * g[k + 1] - g[k];
+    R t1 = e1 + c10[k] * e2 + c11[k] * e3;
+    R t2 = e2 + c2[k] * e3;
+    bk[k] = R(240) * t1 * t1 + R(260) * t2 * t2 + R(781.0 / 3.0) * e3 * e3;
   }
-  double s0 = eps + bk[0], s1 = eps + bk[1], s2 = eps + bk[2], s3 = eps + bk[3];
+  R s0 = eps + bk[0], s1 = eps + bk[1], s2 = eps + bk[2], s3 = eps + bk[3];
   s0 *= s0; s1 *= s1; s2 *= s2; s3 *= s3;
-  double p01 = s0 * s1, p23 = s2 * s3;
-  double a0 = (1.0 / 35.0) * s1 * p23, a1 = (12.0 / 35.0) * s0 * p23;
-  double a2 = (18.0 / 35.0) * p01 * s3, a3 = (4.0 / 35.0) * p01 * s2;
+  R p01 = s0 * s1, p23 = s2 * s3;
+  R a0 = R(1.0 / 35.0) * s1 * p23, a1 = R(12.0 / 35.0) * s0 * p23;
+  R a2 = R(18.0 / 35.0) * p01 * s3, a3 = R(4.0 / 35.0) * p01 * s2;
   return (a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3) / (a0 + a1 + a2 + a3);
 }
 
-template <int WR>
-__device__ __forceinline__ double weno_rec(const double *g) {
-  if constexpr (WR == 3) return weno5(g);
-  else return weno7(g);
+template <int WR, class R>
+__device__ __forceinline__ R weno_rec(const R *g) {
+  if constexpr (WR == 3) return weno5<R>(g);
+  else return weno7<R>(g);
 }
 
 // F_weno - F_central at every listed interface of direction DIR.
@@ -274,13 +282,15 @@ __device__ __forceinline__ double weno_rec(const double *g) {
 // PA = p h2 b (u_n - u~_n), PB = p h2 c~.  Lax-Friedrichs: each field's
 // dissipation is the largest |eigenvalue| (u_n - c, u_n, u_n + c) over the
 // stencil points.  The result goes back with the right eigenvectors.
-template <int DIR, int WR>
+template <int DIR, int WR, class R>
 __global__ void __launch_bounds__(128) k_weno(Dev d) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int NP = 2 * WR;  // stencil points s-WR+1 .. s+WR
+  const View<R> V = view<R>(d);
+  const Consts<R> &K = consts<R>(d);
   const unsigned cnt = d.scal->nlist[DIR];
-  const double *vel[3] = {d.u, d.v, d.ww};
-  const double gam = d.gamma, bq = gam - 1.0;
+  const R *vel[3] = {V.u, V.v, V.ww};
+  const R bq = K.gamma - R(1);
   for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < cnt; e0 += gridDim.x * blockDim.x) {
     const long long slot = d.wlist[DIR][e0];
     int i = 0, j = 0, k = 0, s;
@@ -307,122 +317,122 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     const long long p0 = pidx(d, i, j, k);  // point s of the interface s+1/2
 
     // --- central split-form flux at this interface
-    double FC[5] = {0, 0, 0, 0, 0}, fp = 0.0;
+    R FC[5] = {R(0), R(0), R(0), R(0), R(0)}, fp = R(0);
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
-      double acc[5] = {0, 0, 0, 0, 0}, ps = 0.0;
+      R acc[5] = {R(0), R(0), R(0), R(0), R(0)}, ps = R(0);
 #pragma unroll
       for (int m = 0; m < l; ++m) {
         long long a = p0 - m * stride, b = p0 + (l - m) * stride;
-        double sr = __ldg(d.rho + a) + __ldg(d.rho + b);
-        double su = __ldg(d.u + a) + __ldg(d.u + b), sv = __ldg(d.v + a) + __ldg(d.v + b);
-        double sw = __ldg(d.ww + a) + __ldg(d.ww + b);
-        double sh = __ldg(d.H + a) + __ldg(d.H + b);
-        double sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
-        double mm = sr * sun;
+        R sr = __ldg(V.rho + a) + __ldg(V.rho + b);
+        R su = __ldg(V.u + a) + __ldg(V.u + b), sv = __ldg(V.v + a) + __ldg(V.v + b);
+        R sw = __ldg(V.ww + a) + __ldg(V.ww + b);
+        R sh = __ldg(V.H + a) + __ldg(V.H + b);
+        R sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
+        R mm = sr * sun;
         acc[0] += mm;
         acc[1] += mm * su;
         acc[2] += mm * sv;
         acc[3] += mm * sw;
         acc[4] += mm * sh;
-        ps += __ldg(d.p + a) + __ldg(d.p + b);
+        ps += __ldg(V.p + a) + __ldg(V.p + b);
       }
-      double al = kA[l];
-      FC[0] += 0.5 * al * acc[0];
+      R al = ka<R>(l);
+      FC[0] += R(0.5) * al * acc[0];
 #pragma unroll
-      for (int f = 1; f < 5; ++f) FC[f] += 0.25 * al * acc[f];
+      for (int f = 1; f < 5; ++f) FC[f] += R(0.25) * al * acc[f];
       fp += al * ps;
     }
     FC[1 + DIR] += fp;
 
     // --- Roe average of the two interface states
     const long long ia = p0, ib = p0 + stride;
-    double ra = sqrt(__ldg(d.rho + ia)), rb = sqrt(__ldg(d.rho + ib));
-    double inv = 1.0 / (ra + rb);
-    double un = (ra * __ldg(vel[DIR] + ia) + rb * __ldg(vel[DIR] + ib)) * inv;
-    double ut1 = (ra * __ldg(vel[T1] + ia) + rb * __ldg(vel[T1] + ib)) * inv;
-    double ut2 = (ra * __ldg(vel[T2] + ia) + rb * __ldg(vel[T2] + ib)) * inv;
-    double Ht = (ra * __ldg(d.H + ia) + rb * __ldg(d.H + ib)) * inv;
-    double q2 = un * un + ut1 * ut1 + ut2 * ut2;
-    double c2 = bq * (Ht - 0.5 * q2);
-    double cs = sqrt(c2);
-    double h2 = 0.5 / c2;
-    double hb = h2 * bq, hc = h2 * cs;
+    R ra = sqrt(__ldg(V.rho + ia)), rb = sqrt(__ldg(V.rho + ib));
+    R inv = R(1) / (ra + rb);
+    R un = (ra * __ldg(vel[DIR] + ia) + rb * __ldg(vel[DIR] + ib)) * inv;
+    R ut1 = (ra * __ldg(vel[T1] + ia) + rb * __ldg(vel[T1] + ib)) * inv;
+    R ut2 = (ra * __ldg(vel[T2] + ia) + rb * __ldg(vel[T2] + ib)) * inv;
+    R Ht = (ra * __ldg(V.H + ia) + rb * __ldg(V.H + ib)) * inv;
+    R q2 = un * un + ut1 * ut1 + ut2 * ut2;
+    R c2 = bq * (Ht - R(0.5) * q2);
+    R cs = sqrt(c2);
+    R h2 = R(0.5) / c2;
+    R hb = h2 * bq, hc = h2 * cs;
 
     // --- per stencil point: l_e W and l_e F for the five fields
-    double V[5][NP], G[5][NP];
-    double al0 = 0.0, al1 = 0.0, al4 = 0.0;
+    R Vv[5][NP], G[5][NP];
+    R al0 = R(0), al1 = R(0), al4 = R(0);
 #pragma unroll
     for (int m = 0; m < NP; ++m) {
       long long q = p0 + (m - WR + 1) * stride;
-      double r = __ldg(d.rho + q), unm = __ldg(vel[DIR] + q);
-      double u1 = __ldg(vel[T1] + q), u2 = __ldg(vel[T2] + q);
-      double pm = __ldg(d.p + q), hm = __ldg(d.H + q);
-      double cm = sqrt(d.gR * __ldg(d.T + q));
-      double mn = r * unm, m1 = r * u1, m2 = r * u2, E = r * hm - pm;
-      double A = hb * (0.5 * q2 * r - un * mn - ut1 * m1 - ut2 * m2 + E);
-      double B = hc * (un * r - mn);
-      double PA = pm * hb * (unm - un), PB = pm * hc;
-      V[0][m] = A + B;
-      V[1][m] = r - 2.0 * A;
-      V[2][m] = m1 - ut1 * r;
-      V[3][m] = m2 - ut2 * r;
-      V[4][m] = A - B;
-      G[0][m] = unm * V[0][m] + PA - PB;
-      G[1][m] = unm * V[1][m] - 2.0 * PA;
-      G[2][m] = unm * V[2][m];
-      G[3][m] = unm * V[3][m];
-      G[4][m] = unm * V[4][m] + PA + PB;
+      R r = __ldg(V.rho + q), unm = __ldg(vel[DIR] + q);
+      R u1 = __ldg(vel[T1] + q), u2 = __ldg(vel[T2] + q);
+      R pm = __ldg(V.p + q), hm = __ldg(V.H + q);
+      R cm = sqrt(K.gR * __ldg(V.T + q));
+      R mn = r * unm, m1 = r * u1, m2 = r * u2, E = r * hm - pm;
+      R A = hb * (R(0.5) * q2 * r - un * mn - ut1 * m1 - ut2 * m2 + E);
+      R B = hc * (un * r - mn);
+      R PA = pm * hb * (unm - un), PB = pm * hc;
+      Vv[0][m] = A + B;
+      Vv[1][m] = r - R(2) * A;
+      Vv[2][m] = m1 - ut1 * r;
+      Vv[3][m] = m2 - ut2 * r;
+      Vv[4][m] = A - B;
+      G[0][m] = unm * Vv[0][m] + PA - PB;
+      G[1][m] = unm * Vv[1][m] - R(2) * PA;
+      G[2][m] = unm * Vv[2][m];
+      G[3][m] = unm * Vv[3][m];
+      G[4][m] = unm * Vv[4][m] + PA + PB;
       al0 = fmax(al0, fabs(unm - cm));
       al1 = fmax(al1, fabs(unm));
       al4 = fmax(al4, fabs(unm + cm));
     }
-    double gh[5];
+    R gh[5];
 #pragma unroll
     for (int e = 0; e < 5; ++e) {
-      double alpha = e == 0 ? al0 : (e == 4 ? al4 : al1);
-      double gp[2 * WR - 1], gmn[2 * WR - 1];
+      R alpha = e == 0 ? al0 : (e == 4 ? al4 : al1);
+      R gp[2 * WR - 1], gmn[2 * WR - 1];
 #pragma unroll
       for (int m = 0; m < 2 * WR - 1; ++m) {
-        gp[m] = 0.5 * (G[e][m] + alpha * V[e][m]);
+        gp[m] = R(0.5) * (G[e][m] + alpha * Vv[e][m]);
         int mm = NP - 1 - m;
-        gmn[m] = 0.5 * (G[e][mm] - alpha * V[e][mm]);
+        gmn[m] = R(0.5) * (G[e][mm] - alpha * Vv[e][mm]);
       }
-      gh[e] = weno_rec<WR>(gp) + weno_rec<WR>(gmn);
+      gh[e] = weno_rec<WR, R>(gp) + weno_rec<WR, R>(gmn);
     }
     // --- back to conserved fluxes with the right eigenvectors
-    double s014 = gh[0] + gh[1] + gh[4];
-    double dn = gh[4] - gh[0];
-    double Fr[5];
+    R s014 = gh[0] + gh[1] + gh[4];
+    R dn = gh[4] - gh[0];
+    R Fr[5];
     Fr[0] = s014;
     Fr[1 + DIR] = un * s014 + cs * dn;
     Fr[1 + T1] = ut1 * s014 + gh[2];
     Fr[1 + T2] = ut2 * s014 + gh[3];
-    Fr[4] = Ht * (gh[0] + gh[4]) + un * cs * dn + 0.5 * q2 * gh[1] + ut1 * gh[2] + ut2 * gh[3];
+    Fr[4] = Ht * (gh[0] + gh[4]) + un * cs * dn + R(0.5) * q2 * gh[1] + ut1 * gh[2] + ut2 * gh[3];
     const long long ns = d.nslot[DIR];
 #pragma unroll
-    for (int f = 0; f < 5; ++f) d.dF[DIR][f * ns + slot] = Fr[f] - FC[f];
+    for (int f = 0; f < 5; ++f) V.dF[DIR][f * ns + slot] = Fr[f] - FC[f];
   }
 }
 
-template <int DIR>
+template <int DIR, class R>
 constexpr size_t flux_smem() {
   constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
-  return sizeof(double) * ((size_t)NF * (L + 2 * GH) * W + (size_t)15 * (L + 3) * W);
+  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)15 * (L + 3) * W);
 }
 
-template <int DIR, int WR>
+template <int DIR, int WR, class R>
 cudaError_t launch_one(const Dev &d, int accumulate, cudaStream_t st) {
   constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
   dim3 grid;
   if (DIR == 0) grid = dim3((d.nx + L - 1) / L, (d.ny + W - 1) / W, d.nz);
   if (DIR == 1) grid = dim3((d.nx + W - 1) / W, (d.ny + L - 1) / L, d.nz);
   if (DIR == 2) grid = dim3((d.nx + W - 1) / W, (d.nz + L - 1) / L, d.ny);
-  k_flux<DIR, WR><<<grid, NTHREADS, flux_smem<DIR>(), st>>>(d, accumulate);
+  k_flux<DIR, WR, R><<<grid, NTHREADS, flux_smem<DIR, R>(), st>>>(d, accumulate);
   return cudaGetLastError();
 }
 
-template <int DIR, int WR>
+template <int DIR, int WR, class R>
 cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -431,20 +441,54 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
   long long cap = 8LL * sms;
   unsigned nb = (unsigned)(need < cap ? need : cap);
   if (nb == 0) nb = 1;
-  k_weno<DIR, WR><<<nb, 128, 0, st>>>(d);
+  k_weno<DIR, WR, R><<<nb, 128, 0, st>>>(d);
   return cudaGetLastError();
 }
 
-template <int DIR, int WR>
+template <int DIR, int WR, class R>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_flux<DIR, WR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flux_smem<DIR>());
+  return cudaFuncSetAttribute(k_flux<DIR, WR, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)flux_smem<DIR, R>());
+}
+
+template <class R>
+cudaError_t flux_dispatch(const Dev &d, int dir, int accumulate, cudaStream_t st) {
+  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
+  switch (dir * 10 + wr) {
+    case 0: return launch_one<0, 0, R>(d, accumulate, st);
+    case 3: return launch_one<0, 3, R>(d, accumulate, st);
+    case 4: return launch_one<0, 4, R>(d, accumulate, st);
+    case 10: return launch_one<1, 0, R>(d, accumulate, st);
+    case 13: return launch_one<1, 3, R>(d, accumulate, st);
+    case 14: return launch_one<1, 4, R>(d, accumulate, st);
+    case 20: return launch_one<2, 0, R>(d, accumulate, st);
+    case 23: return launch_one<2, 3, R>(d, accumulate, st);
+    case 24: return launch_one<2, 4, R>(d, accumulate, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class R>
+cudaError_t weno_dispatch(const Dev &d, int dir, cudaStream_t st) {
+  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
+  switch (dir * 10 + wr) {
+    case 3: return launch_weno_one<0, 3, R>(d, st);
+    case 4: return launch_weno_one<0, 4, R>(d, st);
+    case 13: return launch_weno_one<1, 3, R>(d, st);
+    case 14: return launch_weno_one<1, 4, R>(d, st);
+    case 23: return launch_weno_one<2, 3, R>(d, st);
+    case 24: return launch_weno_one<2, 4, R>(d, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 cudaError_t flux_set_attributes() {
   cudaError_t e = cudaSuccess, r;
-#define S2_ATTR(D, R) if ((r = set_attr<D, R>()) != cudaSuccess) e = r;
+#define S2_ATTR(D, W)                                     \
+  if ((r = set_attr<D, W, double>()) != cudaSuccess) e = r; \
+  if ((r = set_attr<D, W, float>()) != cudaSuccess) e = r;
   S2_ATTR(0, 0) S2_ATTR(1, 0) S2_ATTR(2, 0)
   S2_ATTR(0, 3) S2_ATTR(1, 3) S2_ATTR(2, 3)
   S2_ATTR(0, 4) S2_ATTR(1, 4) S2_ATTR(2, 4)
@@ -453,32 +497,11 @@ cudaError_t flux_set_attributes() {
 }
 
 cudaError_t launch_flux(const Dev &d, int dir, int accumulate, cudaStream_t st) {
-  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
-  switch (dir * 10 + wr) {
-    case 0: return launch_one<0, 0>(d, accumulate, st);
-    case 3: return launch_one<0, 3>(d, accumulate, st);
-    case 4: return launch_one<0, 4>(d, accumulate, st);
-    case 10: return launch_one<1, 0>(d, accumulate, st);
-    case 13: return launch_one<1, 3>(d, accumulate, st);
-    case 14: return launch_one<1, 4>(d, accumulate, st);
-    case 20: return launch_one<2, 0>(d, accumulate, st);
-    case 23: return launch_one<2, 3>(d, accumulate, st);
-    case 24: return launch_one<2, 4>(d, accumulate, st);
-  }
-  return cudaErrorInvalidValue;
+  return d.mixed ? flux_dispatch<float>(d, dir, accumulate, st) : flux_dispatch<double>(d, dir, accumulate, st);
 }
 
 cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st) {
-  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
-  switch (dir * 10 + wr) {
-    case 3: return launch_weno_one<0, 3>(d, st);
-    case 4: return launch_weno_one<0, 4>(d, st);
-    case 13: return launch_weno_one<1, 3>(d, st);
-    case 14: return launch_weno_one<1, 4>(d, st);
-    case 23: return launch_weno_one<2, 3>(d, st);
-    case 24: return launch_weno_one<2, 4>(d, st);
-  }
-  return cudaErrorInvalidValue;
+  return d.mixed ? weno_dispatch<float>(d, dir, st) : weno_dispatch<double>(d, dir, st);
 }
 
 }  // namespace s2

@@ -29,6 +29,16 @@ struct Scal {
 // Error bits written by kernels (mapped to S2_ENONFINITE on the host).
 constexpr int ERR_NONFINITE = 1;
 
+// Scheme constants in the arithmetic type R of a kernel (double for the
+// FP64 path, float for the flux arithmetic of the mixed path).
+template <class R>
+struct Consts {
+  R ax[4], az[4];          // a_l/dx, a_l/dz (first derivative, l = 1..3)
+  R bx[4], bz[4];          // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..3)
+  R idx, idz;              // 1/dx, 1/dz
+  R R_gas, cp, gamma, gR, icv, visc_exp, inv_t_ref, t_wall, cp_over_pr, re, thr;
+};
+
 // Everything a kernel needs, passed by value.
 struct Dev {
   int nx, ny, nz;
@@ -46,16 +56,22 @@ struct Dev {
   double cfl;
   double vol_inv;          // 1 / sum(dV) / (dx dz) for the forcing
   int viscous, wall_y, weno, force;
-  // state and registers (interior layout [v][k][j][i])
-  double *w, *fl, *fln;
-  // primitives with ghosts
-  double *rho, *u, *v, *ww, *T, *p, *H;
-  // auxiliary fields
-  double *mu;              // interior
-  double *g;               // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
-  double *div, *sens;      // padded
-  // metrics (length ny)
-  const double *eta_y, *ay, *by, *ry, *dvy;  // eta_y; a_l eta_y (3/j); b_l eta_y^2 (4/j); eta_yy/eta_y; 1/eta_y
+  int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
+  Consts<double> kd;
+  Consts<float> kf;
+  // state (FP64 in both modes; interior layout [v][k][j][i])
+  double *w;
+  // RHS accumulator and RK register (R), same layout
+  void *fl, *fln;
+  // primitives with ghosts (R)
+  void *rho, *u, *v, *ww, *T, *p, *H;
+  // auxiliary fields (R)
+  void *mu;                // interior
+  void *g;                 // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
+  void *div, *sens;        // padded
+  // metrics (length ny): eta_y; a_l eta_y (3/j); b_l eta_y^2 (4/j); eta_yy/eta_y; 1/eta_y
+  const double *eta_y, *ay, *by, *ry, *dvy;
+  const float *eta_yf, *ayf, *byf, *ryf;  // the same in single precision
   Scal *scal;
   double *part;            // reduction partials
   // hybrid scheme, per direction: interface flags (n_d + 1 slots per
@@ -63,9 +79,64 @@ struct Dev {
   // every listed slot (5 values, slot-major per component)
   unsigned char *flag[3];
   unsigned int *wlist[3];
-  double *dF[3];
+  void *dF[3];             // R
   long long nslot[3];
 };
+
+// Typed views of the fields of a Dev in the arithmetic type R.
+template <class R>
+struct View {
+  R *fl, *fln, *rho, *u, *v, *ww, *T, *p, *H, *mu, *g, *div, *sens;
+  R *dF[3];
+  const R *eta_y, *ay, *by, *ry;
+};
+
+template <class R>
+__host__ __device__ inline const Consts<R> &consts(const Dev &d);
+template <>
+__host__ __device__ inline const Consts<double> &consts<double>(const Dev &d) {
+  return d.kd;
+}
+template <>
+__host__ __device__ inline const Consts<float> &consts<float>(const Dev &d) {
+  return d.kf;
+}
+
+template <class R>
+__host__ __device__ inline View<R> view(const Dev &d) {
+  View<R> v;
+  v.fl = (R *)d.fl;
+  v.fln = (R *)d.fln;
+  v.rho = (R *)d.rho;
+  v.u = (R *)d.u;
+  v.v = (R *)d.v;
+  v.ww = (R *)d.ww;
+  v.T = (R *)d.T;
+  v.p = (R *)d.p;
+  v.H = (R *)d.H;
+  v.mu = (R *)d.mu;
+  v.g = (R *)d.g;
+  v.div = (R *)d.div;
+  v.sens = (R *)d.sens;
+  for (int a = 0; a < 3; ++a) v.dF[a] = (R *)d.dF[a];
+  if constexpr (sizeof(R) == 8) {
+    v.eta_y = (const R *)d.eta_y;
+    v.ay = (const R *)d.ay;
+    v.by = (const R *)d.by;
+    v.ry = (const R *)d.ry;
+  } else {
+    v.eta_y = (const R *)d.eta_yf;
+    v.ay = (const R *)d.ayf;
+    v.by = (const R *)d.byf;
+    v.ry = (const R *)d.ryf;
+  }
+  return v;
+}
+
+// Bit pattern of a non-negative value as a signed integer that orders like
+// the value (exact comparisons on the integer pipe).
+__device__ __forceinline__ long long order_bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int order_bits(float x) { return __float_as_int(x); }
 
 __host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
   return d.off0 + (long long)k * d.sz + (long long)j * d.sy + i;
@@ -118,6 +189,11 @@ __host__ __device__ inline long long islot(const Dev &d, int dir, int s, int i, 
   if (dir == 0) return ((long long)k * d.ny + j) * (d.nx + 1) + (s + 1);
   if (dir == 1) return ((long long)k * (d.ny + 1) + (s + 1)) * d.nx + i;
   return ((long long)(s + 1) * d.ny + j) * d.nx + i;
+}
+
+// Single-precision power law mu = (T/T_ref)^omega / Re of the mixed path.
+__device__ __forceinline__ float viscosity(const Dev &d, float T) {
+  return powf(T * d.kf.inv_t_ref, d.kf.visc_exp) / d.kf.re;
 }
 
 // Launch helpers (defined in the kernel translation units).

@@ -83,9 +83,10 @@ __device__ void block_sum(double *v) {
 // y metric from the node ordinates extended into the ghosts (periodic
 // shift or mirror about the walls at -ly/2, ly/2): y_eta by the 6th-order
 // stencil, eta_y = 1/y_eta, eta_yy = -y_etaeta/y_eta^3.  Also the
-// pre-scaled coefficient tables used by the stencil kernels.
-__global__ void k_metric(const double *yn, int ny, double ly, int wall, double *eta_y, double *ay,
-                         double *by, double *ry, double *dvy) {
+// pre-scaled coefficient tables used by the stencil kernels, in double and
+// in single precision.
+__global__ void k_metric(const double *yn, int ny, double ly, int wall, double *eta_y, double *ay, double *by,
+                         double *ry, double *dvy, float *eta_yf, float *ayf, float *byf, float *ryf) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ny) return;
   const double a[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
@@ -108,10 +109,32 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
   double ey = 1.0 / d1;
   double eyy = -d2 / (d1 * d1 * d1);
   eta_y[j] = ey;
-  for (int l = 1; l <= 3; ++l) ay[3 * j + l - 1] = a[l] * ey;
-  for (int l = 0; l <= 3; ++l) by[4 * j + l] = b[l] * ey * ey;
+  eta_yf[j] = (float)ey;
+  for (int l = 1; l <= 3; ++l) {
+    ay[3 * j + l - 1] = a[l] * ey;
+    ayf[3 * j + l - 1] = (float)(a[l] * ey);
+  }
+  for (int l = 0; l <= 3; ++l) {
+    by[4 * j + l] = b[l] * ey * ey;
+    byf[4 * j + l] = (float)(b[l] * ey * ey);
+  }
   ry[j] = eyy / ey;
+  ryf[j] = (float)(eyy / ey);
   dvy[j] = d1;
+}
+
+__device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_dt) {
+  if (want_dt) {
+    __shared__ double red[NT / 32];
+    double m = warp_max(sr);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+      s = warp_max(s);
+      if (threadIdx.x == 0) d.part[blockIdx.x] = s;
+    }
+  }
 }
 
 // ------------------------------------------------------------- primitives
@@ -120,6 +143,7 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
 // CFL spectral radius max into part[block] (c = sqrt(gamma R T)).
 __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  const View<double> V = view<double>(d);
   double sr = 0.0;
   if (q < d.n) {
     int i, j, k;
@@ -132,33 +156,73 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
     double q2 = u * u + v * v + ww * ww;
     double T = (w[4 * d.n + q] * ri - 0.5 * q2) * d.icv;
     double pr = rho * d.R * T;
-    d.rho[p] = rho;
-    d.u[p] = u;
-    d.v[p] = v;
-    d.ww[p] = ww;
-    d.T[p] = T;
-    d.p[p] = pr;
-    d.H[p] = d.cp * T + 0.5 * q2;
+    V.rho[p] = rho;
+    V.u[p] = u;
+    V.v[p] = v;
+    V.ww[p] = ww;
+    V.T[p] = T;
+    V.p[p] = pr;
+    V.H[p] = d.cp * T + 0.5 * q2;
     double mu = 0.0;
     if (d.viscous) {
       mu = viscosity(d, T);
-      d.mu[q] = mu;
+      V.mu[q] = mu;
     }
     if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
     if (want_dt) sr = spectral_radius(d, rho, u, v, ww, T, mu, d.eta_y[j]);
   }
-  if (want_dt) {
-    __shared__ double red[NT / 32];
-    double m = warp_max(sr);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
-      s = warp_max(s);
-      if (threadIdx.x == 0) d.part[blockIdx.x] = s;
+  dt_block_max(d, sr, want_dt);
+}
+
+// Mixed path: the internal energy comes from E - |m|^2/(2 rho) in double
+// precision (E and the kinetic energy nearly cancel at high speed and the
+// temperature carries the pressure), with 1/rho from a single-precision
+// reciprocal refined by one Newton step; everything stored is single
+// precision, as is the rest of the arithmetic.
+__global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int want_dt) {
+  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  const View<float> V = view<float>(d);
+  const Consts<float> &K = d.kf;
+  double sr = 0.0;
+  if (q < d.n) {
+    int i, j, k;
+    point_of(d, q, i, j, k);
+    long long p = pidx(d, i, j, k);
+    const double *w = d.w;
+    double rho = w[q], m1 = w[d.n + q], m2 = w[2 * d.n + q], m3 = w[3 * d.n + q], E = w[4 * d.n + q];
+    float rf = (float)rho;
+    float rif = 1.0f / rf;
+    double ri = (double)rif;
+    ri = ri * (2.0 - rho * ri);
+    double e = (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * ri) * ri;
+    float T = (float)(e * d.icv);
+    float u = (float)m1 * rif, v = (float)m2 * rif, ww = (float)m3 * rif;
+    float q2 = u * u + v * v + ww * ww;
+    V.rho[p] = rf;
+    V.u[p] = u;
+    V.v[p] = v;
+    V.ww[p] = ww;
+    V.T[p] = T;
+    V.p[p] = rf * K.R_gas * T;
+    V.H[p] = K.cp * T + 0.5f * q2;
+    float mu = 0.0f;
+    if (d.viscous) {
+      mu = viscosity(d, T);
+      V.mu[q] = mu;
+    }
+    if (!(rf > 0.0f) || !(T > 0.0f) || !isfinite(rf) || !isfinite(T) || !isfinite(q2))
+      atomicOr(&d.scal->status, ERR_NONFINITE);
+    if (want_dt) {
+      float cs = sqrtf(K.gR * T);
+      float ey = d.eta_yf[j];
+      float srf = (fabsf(u) + cs) * K.idx + (fabsf(v) + cs) * ey + (fabsf(ww) + cs) * K.idz;
+      if (d.viscous)
+        srf += K.gamma * mu / ((float)d.prandtl * rf) * (K.idx * K.idx + ey * ey + K.idz * K.idz);
+      sr = srf;
     }
   }
+  dt_block_max(d, sr, want_dt);
 }
 
 // dt = cfl / max(spectral radius) over the partials of k_prims.
@@ -180,15 +244,10 @@ __global__ void k_dt_final(Dev d, int nparts) {
 }
 
 // ----------------------------------------------------------------- ghosts
-// Face ghosts (GH deep) of the primitive fields.  x and z periodic; y
-// periodic or isothermal no-slip wall mirrored about the face between the
-// outermost node and its ghost: u -> -u, T -> 2 T_w - T, p -> p,
-// rho = p/(R T), H from T and |u|.
-__global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
-  long long nxf = 2LL * GH * d.ny * d.nz, nyf = 2LL * GH * d.nx * d.nz, nzf = 2LL * GH * d.nx * d.ny;
-  long long t = (long long)blockIdx.x * NT + threadIdx.x;
-  if (t >= nxf + nyf + nzf) return;
-  int di, dj, dk, si, sj, sk;
+// Face ghost (GH deep) t of the three face sets -> destination and source.
+__device__ __forceinline__ bool ghost_map(const Dev &d, long long t, int &di, int &dj, int &dk, int &si, int &sj,
+                                          int &sk) {
+  long long nxf = 2LL * GH * d.ny * d.nz, nyf = 2LL * GH * d.nx * d.nz;
   bool wall = false;
   if (t < nxf) {
     int g = (int)(t % (2 * GH));
@@ -221,88 +280,77 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
     si = di; sj = dj;
     sk = imod(dk, d.nz);
   }
+  return wall;
+}
+
+// Face ghosts of the primitive fields.  x and z periodic; y periodic or
+// isothermal no-slip wall mirrored about the face between the outermost
+// node and its ghost: u -> -u, T -> 2 T_w - T, p -> p, rho = p/(R T), H from
+// T and |u|.
+template <class R>
+__global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
+  long long total = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+  long long t = (long long)blockIdx.x * NT + threadIdx.x;
+  if (t >= total) return;
+  const View<R> V = view<R>(d);
+  const Consts<R> &K = consts<R>(d);
+  int di, dj, dk, si, sj, sk;
+  bool wall = ghost_map(d, t, di, dj, dk, si, sj, sk);
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
   if (!wall) {
-    d.rho[dp] = d.rho[sp];
-    d.u[dp] = d.u[sp];
-    d.v[dp] = d.v[sp];
-    d.ww[dp] = d.ww[sp];
-    d.T[dp] = d.T[sp];
-    d.p[dp] = d.p[sp];
-    d.H[dp] = d.H[sp];
+    V.rho[dp] = V.rho[sp];
+    V.u[dp] = V.u[sp];
+    V.v[dp] = V.v[sp];
+    V.ww[dp] = V.ww[sp];
+    V.T[dp] = V.T[sp];
+    V.p[dp] = V.p[sp];
+    V.H[dp] = V.H[sp];
   } else {
-    double u = -d.u[sp], v = -d.v[sp], ww = -d.ww[sp];
-    double T = 2.0 * d.t_wall - d.T[sp];
-    double pr = d.p[sp];
-    d.u[dp] = u;
-    d.v[dp] = v;
-    d.ww[dp] = ww;
-    d.T[dp] = T;
-    d.p[dp] = pr;
-    d.rho[dp] = pr / (d.R * T);
-    d.H[dp] = d.cp * T + 0.5 * (u * u + v * v + ww * ww);
-    if (!(T > 0.0)) atomicOr(&d.scal->status, ERR_NONFINITE);
+    R u = -V.u[sp], v = -V.v[sp], ww = -V.ww[sp];
+    R T = R(2) * K.t_wall - V.T[sp];
+    R pr = V.p[sp];
+    V.u[dp] = u;
+    V.v[dp] = v;
+    V.ww[dp] = ww;
+    V.T[dp] = T;
+    V.p[dp] = pr;
+    V.rho[dp] = pr / (K.R_gas * T);
+    V.H[dp] = K.cp * T + R(0.5) * (u * u + v * v + ww * ww);
+    if (!(T > R(0))) atomicOr(&d.scal->status, ERR_NONFINITE);
   }
 }
 
 // Face ghosts of div u and of the sensor.  At a wall the sensor is
 // mirrored and the divergence of the mirrored velocity field is
 // -u_x + v_y - w_z at the mirror node.
+template <class R>
 __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
-  long long nxf = 2LL * GH * d.ny * d.nz, nyf = 2LL * GH * d.nx * d.nz, nzf = 2LL * GH * d.nx * d.ny;
+  long long total = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
   long long t = (long long)blockIdx.x * NT + threadIdx.x;
-  if (t >= nxf + nyf + nzf) return;
+  if (t >= total) return;
+  const View<R> V = view<R>(d);
   int di, dj, dk, si, sj, sk;
-  bool wall = false;
-  if (t < nxf) {
-    int g = (int)(t % (2 * GH));
-    long long r = t / (2 * GH);
-    dj = (int)(r % d.ny);
-    dk = (int)(r / d.ny);
-    di = g < GH ? -1 - g : d.nx + (g - GH);
-    si = imod(di, d.nx); sj = dj; sk = dk;
-  } else if (t < nxf + nyf) {
-    t -= nxf;
-    di = (int)(t % d.nx);
-    long long r = t / d.nx;
-    int g = (int)(r % (2 * GH));
-    dk = (int)(r / (2 * GH));
-    dj = g < GH ? -1 - g : d.ny + (g - GH);
-    si = di; sk = dk;
-    if (d.wall_y) {
-      wall = true;
-      sj = dj < 0 ? -1 - dj : 2 * d.ny - 1 - dj;
-    } else {
-      sj = imod(dj, d.ny);
-    }
-  } else {
-    t -= nxf + nyf;
-    di = (int)(t % d.nx);
-    long long r = t / d.nx;
-    int g = (int)(r % (2 * GH));
-    dj = (int)(r / (2 * GH));
-    dk = g < GH ? -1 - g : d.nz + (g - GH);
-    si = di; sj = dj;
-    sk = imod(dk, d.nz);
-  }
+  bool wall = ghost_map(d, t, di, dj, dk, si, sj, sk);
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
-  d.sens[dp] = d.sens[sp];
+  V.sens[dp] = V.sens[sp];
   if (!wall) {
-    d.div[dp] = d.div[sp];
+    V.div[dp] = V.div[sp];
   } else {
     long long q = ((long long)sk * d.ny + sj) * d.nx + si;
-    double ux = d.g[0 * d.n + q], vy = d.g[4 * d.n + q], wz = d.g[8 * d.n + q];
-    d.div[dp] = -ux + vy - wz;
+    R ux = V.g[0 * d.n + q], vy = V.g[4 * d.n + q], wz = V.g[8 * d.n + q];
+    V.div[dp] = -ux + vy - wz;
   }
 }
 
 // ---------------------------------------------------------------- forcing
 // force_rhs_1: partial sums of R_rhou dV (dV ~ 1/eta_y), deterministic.
+template <class R>
 __global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
+  const View<R> V = view<R>(d);
   double s = 0.0;
   for (long long q = (long long)blockIdx.x * NT + threadIdx.x; q < d.n; q += (long long)gridDim.x * NT) {
     int j = (int)((q / d.nx) % d.ny);
-    s += d.fl[d.n + q] * d.dvy[j];
+    s += (double)V.fl[d.n + q] * d.dvy[j];
   }
   double v[1] = {s};
   block_sum<1>(v);
@@ -323,6 +371,7 @@ __global__ void k_force_final(Dev d, int nparts) {
 // stage writes none and advances the clock.
 __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int stage) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  const View<double> V = view<double>(d);
   const double dt = d.scal->dt;
   if (q < d.n) {
     double f = d.force ? d.scal->force : 0.0;
@@ -330,41 +379,73 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
     if (d.force) {
       int i, j, k;
       point_of(d, q, i, j, k);
-      fu = f * d.u[pidx(d, i, j, k)];
+      fu = f * V.u[pidx(d, i, j, k)];
     }
     const double a = dt * gk, b = dt * rk1;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       long long o = v * d.n + q;
-      double R = d.fl[o];
+      double R = V.fl[o];
       if (v == 1) R += f;
       if (v == 4) R += fu;
       double wn = fma(a, R, d.w[o]);
-      if (stage > 0) wn += d.fln[o];
+      if (stage > 0) wn += V.fln[o];
       d.w[o] = wn;
-      if (stage < 2) d.fln[o] = b * R;
+      if (stage < 2) V.fln[o] = b * R;
     }
   }
   if (stage == 2 && q == 0) d.scal->t += dt;
 }
 
-// R = fl + forcing into out (diagnostics).
+// Mixed path: the increment dt gamma_k R + fln is formed in single
+// precision (R and the register are single precision) and accumulated
+// into the double-precision state.
+__global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk1, int stage) {
+  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  const View<float> V = view<float>(d);
+  const double dt = d.scal->dt;
+  if (q < d.n) {
+    float f = d.force ? (float)d.scal->force : 0.0f;
+    float fu = 0.0f;
+    if (d.force) {
+      int i, j, k;
+      point_of(d, q, i, j, k);
+      fu = f * V.u[pidx(d, i, j, k)];
+    }
+    const float a = (float)(dt * gk), b = (float)(dt * rk1);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      long long o = v * d.n + q;
+      float R = V.fl[o];
+      if (v == 1) R += f;
+      if (v == 4) R += fu;
+      float inc = stage > 0 ? fmaf(a, R, V.fln[o]) : a * R;
+      d.w[o] += (double)inc;
+      if (stage < 2) V.fln[o] = b * R;
+    }
+  }
+  if (stage == 2 && q == 0) d.scal->t += dt;
+}
+
+// R = fl + forcing into out (diagnostics, double).
+template <class R>
 __global__ void __launch_bounds__(NT) k_rhs_out(Dev d, double *out) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   if (q >= d.n) return;
+  const View<R> V = view<R>(d);
   double f = d.force ? d.scal->force : 0.0;
   double fu = 0.0;
   if (d.force) {
     int i, j, k;
     point_of(d, q, i, j, k);
-    fu = f * d.u[pidx(d, i, j, k)];
+    fu = f * (double)V.u[pidx(d, i, j, k)];
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    double R = d.fl[v * d.n + q];
-    if (v == 1) R += f;
-    if (v == 4) R += fu;
-    out[v * d.n + q] = R;
+    double Rv = (double)V.fl[v * d.n + q];
+    if (v == 1) Rv += f;
+    if (v == 4) Rv += fu;
+    out[v * d.n + q] = Rv;
   }
 }
 
@@ -372,7 +453,9 @@ __global__ void __launch_bounds__(NT) k_rhs_out(Dev d, double *out) {
 // Integrals of rho, rho u_a, rho E, rho|u|^2/2 (dV = dx dz / eta_y) and
 // the sum of (R_rhou)^2 of the last RHS evaluation.
 constexpr int NSTAT = 7;
+template <class R>
 __global__ void __launch_bounds__(NT) k_stats_partial(Dev d) {
+  const View<R> V = view<R>(d);
   double v[NSTAT] = {0, 0, 0, 0, 0, 0, 0};
   double f = d.force ? d.scal->force : 0.0;
   for (long long q = (long long)blockIdx.x * NT + threadIdx.x; q < d.n; q += (long long)gridDim.x * NT) {
@@ -385,7 +468,7 @@ __global__ void __launch_bounds__(NT) k_stats_partial(Dev d) {
     v[3] += mz * dv;
     v[4] += d.w[4 * d.n + q] * dv;
     v[5] += 0.5 * (mx * mx + my * my + mz * mz) / rho * dv;
-    double r = d.fl[d.n + q] + f;
+    double r = (double)V.fl[d.n + q] + f;
     v[6] += r * r;
   }
   block_sum<NSTAT>(v);
@@ -430,6 +513,8 @@ struct s2_solver {
   size_t flag_bytes[3];
   long long launches_per_step[2];
   long long launches;
+  size_t rsize;         // bytes of the arithmetic type (8 FP64, 4 mixed)
+  double *rhs_stage;    // staging of s2_rhs output
 };
 
 namespace {
@@ -499,7 +584,8 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
   long long nghost = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
   unsigned ngb = (unsigned)((nghost + NT - 1) / NT);
   e = run(tr, st, S2_PROF_PRIMS, 1, [&] {
-    k_prims<<<nb, NT, 0, st>>>(d, want_dt);
+    if (d.mixed) k_prims_mixed<<<nb, NT, 0, st>>>(d, want_dt);
+    else k_prims<<<nb, NT, 0, st>>>(d, want_dt);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
@@ -511,7 +597,8 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
     if (e != cudaSuccess) return e;
   }
   e = run(tr, st, S2_PROF_GHOST, 1, [&] {
-    k_ghost_prim<<<ngb, NT, 0, st>>>(d);
+    if (d.mixed) k_ghost_prim<float><<<ngb, NT, 0, st>>>(d);
+    else k_ghost_prim<double><<<ngb, NT, 0, st>>>(d);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
@@ -519,7 +606,8 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
     e = run(tr, st, S2_PROF_GRAD, 1, [&] { return launch_grad(d, st); });
     if (e != cudaSuccess) return e;
     e = run(tr, st, S2_PROF_GHOST_AUX, 1, [&] {
-      k_ghost_aux<<<ngb, NT, 0, st>>>(d);
+      if (d.mixed) k_ghost_aux<float><<<ngb, NT, 0, st>>>(d);
+      else k_ghost_aux<double><<<ngb, NT, 0, st>>>(d);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -551,7 +639,8 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
   }
   if (d.force) {
     e = run(tr, st, S2_PROF_FORCE, 2, [&] {
-      k_force_partial<<<NRED, NT, 0, st>>>(d);
+      if (d.mixed) k_force_partial<float><<<NRED, NT, 0, st>>>(d);
+      else k_force_partial<double><<<NRED, NT, 0, st>>>(d);
       k_force_final<<<1, NT, 0, st>>>(d, NRED);
       return cudaGetLastError();
     });
@@ -567,7 +656,8 @@ cudaError_t enqueue_step(s2_solver *s, int want_dt, Trace *tr) {
   for (int st = 0; st < 3; ++st) {
     if ((e = enqueue_rhs(s, st == 0 ? want_dt : 0, tr)) != cudaSuccess) return e;
     e = run(tr, s->stream, S2_PROF_UPDATE, 1, [&] {
-      k_update<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
+      if (d.mixed) k_update_mixed<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
+      else k_update<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
       return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -685,7 +775,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (bcs->y == S2_BC_ISOTHERMAL_WALL && (grid->ny < GH || !(bcs->t_wall > 0))) return S2_EINVAL;
   if (scheme->central_order != 6 || scheme->visc_order != 6) return S2_EINVAL;
   if (scheme->weno_order != 0 && scheme->weno_order != 5 && scheme->weno_order != 7) return S2_EINVAL;
-  if (scheme->precision != S2_FP64) return S2_EINVAL;
+  if (scheme->precision != S2_FP64 && scheme->precision != S2_MIXED) return S2_EINVAL;
   if (!(scheme->cfl > 0) && !(scheme->dt_fixed > 0)) return S2_EINVAL;
   if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
@@ -773,24 +863,80 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.wall_y = bcs->y == S2_BC_ISOTHERMAL_WALL;
   d.weno = scheme->weno_order;
   d.force = bcs->force_mass_flow ? 1 : 0;
+  d.mixed = scheme->precision == S2_MIXED ? 1 : 0;
+  // scheme constants in both arithmetic types
+  {
+    Consts<double> &k = d.kd;
+    for (int l = 0; l < 4; ++l) {
+      k.ax[l] = d.ax[l];
+      k.az[l] = d.az[l];
+      k.bx[l] = d.bx[l];
+      k.bz[l] = d.bz[l];
+    }
+    k.idx = d.idx;
+    k.idz = d.idz;
+    k.R_gas = d.R;
+    k.cp = d.cp;
+    k.gamma = d.gamma;
+    k.gR = d.gR;
+    k.icv = d.icv;
+    k.visc_exp = d.visc_exp;
+    k.inv_t_ref = d.inv_t_ref;
+    k.t_wall = d.t_wall;
+    k.cp_over_pr = d.cp_over_pr;
+    k.re = d.re;
+    k.thr = d.thr;
+    Consts<float> &f = d.kf;
+    for (int l = 0; l < 4; ++l) {
+      f.ax[l] = (float)k.ax[l];
+      f.az[l] = (float)k.az[l];
+      f.bx[l] = (float)k.bx[l];
+      f.bz[l] = (float)k.bz[l];
+    }
+    f.idx = (float)k.idx;
+    f.idz = (float)k.idz;
+    f.R_gas = (float)k.R_gas;
+    f.cp = (float)k.cp;
+    f.gamma = (float)k.gamma;
+    f.gR = (float)k.gR;
+    f.icv = (float)k.icv;
+    f.visc_exp = (float)k.visc_exp;
+    f.inv_t_ref = (float)k.inv_t_ref;
+    f.t_wall = (float)k.t_wall;
+    f.cp_over_pr = (float)k.cp_over_pr;
+    f.re = (float)k.re;
+    f.thr = (float)k.thr;
+  }
 
   size_t np = (size_t)d.px * d.py * d.pz;
   size_t nn = (size_t)n;
+  const size_t rs = d.mixed ? sizeof(float) : sizeof(double);  // bytes of the arithmetic type
+  s->rsize = rs;
   bool ok = true;
   auto A = [&](size_t count) -> double * {
     double *p = (double *)dalloc(s, count * sizeof(double));
     if (!p) ok = false;
     return p;
   };
+  auto AR = [&](size_t count) -> void * {
+    void *p = dalloc(s, count * rs);
+    if (!p) ok = false;
+    return p;
+  };
   d.w = A(NV * nn);
-  d.fl = A(NV * nn);
-  d.fln = A(NV * nn);
-  d.rho = A(np); d.u = A(np); d.v = A(np); d.ww = A(np);
-  d.T = A(np); d.p = A(np); d.H = A(np);
-  d.div = A(np); d.sens = A(np);
-  d.mu = A(nn);
-  d.g = A(9 * nn);
+  d.fl = AR(NV * nn);
+  d.fln = AR(NV * nn);
+  d.rho = AR(np); d.u = AR(np); d.v = AR(np); d.ww = AR(np);
+  d.T = AR(np); d.p = AR(np); d.H = AR(np);
+  d.div = AR(np); d.sens = AR(np);
+  d.mu = AR(nn);
+  d.g = AR(9 * nn);
+  // s2_rhs stages its double output in fln when that is double, else here
+  s->rhs_stage = d.mixed ? A(NV * nn) : (double *)d.fln;
   double *eta = A(grid->ny), *ay = A(3 * grid->ny), *by = A(4 * grid->ny), *ry = A(grid->ny), *dvy = A(grid->ny);
+  float *etaf = (float *)dalloc(s, sizeof(float) * grid->ny), *ayf = (float *)dalloc(s, sizeof(float) * 3 * grid->ny);
+  float *byf = (float *)dalloc(s, sizeof(float) * 4 * grid->ny), *ryf = (float *)dalloc(s, sizeof(float) * grid->ny);
+  if (!etaf || !ayf || !byf || !ryf) ok = false;
   size_t nparts = (size_t)((n + NT - 1) / NT);
   if (nparts < (size_t)NRED * NSTAT) nparts = (size_t)NRED * NSTAT;
   d.part = A(nparts);
@@ -804,7 +950,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     d.flag[a] = (unsigned char *)dalloc(s, s->flag_bytes[a]);
     size_t nl = scheme->weno_order ? s->flag_bytes[a] : 1;
     d.wlist[a] = (unsigned *)dalloc(s, nl * sizeof(unsigned));
-    d.dF[a] = (double *)dalloc(s, NV * nl * sizeof(double));
+    d.dF[a] = dalloc(s, NV * nl * rs);
     if (!d.flag[a] || !d.wlist[a] || !d.dF[a]) ok = false;
   }
   if (!ok) {
@@ -817,14 +963,18 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.by = by;
   d.ry = ry;
   d.dvy = dvy;
+  d.eta_yf = etaf;
+  d.ayf = ayf;
+  d.byf = byf;
+  d.ryf = ryf;
 
   cudaError_t e = cudaSuccess;
-  double *pads[] = {d.rho, d.u, d.v, d.ww, d.T, d.p, d.H, d.div, d.sens};
-  for (double *p : pads)
-    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, np * sizeof(double), s->stream);
+  void *pads[] = {d.rho, d.u, d.v, d.ww, d.T, d.p, d.H, d.div, d.sens};
+  for (void *p : pads)
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, np * rs, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.w, 0, NV * nn * sizeof(double), s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.fl, 0, NV * nn * sizeof(double), s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.fln, 0, NV * nn * sizeof(double), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.fl, 0, NV * nn * rs, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.fln, 0, NV * nn * rs, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.scal, 0, sizeof(Scal), s->stream);
   for (int a = 0; a < 3 && e == cudaSuccess; ++a)
     e = cudaMemsetAsync(d.flag[a], 0, s->flag_bytes[a], s->stream);
@@ -842,7 +992,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     e = cudaMemcpyAsync(ynd, yn.data(), sizeof(double) * grid->ny, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) {
     k_metric<<<(grid->ny + 127) / 128, 128, 0, s->stream>>>(ynd, grid->ny, grid->ly, d.wall_y, eta, ay, by, ry,
-                                                             dvy);
+                                                             dvy, etaf, ayf, byf, ryf);
     e = cudaGetLastError();
   }
   std::vector<double> dv(grid->ny);
@@ -880,7 +1030,7 @@ int s2_set_state(s2_solver *s, const double *w, int where) {
   size_t bytes = NV * (size_t)s->d.n * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(s->d.w, w, bytes, where == S2_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                                   s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.fln, 0, bytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.fln, 0, NV * (size_t)s->d.n * s->rsize, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(&s->d.scal->status, 0, sizeof(int), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_err(e);
@@ -942,14 +1092,15 @@ int s2_rhs(s2_solver *s, double *rhs, int where) {
   if (e != cudaSuccess) return S2_ECUDA;
   unsigned nb = (unsigned)((s->d.n + NT - 1) / NT);
   size_t bytes = NV * (size_t)s->d.n * sizeof(double);
-  // fln is zero between steps and rewritten before it is read: use it as
-  // the staging buffer, then clear it again.
-  double *dst = where == S2_DEVICE ? rhs : s->d.fln;
-  k_rhs_out<<<nb, NT, 0, s->stream>>>(s->d, dst);
+  // FP64: fln is zero between steps and rewritten before it is read, so it
+  // serves as the staging buffer and is cleared again afterwards.
+  double *dst = where == S2_DEVICE ? rhs : s->rhs_stage;
+  if (s->d.mixed) k_rhs_out<float><<<nb, NT, 0, s->stream>>>(s->d, dst);
+  else k_rhs_out<double><<<nb, NT, 0, s->stream>>>(s->d, dst);
   if ((e = cudaGetLastError()) != cudaSuccess) return S2_ECUDA;
   if (where == S2_HOST) {
-    e = cudaMemcpyAsync(rhs, s->d.fln, bytes, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d.fln, 0, bytes, s->stream);
+    e = cudaMemcpyAsync(rhs, s->rhs_stage, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && !s->d.mixed) e = cudaMemsetAsync(s->d.fln, 0, bytes, s->stream);
     if (e != cudaSuccess) return S2_ECUDA;
   }
   return read_status(s);
@@ -970,7 +1121,8 @@ int s2_get_flags(s2_solver *s, unsigned char *fx, unsigned char *fy, unsigned ch
 int s2_stats(s2_solver *s, s2_stats_t *out) {
   if (!s || !out) return S2_EINVAL;
   DeviceGuard guard(s->device);
-  k_stats_partial<<<NRED, NT, 0, s->stream>>>(s->d);
+  if (s->d.mixed) k_stats_partial<float><<<NRED, NT, 0, s->stream>>>(s->d);
+  else k_stats_partial<double><<<NRED, NT, 0, s->stream>>>(s->d);
   if (cudaGetLastError() != cudaSuccess) return S2_ECUDA;
   k_stats_final<<<1, NT, 0, s->stream>>>(s->d, NRED);
   if (cudaGetLastError() != cudaSuccess) return S2_ECUDA;

@@ -22,7 +22,7 @@ S2_OK, S2_EINVAL, S2_ENOMEM, S2_ECUDA, S2_ENONFINITE, S2_ETIMEOUT, S2_EBUSY = 0,
 S2_ETOOBIG = -7
 S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL = 0, 1
 S2_HOST, S2_DEVICE = 0, 1
-S2_FP64 = 0
+S2_FP64, S2_MIXED = 0, 1
 
 
 class S2Error(RuntimeError):
@@ -221,7 +221,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, lx, ly, lz, *, y=None, gamma=1.4, prandtl=0.72, mach=0.1, re=1600.0,
                  visc_exp=0.76, t_ref=1.0, wall_y=False, t_wall=1.0, force=False, weno_order=0,
-                 threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1):
+                 threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1, precision="fp64"):
         self.shape = (5, nz, ny, nx)
         self.n = nx * ny * nz
         grid = s2_grid(nx, ny, nz, lx, ly, lz)
@@ -233,7 +233,8 @@ class Solver:
         gas = s2_gas(gamma, prandtl, mach, re, visc_exp, t_ref)
         bcs = s2_bcs(S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL if wall_y else S2_BC_PERIODIC, S2_BC_PERIODIC,
                      t_wall, 1 if force else 0)
-        sch = s2_scheme(6, weno_order, 6, threshold, S2_FP64, cfl, dt_fixed, dt_every)
+        prec = {"fp64": S2_FP64, "mixed": S2_MIXED}[precision]
+        sch = s2_scheme(6, weno_order, 6, threshold, prec, cfl, dt_fixed, dt_every)
         dev = s2_device()
         dev.stream = stream
         dev.device = device
