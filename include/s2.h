@@ -160,6 +160,14 @@ int s2_step(s2_solver *s, int n);
 /* Wait for the solver's stream; returns the device status. */
 int s2_sync(s2_solver *s);
 
+/* Flux tile shape per direction: tiles[d] = 0 (default: 64x4 points for x,
+ * 32x8 for y and z) or 1 (narrower along the direction: 32x8 for x, 16x16
+ * for y and z, for small boxes).  Chosen per grid by the autotuner
+ * (paper_2304_05494_gb300/autotune.py, the tile knobs of the paper's
+ * launch-bounds study, Table 3).  Takes effect at the next s2_step; batches
+ * created earlier keep the previous choice.  Results do not depend on it. */
+int s2_set_tiles(s2_solver *s, const int *tiles);
+
 /* Restore the clock (for a restart from a saved state). */
 int s2_set_clock(s2_solver *s, double t, long long step, double dt);
 
@@ -206,6 +214,25 @@ const char *s2_profile_name(int kind);
 
 /* Release everything; NULL is accepted. */
 void s2_destroy(s2_solver *s);
+
+/* Batched stepping, for many independent boxes (ensembles, serving).  A
+ * batch groups count distinct solvers created on the same device;
+ * s2_batch_step advances every member by n RK3 steps, each step one CUDA
+ * graph launch in which the members' kernel sequences are independent
+ * branches that the GPU runs concurrently, so that boxes too small to fill
+ * the GPU alone (the paper finds ~2M points are needed, Sec. 4.1) fill it
+ * together.  Members keep their own state, parameters, streams and clocks;
+ * no buffer is shared, so a member's results are the same alone and in a
+ * batch.  stream: the batch's cudaStream_t, or NULL for a private one.
+ * s2_batch_create waits for the members' pending work.  s2_batch_step is
+ * asynchronous on the batch stream; s2_batch_sync waits for it and returns
+ * the first member error.  Do not step a member on its own while its batch
+ * is in flight, and destroy the batch before any of its members. */
+typedef struct s2_batch s2_batch;
+int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out);
+int s2_batch_step(s2_batch *b, int n);
+int s2_batch_sync(s2_batch *b);
+void s2_batch_destroy(s2_batch *b);
 
 /* Allocation-free CFL time step.  The paper has no counterpart: this entry
  * point serves callers that must not allocate device memory when they need

@@ -36,27 +36,42 @@ __device__ __forceinline__ constexpr R ka(int l) {
   return l == 1 ? R(3.0 / 4.0) : (l == 2 ? R(-3.0 / 20.0) : R(1.0 / 60.0));
 }
 
-template <int DIR>
+// Tile shapes (L points along the direction x W pencils, 256 threads):
+// variant 0 is the default; variant 1 is narrower along the direction for
+// small boxes.  The autotuner picks one per direction and grid.
+template <int DIR, int V>
 struct Tile;
 template <>
-struct Tile<0> {  // x: 64 along x, 4 rows (y)
+struct Tile<0, 0> {  // x: 64 along x, 4 rows (y)
   static constexpr int L = 64, W = 4;
 };
 template <>
-struct Tile<1> {  // y: 32 along y, 8 columns (x)
+struct Tile<0, 1> {  // x: 32 along x, 8 rows
   static constexpr int L = 32, W = 8;
 };
 template <>
-struct Tile<2> {  // z: 32 along z, 8 columns (x)
+struct Tile<1, 0> {  // y: 32 along y, 8 columns (x)
   static constexpr int L = 32, W = 8;
+};
+template <>
+struct Tile<1, 1> {  // y: 16 along y, 16 columns
+  static constexpr int L = 16, W = 16;
+};
+template <>
+struct Tile<2, 0> {  // z: 32 along z, 8 columns (x)
+  static constexpr int L = 32, W = 8;
+};
+template <>
+struct Tile<2, 1> {  // z: 16 along z, 16 columns
+  static constexpr int L = 16, W = 16;
 };
 
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
-template <int DIR, int WR, class R>
+template <int DIR, int WR, class R, int TV>
 __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
-  constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
+  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   constexpr int LE = L + 2 * GH;       // extended positions per pencil
   constexpr int SF = LE * W;           // doubles per shared field
   constexpr int LT = L + 3;            // pair-flux positions a = -3 .. L-1
@@ -415,21 +430,26 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
   }
 }
 
-template <int DIR, class R>
+template <int DIR, class R, int TV>
 constexpr size_t flux_smem() {
-  constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
+  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)15 * (L + 3) * W);
 }
 
-template <int DIR, int WR, class R>
+template <int DIR, int WR, class R, int TV>
 cudaError_t launch_one(const Dev &d, int accumulate, cudaStream_t st) {
-  constexpr int L = Tile<DIR>::L, W = Tile<DIR>::W;
+  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   dim3 grid;
   if (DIR == 0) grid = dim3((d.nx + L - 1) / L, (d.ny + W - 1) / W, d.nz);
   if (DIR == 1) grid = dim3((d.nx + W - 1) / W, (d.ny + L - 1) / L, d.nz);
   if (DIR == 2) grid = dim3((d.nx + W - 1) / W, (d.nz + L - 1) / L, d.ny);
-  k_flux<DIR, WR, R><<<grid, NTHREADS, flux_smem<DIR, R>(), st>>>(d, accumulate);
+  k_flux<DIR, WR, R, TV><<<grid, NTHREADS, flux_smem<DIR, R, TV>(), st>>>(d, accumulate);
   return cudaGetLastError();
+}
+
+template <int DIR, int WR, class R>
+cudaError_t launch_tv(const Dev &d, int accumulate, cudaStream_t st) {
+  return d.tile[DIR] ? launch_one<DIR, WR, R, 1>(d, accumulate, st) : launch_one<DIR, WR, R, 0>(d, accumulate, st);
 }
 
 template <int DIR, int WR, class R>
@@ -447,23 +467,26 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
 
 template <int DIR, int WR, class R>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_flux<DIR, WR, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)flux_smem<DIR, R>());
+  cudaError_t e = cudaFuncSetAttribute(k_flux<DIR, WR, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)flux_smem<DIR, R, 0>());
+  cudaError_t e1 = cudaFuncSetAttribute(k_flux<DIR, WR, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)flux_smem<DIR, R, 1>());
+  return e != cudaSuccess ? e : e1;
 }
 
 template <class R>
 cudaError_t flux_dispatch(const Dev &d, int dir, int accumulate, cudaStream_t st) {
   int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
   switch (dir * 10 + wr) {
-    case 0: return launch_one<0, 0, R>(d, accumulate, st);
-    case 3: return launch_one<0, 3, R>(d, accumulate, st);
-    case 4: return launch_one<0, 4, R>(d, accumulate, st);
-    case 10: return launch_one<1, 0, R>(d, accumulate, st);
-    case 13: return launch_one<1, 3, R>(d, accumulate, st);
-    case 14: return launch_one<1, 4, R>(d, accumulate, st);
-    case 20: return launch_one<2, 0, R>(d, accumulate, st);
-    case 23: return launch_one<2, 3, R>(d, accumulate, st);
-    case 24: return launch_one<2, 4, R>(d, accumulate, st);
+    case 0: return launch_tv<0, 0, R>(d, accumulate, st);
+    case 3: return launch_tv<0, 3, R>(d, accumulate, st);
+    case 4: return launch_tv<0, 4, R>(d, accumulate, st);
+    case 10: return launch_tv<1, 0, R>(d, accumulate, st);
+    case 13: return launch_tv<1, 3, R>(d, accumulate, st);
+    case 14: return launch_tv<1, 4, R>(d, accumulate, st);
+    case 20: return launch_tv<2, 0, R>(d, accumulate, st);
+    case 23: return launch_tv<2, 3, R>(d, accumulate, st);
+    case 24: return launch_tv<2, 4, R>(d, accumulate, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -23,6 +23,7 @@ struct Scal {
   unsigned int nlist[4];  // per-direction lengths of the flagged-interface lists
   int status;             // 0 or the first error code met
   int pad;
+  long long nstep;        // completed RK3 steps (decides the dt recomputation on the device)
   double red[8];          // results of the last stats reduction
 };
 
@@ -54,9 +55,11 @@ struct Dev {
   int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
   double thr;              // sensor threshold
   double cfl;
+  int dt_every;            // recompute dt at steps that are multiples of this (cfl > 0)
   double vol_inv;          // 1 / sum(dV) / (dx dz) for the forcing
   int viscous, wall_y, weno, force;
   int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
+  int tile[3];             // flux tile variant per direction (0 default, 1 narrow)
   Consts<double> kd;
   Consts<float> kf;
   // state (FP64 in both modes; interior layout [v][k][j][i])
@@ -194,6 +197,12 @@ __host__ __device__ inline long long islot(const Dev &d, int dir, int s, int i, 
 // Single-precision power law mu = (T/T_ref)^omega / Re of the mixed path.
 __device__ __forceinline__ float viscosity(const Dev &d, float T) {
   return powf(T * d.kf.inv_t_ref, d.kf.visc_exp) / d.kf.re;
+}
+
+// Whether the CFL dt is recomputed at the step now starting (read on the
+// device from the step counter, so one captured graph serves every step).
+__device__ __forceinline__ bool dt_due(const Dev &d) {
+  return d.cfl > 0.0 && (d.scal->nstep % d.dt_every) == 0;
 }
 
 // Launch helpers (defined in the kernel translation units).

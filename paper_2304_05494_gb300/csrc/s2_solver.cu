@@ -141,9 +141,10 @@ __device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_d
 // rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v, p = rho R T,
 // H = c_p T + |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the
 // CFL spectral radius max into part[block] (c = sqrt(gamma R T)).
-__global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
+__global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<double> V = view<double>(d);
+  const int want_dt = stage0 && dt_due(d);
   double sr = 0.0;
   if (q < d.n) {
     int i, j, k;
@@ -180,9 +181,10 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int want_dt) {
 // temperature carries the pressure), with 1/rho from a single-precision
 // reciprocal refined by one Newton step; everything stored is single
 // precision, as is the rest of the arithmetic.
-__global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int want_dt) {
+__global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<float> V = view<float>(d);
+  const int want_dt = stage0 && dt_due(d);
   const Consts<float> &K = d.kf;
   double sr = 0.0;
   if (q < d.n) {
@@ -225,8 +227,10 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int want_dt) {
   dt_block_max(d, sr, want_dt);
 }
 
-// dt = cfl / max(spectral radius) over the partials of k_prims.
+// dt = cfl / max(spectral radius) over the partials of k_prims, at the
+// steps where it is due (no-op otherwise).
 __global__ void k_dt_final(Dev d, int nparts) {
+  if (!dt_due(d)) return;
   double m = 0.0;
   for (int b = threadIdx.x; b < nparts; b += NT) m = fmax(m, d.part[b]);
   __shared__ double red[NT / 32];
@@ -394,7 +398,10 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
       if (stage < 2) V.fln[o] = b * R;
     }
   }
-  if (stage == 2 && q == 0) d.scal->t += dt;
+  if (stage == 2 && q == 0) {
+    d.scal->t += dt;
+    d.scal->nstep += 1;
+  }
 }
 
 // Mixed path: the increment dt gamma_k R + fln is formed in single
@@ -424,7 +431,10 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
       if (stage < 2) V.fln[o] = b * R;
     }
   }
-  if (stage == 2 && q == 0) d.scal->t += dt;
+  if (stage == 2 && q == 0) {
+    d.scal->t += dt;
+    d.scal->nstep += 1;
+  }
 }
 
 // R = fl + forcing into out (diagnostics, double).
@@ -506,12 +516,12 @@ struct s2_solver {
   std::vector<void *> blocks;
   long long step;
   int nparts_prims;
-  cudaGraphExec_t graph[2];
-  bool graph_ready[2];
+  cudaGraphExec_t graph;
+  bool graph_ready;
   bool graph_disabled;
   int last_status;
   size_t flag_bytes[3];
-  long long launches_per_step[2];
+  long long launches_per_step;
   long long launches;
   size_t rsize;         // bytes of the arithmetic type (8 FP64, 4 mixed)
   double *rhs_stage;    // staging of s2_rhs output
@@ -535,8 +545,7 @@ void *dalloc(s2_solver *s, size_t bytes) {
 }
 
 void release(s2_solver *s) {
-  for (int g = 0; g < 2; ++g)
-    if (s->graph_ready[g]) cudaGraphExecDestroy(s->graph[g]);
+  if (s->graph_ready) cudaGraphExecDestroy(s->graph);
   for (void *p : s->blocks) {
     if (s->dev.free) s->dev.free(p, s->dev.ctx);
     else cudaFree(p);
@@ -576,7 +585,7 @@ cudaError_t run(Trace *tr, cudaStream_t st, int kind, int nkernels, F f) {
 }
 
 // One RHS evaluation (all terms up to the forcing reduction).
-cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
+cudaError_t enqueue_rhs(s2_solver *s, int stage0, Trace *tr) {
   const Dev &d = s->d;
   cudaStream_t st = s->stream;
   cudaError_t e;
@@ -584,12 +593,12 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
   long long nghost = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
   unsigned ngb = (unsigned)((nghost + NT - 1) / NT);
   e = run(tr, st, S2_PROF_PRIMS, 1, [&] {
-    if (d.mixed) k_prims_mixed<<<nb, NT, 0, st>>>(d, want_dt);
-    else k_prims<<<nb, NT, 0, st>>>(d, want_dt);
+    if (d.mixed) k_prims_mixed<<<nb, NT, 0, st>>>(d, stage0);
+    else k_prims<<<nb, NT, 0, st>>>(d, stage0);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
-  if (want_dt) {
+  if (stage0 && d.cfl > 0.0) {
     e = run(tr, st, S2_PROF_DT, 1, [&] {
       k_dt_final<<<1, NT, 0, st>>>(d, (int)nb);
       return cudaGetLastError();
@@ -649,12 +658,12 @@ cudaError_t enqueue_rhs(s2_solver *s, int want_dt, Trace *tr) {
   return cudaSuccess;
 }
 
-cudaError_t enqueue_step(s2_solver *s, int want_dt, Trace *tr) {
+cudaError_t enqueue_step(s2_solver *s, Trace *tr) {
   const Dev &d = s->d;
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
   cudaError_t e;
   for (int st = 0; st < 3; ++st) {
-    if ((e = enqueue_rhs(s, st == 0 ? want_dt : 0, tr)) != cudaSuccess) return e;
+    if ((e = enqueue_rhs(s, st == 0, tr)) != cudaSuccess) return e;
     e = run(tr, s->stream, S2_PROF_UPDATE, 1, [&] {
       if (d.mixed) k_update_mixed<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
       else k_update<<<nb, NT, 0, s->stream>>>(d, RK_G[st], RK_R[st + 1], st);
@@ -671,14 +680,14 @@ long long total(const Trace &t) {
   return c;
 }
 
-int build_graph(s2_solver *s, int variant) {
+int build_graph(s2_solver *s) {
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
   Trace tr;
-  cudaError_t e = enqueue_step(s, variant, &tr);
+  cudaError_t e = enqueue_step(s, &tr);
   cudaError_t e2 = cudaStreamEndCapture(s->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -692,9 +701,9 @@ int build_graph(s2_solver *s, int variant) {
     return -1;
   }
   cudaGraphDestroy(g);
-  s->graph[variant] = ex;
-  s->graph_ready[variant] = true;
-  s->launches_per_step[variant] = total(tr);
+  s->graph = ex;
+  s->graph_ready = true;
+  s->launches_per_step = total(tr);
   return 0;
 }
 
@@ -860,6 +869,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.t_wall = bcs->t_wall;
   d.thr = scheme->sensor_threshold;
   d.cfl = scheme->cfl;
+  d.dt_every = s->sch.dt_every;
   d.wall_y = bcs->y == S2_BC_ISOTHERMAL_WALL;
   d.weno = scheme->weno_order;
   d.force = bcs->force_mass_flow ? 1 : 0;
@@ -1050,15 +1060,14 @@ int s2_step(s2_solver *s, int n) {
   if (!s || n < 0) return S2_EINVAL;
   DeviceGuard guard(s->device);
   for (int it = 0; it < n; ++it) {
-    int want_dt = (s->sch.cfl > 0 && (s->step % s->sch.dt_every) == 0) ? 1 : 0;
-    if (!s->graph_disabled && !s->graph_ready[want_dt] && build_graph(s, want_dt) != 0) s->graph_disabled = true;
+    if (!s->graph_disabled && !s->graph_ready && build_graph(s) != 0) s->graph_disabled = true;
     cudaError_t e;
     if (!s->graph_disabled) {
-      e = cudaGraphLaunch(s->graph[want_dt], s->stream);
-      s->launches += s->launches_per_step[want_dt];
+      e = cudaGraphLaunch(s->graph, s->stream);
+      s->launches += s->launches_per_step;
     } else {
       Trace tr;
-      e = enqueue_step(s, want_dt, &tr);
+      e = enqueue_step(s, &tr);
       s->launches += total(tr);
     }
     if (e != cudaSuccess) return S2_ECUDA;
@@ -1073,10 +1082,26 @@ int s2_sync(s2_solver *s) {
   return read_status(s);
 }
 
+int s2_set_tiles(s2_solver *s, const int *tiles) {
+  if (!s || !tiles) return S2_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (tiles[a] != 0 && tiles[a] != 1) return S2_EINVAL;
+  DeviceGuard guard(s->device);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
+  for (int a = 0; a < 3; ++a) s->d.tile[a] = tiles[a];
+  if (s->graph_ready) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph_ready = false;
+  }
+  return S2_OK;
+}
+
 int s2_set_clock(s2_solver *s, double t, long long step, double dt) {
   if (!s || step < 0) return S2_EINVAL;
   DeviceGuard guard(s->device);
   cudaError_t e = cudaMemcpyAsync(&s->d.scal->t, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&s->d.scal->nstep, &step, sizeof(long long), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess && dt > 0)
     e = cudaMemcpyAsync(&s->d.scal->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1154,8 +1179,7 @@ int s2_profile(s2_solver *s, int n, double *ms, long long *launches) {
   tr.timed = true;
   int rc = S2_OK;
   for (int it = 0; it < n && rc == S2_OK; ++it) {
-    int want_dt = (s->sch.cfl > 0 && (s->step % s->sch.dt_every) == 0) ? 1 : 0;
-    if (enqueue_step(s, want_dt, &tr) != cudaSuccess) rc = S2_ECUDA;
+    if (enqueue_step(s, &tr) != cudaSuccess) rc = S2_ECUDA;
     else s->step++;
   }
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) rc = S2_ECUDA;
@@ -1179,6 +1203,156 @@ const char *s2_profile_name(int kind) {
   static const char *names[S2_PROF_KINDS] = {"prims", "dt", "ghost", "grad", "ghost_aux", "flux_x", "flux_y",
                                              "flux_z", "visc", "force", "update", "weno", "apply"};
   return (kind >= 0 && kind < S2_PROF_KINDS) ? names[kind] : nullptr;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Batched stepping: one graph whose branches are the members' steps
+// ======================================================================
+struct s2_batch {
+  std::vector<s2_solver *> members;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  cudaGraphExec_t graph;
+  bool ready;
+  long long launches_per_step;
+  std::vector<long long> member_launches;  // kernels per step of each member
+  std::vector<cudaEvent_t> events;         // fork + one join per member
+};
+
+namespace {
+
+int batch_build(s2_batch *b) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return S2_ECUDA;
+  }
+  cudaError_t e = cudaEventRecord(b->events[0], b->stream);
+  long long total_launches = 0;
+  b->member_launches.assign(b->members.size(), 0);
+  for (size_t m = 0; m < b->members.size() && e == cudaSuccess; ++m) {
+    s2_solver *s = b->members[m];
+    e = cudaStreamWaitEvent(s->stream, b->events[0], 0);
+    Trace tr;
+    if (e == cudaSuccess) e = enqueue_step(s, &tr);
+    total_launches += total(tr);
+    b->member_launches[m] = total(tr);
+    if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + m], s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[1 + m], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return S2_ECUDA;
+  }
+  cudaGraphExec_t ex;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return S2_ECUDA;
+  }
+  b->graph = ex;
+  b->ready = true;
+  b->launches_per_step = total_launches;
+  return S2_OK;
+}
+
+void batch_release(s2_batch *b) {
+  if (b->ready) cudaGraphExecDestroy(b->graph);
+  for (cudaEvent_t ev : b->events)
+    if (ev) cudaEventDestroy(ev);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out) {
+  if (!out || !members || count < 1) return S2_EINVAL;
+  *out = nullptr;
+  int device = members[0] ? members[0]->device : -1;
+  for (int m = 0; m < count; ++m) {
+    if (!members[m] || members[m]->device != device) return S2_EINVAL;
+    for (int k = 0; k < m; ++k)
+      if (members[k] == members[m]) return S2_EINVAL;
+  }
+  s2_batch *b = new (std::nothrow) s2_batch();
+  if (!b) return S2_ENOMEM;
+  DeviceGuard guard(device);
+  b->members.assign(members, members + count);
+  b->device = device;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+    b->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return S2_ECUDA;
+  } else {
+    b->own_stream = true;
+  }
+  b->events.assign(count + 1, nullptr);
+  for (auto &ev : b->events)
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      batch_release(b);
+      delete b;
+      return S2_ECUDA;
+    }
+  // the members' own pending work is ordered before the batch's first step
+  for (s2_solver *s : b->members)
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      batch_release(b);
+      delete b;
+      return S2_ECUDA;
+    }
+  int rc = batch_build(b);
+  if (rc != S2_OK) {
+    batch_release(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return S2_OK;
+}
+
+int s2_batch_step(s2_batch *b, int n) {
+  if (!b || n < 0) return S2_EINVAL;
+  DeviceGuard guard(b->device);
+  for (int it = 0; it < n; ++it) {
+    if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return S2_ECUDA;
+    for (size_t m = 0; m < b->members.size(); ++m) {
+      b->members[m]->step++;
+      b->members[m]->launches += b->member_launches[m];
+    }
+  }
+  return S2_OK;
+}
+
+int s2_batch_sync(s2_batch *b) {
+  if (!b) return S2_EINVAL;
+  DeviceGuard guard(b->device);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return S2_ECUDA;
+  int rc = S2_OK;
+  for (s2_solver *s : b->members) {
+    int r = read_status(s);
+    if (r != S2_OK && rc == S2_OK) rc = r;
+  }
+  return rc;
+}
+
+void s2_batch_destroy(s2_batch *b) {
+  if (!b) return;
+  {
+    DeviceGuard guard(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+  }
+  delete b;
 }
 
 void s2_destroy(s2_solver *s) {

@@ -101,6 +101,16 @@ def _load():
     lib.s2_profile_name.restype = C.c_char_p
     lib.s2_cfl_dt_noalloc.argtypes = [C.POINTER(s2_grid), C.POINTER(s2_gas), P, P, C.c_double, P, P]
     lib.s2_cfl_dt_noalloc.restype = C.c_int
+    lib.s2_batch_create.argtypes = [C.POINTER(P), C.c_int, P, C.POINTER(P)]
+    lib.s2_batch_create.restype = C.c_int
+    lib.s2_batch_step.argtypes = [P, C.c_int]
+    lib.s2_batch_step.restype = C.c_int
+    lib.s2_batch_sync.argtypes = [P]
+    lib.s2_batch_sync.restype = C.c_int
+    lib.s2_batch_destroy.argtypes = [P]
+    lib.s2_batch_destroy.restype = None
+    lib.s2_set_tiles.argtypes = [P, C.POINTER(C.c_int)]
+    lib.s2_set_tiles.restype = C.c_int
     lib.s2_strerror.argtypes = [C.c_int]
     lib.s2_strerror.restype = C.c_char_p
     for f in ("s2_set_state", "s2_get_state", "s2_step", "s2_sync", "s2_set_clock", "s2_stats", "s2_rhs",
@@ -171,6 +181,11 @@ def s2_set_clock(h, t: float, step: int, dt: float) -> None:
     _check(_lib.s2_set_clock(h, t, step, dt), "s2_set_clock")
 
 
+def s2_set_tiles(h, tiles) -> None:
+    arr = (C.c_int * 3)(*[int(t) for t in tiles])
+    _check(_lib.s2_set_tiles(h, arr), "s2_set_tiles")
+
+
 def s2_stats(h) -> dict:
     st = s2_stats_t()
     rc = _lib.s2_stats(h, C.byref(st))
@@ -210,6 +225,56 @@ def s2_cfl_dt_noalloc(grid, gas, w, eta_y, cfl: float, dt, stream=None) -> int:
     Returns the status code (no exception, so callers can test it)."""
     return _lib.s2_cfl_dt_noalloc(C.byref(grid), C.byref(gas), w.data_ptr(),
                                   eta_y.data_ptr() if eta_y is not None else None, cfl, dt.data_ptr(), stream)
+
+
+def s2_batch_create(handles, stream=None):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    b = C.c_void_p()
+    _check(_lib.s2_batch_create(arr, len(handles), stream, C.byref(b)), "s2_batch_create")
+    return b
+
+
+def s2_batch_step(b, n: int) -> None:
+    _check(_lib.s2_batch_step(b, int(n)), "s2_batch_step")
+
+
+def s2_batch_sync(b) -> None:
+    _check(_lib.s2_batch_sync(b), "s2_batch_sync")
+
+
+def s2_batch_destroy(b) -> None:
+    _lib.s2_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper of a batch of solvers (destroyed before its members)."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        self.b = s2_batch_create([sv.h for sv in self.solvers], stream)
+
+    def step(self, n: int = 1):
+        s2_batch_step(self.b, n)
+
+    def sync(self):
+        s2_batch_sync(self.b)
+
+    def close(self):
+        if self.b:
+            s2_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def s2_destroy(h) -> None:
@@ -263,6 +328,9 @@ class Solver:
 
     def sync(self):
         s2_sync(self.h)
+
+    def set_tiles(self, tiles):
+        s2_set_tiles(self.h, tiles)
 
     def set_clock(self, t, step, dt):
         s2_set_clock(self.h, t, step, dt)

@@ -1,0 +1,242 @@
+"""Continuous-batching serving loop for ensembles of independent box solves.
+
+Requests (periodic boxes: Taylor-Green or seeded decaying turbulence, of
+different sizes, Mach and Reynolds numbers, step counts and precisions)
+arrive over time.  The server admits a request as soon as a slot and enough
+device memory are free, keeps its state resident on the GPU, and advances
+all admitted boxes together: each tick is one s2_batch_step, a single CUDA
+graph launch whose branches are the members' RK3 steps, so boxes too small
+to fill the GPU alone fill it together.  Requests that arrive while others
+are running join at the next tick; finished ones leave and free their slot
+and memory.  Each box's arithmetic is independent of the others (no shared
+buffers, deterministic kernels), so a result is the same alone and in the
+mix.
+
+Reported: throughput (point-steps/s over the run), p50/p99 of the per-step
+latency seen by requests (tick time / steps per tick), queueing delay.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import workloads as W
+
+SIZES = (32, 48, 64, 96, 128)
+# device bytes per grid point (state, registers, padded primitives,
+# gradients, hybrid-scheme lists), measured from s2_create's allocations
+BYTES_PER_POINT = {"fp64": 560, "mixed": 330}
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    mach: float
+    re: float
+    steps: int
+    kind: str          # "tgv" or "turb"
+    precision: str     # "fp64" or "mixed"
+    seed: int
+    arrival: float = 0.0
+    # filled by the server
+    admitted: Optional[float] = None
+    finished: Optional[float] = None
+    result: Optional[np.ndarray] = field(default=None, repr=False)
+
+    @property
+    def points(self) -> int:
+        return self.n ** 3
+
+
+def make_requests(count: int, seed: int = 4321, sizes=SIZES, steps=(100, 1000), precisions=("mixed",),
+                  mach=(0.1, 0.8), re=(400.0, 3200.0), kinds=("tgv", "turb")) -> List[Request]:
+    """The serving workload: sizes, Mach, Re, step counts and case kinds
+    drawn uniformly from the given ranges (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        out.append(Request(rid=i, n=int(rng.choice(sizes)), mach=float(rng.uniform(*mach)),
+                           re=float(rng.uniform(*re)), steps=int(rng.integers(steps[0], steps[1] + 1)),
+                           kind=str(rng.choice(kinds)), precision=str(rng.choice(precisions)),
+                           seed=int(rng.integers(0, 2 ** 31 - 1))))
+    return out
+
+
+def poisson_arrivals(reqs: List[Request], rate: float, seed: int = 99) -> None:
+    """Exponential inter-arrival times with the given rate (requests/s)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for r in reqs:
+        r.arrival = t
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+
+
+def initial_case(req: Request) -> W.Case:
+    if req.kind == "tgv":
+        c = W.taylor_green(req.n, mach=req.mach, re=req.re, seed=req.seed)
+    else:
+        c = W.isotropic(req.n, mach_t=req.mach, re_lambda=0.0, seed=req.seed, weno_order=5)
+        c.re = req.re
+    c.weno_order = 5
+    c.threshold = 0.2
+    c.cfl = 0.8
+    c.dt_every = 10
+    return c
+
+
+class Server:
+    def __init__(self, hbm_budget: Optional[float] = None, max_slots: int = 64, steps_per_tick: int = 10,
+                 keep_results: bool = False, stream=None):
+        import torch
+        from . import s2
+        self.s2 = s2
+        self.torch = torch
+        if hbm_budget is None:
+            free, total = torch.cuda.mem_get_info()
+            hbm_budget = 0.8 * free
+        self.budget = hbm_budget
+        self.max_slots = max_slots
+        self.k = steps_per_tick
+        self.keep = keep_results
+        self.stream = stream
+
+    def _bytes(self, req: Request) -> float:
+        n = req.n
+        return BYTES_PER_POINT[req.precision] * (n + 8) ** 3
+
+    def run(self, reqs: List[Request], log=None) -> dict:
+        s2 = self.s2
+        pending = sorted(reqs, key=lambda r: r.arrival)
+        active = []           # (req, solver, remaining)
+        used = 0.0
+        batch = None
+        changed = False
+        lat = []              # (per-step latency seconds, weight = active boxes)
+        ticks = 0
+        done_points = 0
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            # admission: arrived requests, while a slot and memory are free
+            while pending and pending[0].arrival <= now and len(active) < self.max_slots \
+                    and used + self._bytes(pending[0]) <= self.budget:
+                r = pending.pop(0)
+                c = initial_case(r)
+                sv = s2.Solver.from_case(c, precision=r.precision, stream=None)
+                sv.set_state(c.w0)
+                active.append([r, sv, r.steps])
+                used += self._bytes(r)
+                r.admitted = time.perf_counter() - t0
+                changed = True
+            if not active:
+                # idle until the next arrival
+                wait = pending[0].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.05))
+                continue
+            if changed:
+                if batch is not None:
+                    batch.close()
+                batch = s2.Batch([a[1] for a in active], self.stream)
+                changed = False
+            k = min(self.k, min(a[2] for a in active))
+            ts = time.perf_counter()
+            batch.step(k)
+            batch.sync()
+            dt_tick = time.perf_counter() - ts
+            ticks += 1
+            lat.append((dt_tick / k, len(active), k))
+            for a in active:
+                a[2] -= k
+                done_points += a[0].points * k
+            finished = [a for a in active if a[2] == 0]
+            if finished:
+                batch.close()
+                batch = None
+                changed = True
+                for a in finished:
+                    r, sv = a[0], a[1]
+                    if self.keep:
+                        r.result = sv.get_state()
+                    else:
+                        sv.sync()
+                    sv.close()
+                    r.finished = time.perf_counter() - t0
+                    used -= self._bytes(r)
+                    active.remove(a)
+            if log:
+                log(ticks, len(active), len(pending), dt_tick)
+        if batch is not None:
+            batch.close()
+        wall = time.perf_counter() - t0
+        # per-step latency distribution, weighted by the boxes and steps of each tick
+        vals = np.array([l for l, _, _ in lat])
+        wts = np.array([m * k for _, m, k in lat], dtype=float)
+        order = np.argsort(vals)
+        cw = np.cumsum(wts[order]) / max(wts.sum(), 1.0)
+
+        def pct(p):
+            return float(vals[order][np.searchsorted(cw, p)]) if len(vals) else float("nan")
+
+        waits = np.array([r.admitted - r.arrival for r in reqs])
+        return {"requests": len(reqs), "wall_s": wall, "point_steps": done_points,
+                "throughput": done_points / wall, "ticks": ticks,
+                "p50_step_latency_ms": pct(0.5) * 1e3, "p99_step_latency_ms": pct(0.99) * 1e3,
+                "p50_queue_s": float(np.percentile(waits, 50)), "p99_queue_s": float(np.percentile(waits, 99))}
+
+
+def capacity(precision: str, sizes=SIZES, steps: int = 10) -> float:
+    """Point-steps/s of a full batch of one box of each size (the rate the
+    arrival process is tuned against)."""
+    from . import s2
+    reqs = [Request(rid=i, n=n, mach=0.4, re=1600.0, steps=steps, kind="tgv", precision=precision, seed=i)
+            for i, n in enumerate(sizes)]
+    solvers = []
+    for r in reqs:
+        c = initial_case(r)
+        sv = s2.Solver.from_case(c, precision=precision)
+        sv.set_state(c.w0)
+        solvers.append(sv)
+    with s2.Batch(solvers) as b:
+        b.step(2)
+        b.sync()
+        t = time.perf_counter()
+        b.step(steps)
+        b.sync()
+        el = time.perf_counter() - t
+    for sv in solvers:
+        sv.close()
+    return sum(r.points for r in reqs) * steps / el
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--load", type=float, default=0.8, help="arrival rate as a fraction of capacity")
+    ap.add_argument("--min-steps", type=int, default=100)
+    ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--steps-per-tick", type=int, default=10)
+    args = ap.parse_args(argv)
+    cap = capacity(args.precision)
+    reqs = make_requests(args.requests, steps=(args.min_steps, args.max_steps), precisions=(args.precision,))
+    mean_work = np.mean([r.points * r.steps for r in reqs])
+    rate = args.load * cap / mean_work
+    poisson_arrivals(reqs, rate)
+    out = Server(max_slots=args.slots, steps_per_tick=args.steps_per_tick).run(reqs)
+    out.update({"precision": args.precision, "capacity": cap, "arrival_rate": rate, "load": args.load})
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -213,3 +213,48 @@ def double_sod(n: int, L: float = 2.0):
     z = np.zeros_like(x)
     w0 = conserved(rho, z, z, z, T, gamma, mach).reshape(5, 1, 1, n)
     return np.ascontiguousarray(w0), x, mach
+
+
+def isotropic(n: int = 512, mach_t: float = 0.6, re_lambda: float = 100.0, k0: float = 4.0,
+              seed: int = SEED_BASE + 2, weno_order: int = 7) -> Case:
+    """Decaying compressible isotropic turbulence on the periodic [0, 2 pi]^3:
+    a seeded random-phase solenoidal velocity with energy spectrum
+    E(k) ~ k^4 exp(-2 (k/k0)^2), scaled to the turbulent Mach number
+    M_t = sqrt(<u.u>)/c = mach_t, with uniform density and temperature
+    (rho = T = 1, reference Mach 1 so that c = 1).  Re follows from
+    Re_lambda = u' lambda / nu with u' = sqrt(<u.u>/3) and the Taylor
+    microscale of the initial spectrum."""
+    L = 2.0 * np.pi
+    rng = np.random.default_rng(seed)
+    k1 = np.fft.fftfreq(n, d=1.0 / n)
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(kx * kx + ky * ky + kz * kz)
+    kk[0, 0, 0] = 1.0
+    # random complex vector field, projected onto the solenoidal subspace
+    comps = [rng.normal(size=kk.shape) + 1j * rng.normal(size=kk.shape) for _ in range(3)]
+    kdot = (kx * comps[0] + ky * comps[1] + kz * comps[2]) / (kk * kk)
+    comps = [comps[0] - kx * kdot, comps[1] - ky * kdot, comps[2] - kz * kdot]
+    amp = np.sqrt(kk ** 4 * np.exp(-2.0 * (kk / k0) ** 2) / (4.0 * np.pi * kk * kk))
+    amp[0, 0, 0] = 0.0
+    vel = []
+    for c in comps:
+        f = np.fft.ifftn(c * amp).real
+        vel.append(f)
+    del comps, kdot
+    u2 = np.mean(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2)
+    gamma = 1.4
+    mach_ref = 1.0
+    c0 = 1.0 / mach_ref  # sound speed at T = 1 in reference units
+    scale = mach_t * c0 / np.sqrt(u2)
+    vel = [v * scale for v in vel]
+    # Taylor microscale from the discrete velocity gradient
+    dudx = np.gradient(vel[0], L / n, axis=2)
+    uprime = np.sqrt(np.mean(vel[0] ** 2 + vel[1] ** 2 + vel[2] ** 2) / 3.0)
+    lam = uprime / np.sqrt(np.mean(dudx * dudx))
+    del dudx
+    re = re_lambda / (uprime * lam)  # nu = 1/Re at rho = T = 1
+    one = np.ones_like(vel[0])
+    w0 = conserved(one, vel[0], vel[1], vel[2], one, gamma, mach_ref)
+    return Case("isotropic_%d" % n, n, n, n, L, L, L, w0, gamma=gamma, mach=mach_ref, re=re,
+                visc_exp=0.76, prandtl=0.72, weno_order=weno_order, threshold=0.2, cfl=0.8, steps=100,
+                extra={"mach_t": mach_t, "re_lambda": re_lambda, "uprime": uprime, "lambda": lam})
