@@ -77,9 +77,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int LT = L + 3;            // pair-flux positions a = -3 .. L-1
   constexpr int ST = LT * W;           // doubles per pair-flux slot
   constexpr int NFLD = WR > 0 ? NF : F_S;  // the sensor is staged only for WENO
+  // Shared layouts: for x the position index runs fastest (threads walk
+  // along x, as the global rows do); for y and z the pencil index runs
+  // fastest (threads walk across x).  Either way consecutive threads touch
+  // consecutive words: no bank conflicts.
+  constexpr int SA = DIR == 0 ? 1 : W;    // stride between positions
+  constexpr int SCS = DIR == 0 ? LE : 1;  // stride between pencils in S
+  constexpr int SCT = DIR == 0 ? LT : 1;  // stride between pencils in TP
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *S = (R *)smem_raw;                // [NF][LE][W]
-  R *TP = S + NF * SF;                 // [3][5][LT][W]
+  R *S = (R *)smem_raw;                // [NF][positions x pencils]
+  R *TP = S + NF * SF;                 // [3][5][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
 
@@ -109,24 +116,26 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
       else g = pidx(d, x0 + cc, y0, s);
     }
 #pragma unroll
-    for (int f = 0; f < NFLD; ++f) S[f * SF + a * W + cc] = ok ? __ldg(src[f] + g) : R(1);
+    for (int f = 0; f < NFLD; ++f) S[f * SF + a * SA + cc * SCS] = ok ? __ldg(src[f] + g) : R(1);
   }
   __syncthreads();
 
   // ---- 2. pair fluxes T_l(a), a = -3 .. L-1 ----
   for (int idx = tid; idx < ST; idx += NTHREADS) {
-    int a = idx / W, cc = idx % W;        // a in 0..LT-1 <-> position a-3
+    int a, cc;                            // a in 0..LT-1 <-> position a-3
+    if (DIR == 0) { a = idx % LT; cc = idx / LT; }
+    else { a = idx / W; cc = idx % W; }
     int ae = a - 3 + GH;                  // extended index of the position
     const R *Sr = S + F_RHO * SF, *Su = S + F_U * SF, *Sv = S + F_V * SF, *Sw = S + F_W * SF, *Sh = S + F_H * SF;
-    int q0 = ae * W + cc;
+    int q0 = ae * SA + cc * SCS;
     R r0 = Sr[q0], u0 = Su[q0], v0 = Sv[q0], w0 = Sw[q0], h0 = Sh[q0];
 #pragma unroll
     for (int l = 1; l <= 3; ++l) {
-      int q1 = q0 + l * W;
+      int q1 = q0 + l * SA;
       R su = u0 + Su[q1], sv = v0 + Sv[q1], sw = w0 + Sw[q1];
       R sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
       R m = (r0 + Sr[q1]) * sun;
-      R *T = TP + ((l - 1) * 5) * ST + idx;
+      R *T = TP + ((l - 1) * 5) * ST + a * SA + cc * SCT;
       T[0] = m;
       T[ST] = m * su;
       T[2 * ST] = m * sv;
@@ -149,7 +158,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
       bool flag = false;
       long long slot = 0;
       if (idx < NI) {
-        int a = idx / W - 1, cc = idx % W;
+        int a, cc;
+        if (DIR == 0) { a = idx % (L + 1) - 1; cc = idx / (L + 1); }
+        else { a = idx / W - 1; cc = idx % W; }
         int s = s0 + a;
         bool own = (c0 + cc < nac) && s <= n - 1 && (a >= 0 || s == -1);
         if (own) {
@@ -158,7 +169,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
           decltype(order_bits(R(0))) mx = 0;
 #pragma unroll
           for (int m = -WR + 1; m <= WR; ++m) {
-            auto b = order_bits(Ss[(a + m + GH) * W + cc]);
+            auto b = order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
             mx = b > mx ? b : mx;
           }
           flag = K.thr < R(0) || mx > thr_bits;
@@ -191,22 +202,22 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
     const R c1[4] = {R(0), R(0.5 * 0.75), R(0.5 * -0.15), R(0.5 * (1.0 / 60.0))};
     const R c2[4] = {R(0), R(0.25 * 0.75), R(0.25 * -0.15), R(0.25 * (1.0 / 60.0))};
     R D[5];
-    int at = (a + 3) * W + cc;
+    int at = (a + 3) * SA + cc * SCT;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       R acc = R(0);
 #pragma unroll
       for (int l = 1; l <= 3; ++l) {
         const R *T = TP + ((l - 1) * 5 + f) * ST;
-        acc = fma(f == 0 ? c1[l] : c2[l], T[at] - T[at - l * W], acc);
+        acc = fma(f == 0 ? c1[l] : c2[l], T[at] - T[at - l * SA], acc);
       }
       D[f] = acc;
     }
     const R *Sp = S + F_P * SF;
-    int ap = (a + GH) * W + cc;
+    int ap = (a + GH) * SA + cc * SCS;
     R dp = R(0);
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) dp = fma(ka<R>(l), Sp[ap + l * W] - Sp[ap - l * W], dp);
+    for (int l = 1; l <= 3; ++l) dp = fma(ka<R>(l), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
     D[1 + DIR] += dp;
     int i = DIR == 0 ? x0 + a : x0 + cc;
     int j = DIR == 0 ? y0 + cc : (DIR == 1 ? y0 + a : y0);

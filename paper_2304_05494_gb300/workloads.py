@@ -258,3 +258,15 @@ def isotropic(n: int = 512, mach_t: float = 0.6, re_lambda: float = 100.0, k0: f
     return Case("isotropic_%d" % n, n, n, n, L, L, L, w0, gamma=gamma, mach=mach_ref, re=re,
                 visc_exp=0.76, prandtl=0.72, weno_order=weno_order, threshold=0.2, cfl=0.8, steps=100,
                 extra={"mach_t": mach_t, "re_lambda": re_lambda, "uprime": uprime, "lambda": lam})
+
+
+def channel_big(seed: int = SEED_BASE + 3, weno_order: int = 5) -> Case:
+    """The large channel: 1024 x 256 x 512 points on 6 pi h x 2h x 2 pi h,
+    Re_tau ~ 550 (Re_b ~ 8400 on the wall viscosity, scaled from the
+    Re_b = 3000 / Re_tau = 222 pair of the M = 1.5 channel with the
+    Re_tau ~ Re_b^0.88 law), first wall cell at dy+ = 0.7."""
+    re_b = 3000.0 * (550.0 / 222.0) ** (1.0 / 0.88)
+    c = channel(1024, 256, 512, re_b=re_b, re_tau=550.0, seed=seed, weno_order=weno_order)
+    c.name = "channel_1024x256x512"
+    c.steps = 100
+    return c

@@ -1,0 +1,60 @@
+"""Full-size parity for the large configurations: the FP64 path against the
+oracle on the whole grid (one RHS evaluation, every point), and the mixed
+path against the FP64 path after a few steps.
+
+Decaying isotropic turbulence at 512^3 with WENO7 (the hybrid flags are
+compared too) and the 1024 x 256 x 512 channel at Re_tau ~ 550.  Both hold
+134M points; the oracle needs ~30 GB of host memory and ~40 s here.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2304_05494_gb300 import workloads as W
+from tests.test_gpu_parity import RHS_TOL, case_kw, field_err, flux_scale
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def s2():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_05494_gb300 import s2 as mod
+    return mod
+
+
+@pytest.fixture(scope="module", params=["isotropic512", "channel1024"])
+def big(request):
+    if request.param == "isotropic512":
+        return W.isotropic(512)
+    return W.channel_big()
+
+
+def test_full_size_rhs_parity_and_mixed(s2, big):
+    c = big
+    kw = case_kw(c)
+    pr = O.Problem(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, **kw)
+    with s2.Solver.from_case(c, cfl=0.8, dt_every=10) as sv:
+        sv.set_state(c.w0)
+        r = sv.rhs()
+        f = sv.flags()
+    ref, of = O.rhs(pr, c.w0, flags=True)
+    S = np.maximum(flux_scale(c.w0, pr), np.max(np.abs(ref), axis=(1, 2, 3)))
+    e = np.max(np.abs(r - ref), axis=(1, 2, 3)) / S
+    print("%s full-size rhs error / flux scale:" % c.name, e)
+    assert np.all(e < RHS_TOL), e
+    for a, b in zip(f, of):
+        assert np.array_equal(a, b)
+    del r, ref
+    # mixed against FP64 on the GPU, 5 steps at CFL 0.8
+    out = {}
+    for prec in ("fp64", "mixed"):
+        with s2.Solver.from_case(c, precision=prec, cfl=0.8, dt_every=10) as sv:
+            sv.set_state(c.w0)
+            sv.step(5)
+            out[prec] = sv.get_state()
+    err = field_err(out["mixed"], out["fp64"])
+    print("%s mixed vs FP64 after 5 steps (field-normalised):" % c.name, err)
+    assert np.all(err < 1e-4), err
