@@ -48,6 +48,7 @@ class _Cfg(C.Structure):
         ("re", C.c_double), ("visc_exp", C.c_double), ("t_ref", C.c_double),
         ("bc_y", C.c_int), ("t_wall", C.c_double),
         ("force", C.c_int), ("weno_order", C.c_int), ("threshold", C.c_double),
+        ("central_order", C.c_int), ("visc_order", C.c_int),
     ]
 
 
@@ -112,8 +113,10 @@ class Problem:
     wall_y: bool = False                 # isothermal no-slip walls at y = -ly/2, +ly/2
     t_wall: float = 1.0
     force: bool = False
-    weno_order: int = 0                  # 0, 5, 7
+    weno_order: int = 0                  # 0, 1, 3, 5, 7
     threshold: float = 0.2
+    central_order: int = 6               # 2, 4, 6, 8
+    visc_order: int = 6                  # 2, 4, 6, 8
     _y_buf: Optional[np.ndarray] = field(default=None, repr=False)
 
     def cfg(self) -> _Cfg:
@@ -135,6 +138,8 @@ class Problem:
         c.force = 1 if self.force else 0
         c.weno_order = self.weno_order
         c.threshold = self.threshold
+        c.central_order = self.central_order
+        c.visc_order = self.visc_order
         return c
 
     @property

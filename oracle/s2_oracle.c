@@ -38,10 +38,21 @@
 #define NV 5
 #define GH 4 /* ghost width of the padded work arrays (WENO7 needs 4) */
 
-/* 6th-order central first derivative: f' = sum_l a_l (f_{i+l} - f_{i-l}) */
-static const double A1[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
-/* 6th-order central second derivative: f'' = b_0 f_i + sum_l b_l (f_{i+l} + f_{i-l}) */
-static const double B2[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+/* Central first derivative of order 2L (L = 1..4, the paper's orders
+ * 2/4/6/8, Sec. 2): f' = sum_{l=1..L} a_l (f_{i+l} - f_{i-l}). */
+static const double A1_ORD[5][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {0.0, 1.0 / 2.0, 0.0, 0.0, 0.0},
+    {0.0, 2.0 / 3.0, -1.0 / 12.0, 0.0, 0.0},
+    {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0, 0.0},
+    {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0}};
+/* Central second derivative of order 2L: f'' = b_0 f_i + sum_l b_l (f_{i+l} + f_{i-l}). */
+static const double B2_ORD[5][5] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0},
+    {-2.0, 1.0, 0.0, 0.0, 0.0},
+    {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0, 0.0, 0.0},
+    {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0, 0.0},
+    {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0}};
 
 /* Wray's low-storage RK3: w_k = w_{k-1} + dt (gamma_k R_{k-1} + rho_k R_{k-2}) */
 static const double RK_GAMMA[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
@@ -59,8 +70,10 @@ typedef struct {
   int bc_y;             /* 0 periodic, 1 isothermal no-slip walls */
   double t_wall;
   int force;            /* 1: uniform x body force keeping the bulk rho*u constant */
-  int weno_order;       /* 0 (central everywhere), 5 or 7 */
+  int weno_order;       /* 0 (central everywhere), 1, 3, 5 or 7 */
   double threshold;     /* interface is WENO iff max sensor over its stencil > threshold */
+  int central_order;    /* 2, 4, 6 or 8: split-form convective flux */
+  int visc_order;       /* 2, 4, 6 or 8: viscous terms and the sensor's derivatives */
 } or_cfg;
 
 /* Which terms or_rhs evaluates. */
@@ -70,6 +83,8 @@ typedef struct {
 
 typedef struct {
   const or_cfg *c;
+  int lc, lv;               /* stencil half-widths: central flux, viscous/sensor */
+  const double *ac, *av, *bv; /* their coefficients */
   int nx, ny, nz, px, py, pz;
   size_t np, n;
   double R, cv, cp, dx, dz, eps_sensor;
@@ -107,10 +122,18 @@ static double ext_y(const or_cfg *c, int j) {
   return 2.0 * (0.5 * c->ly) - node_y(c, 2 * ny - 1 - j);
 }
 
+/* Metric stencils: the higher of the two orders in use. */
+static int metric_half_width(const or_cfg *c) {
+  int o = c->central_order > c->visc_order ? c->central_order : c->visc_order;
+  return o / 2;
+}
+
 void or_metric(const or_cfg *c, double *eta_y, double *eta_yy) {
+  int lm = metric_half_width(c);
+  const double *A1 = A1_ORD[lm], *B2 = B2_ORD[lm];
   for (int j = 0; j < c->ny; ++j) {
     double d1 = 0.0, d2 = B2[0] * ext_y(c, j);
-    for (int l = 1; l <= 3; ++l) {
+    for (int l = 1; l <= lm; ++l) {
       d1 += A1[l] * (ext_y(c, j + l) - ext_y(c, j - l));
       d2 += B2[l] * (ext_y(c, j + l) + ext_y(c, j - l));
     }
@@ -120,9 +143,17 @@ void or_metric(const or_cfg *c, double *eta_y, double *eta_yy) {
 }
 
 /* ------------------------------------------------------------ workspace --- */
+static int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8; }
+
 static int ws_init(ws_t *s, const or_cfg *c) {
   memset(s, 0, sizeof(*s));
   s->c = c;
+  if (!valid_order(c->central_order) || !valid_order(c->visc_order)) return -1;
+  s->lc = c->central_order / 2;
+  s->lv = c->visc_order / 2;
+  s->ac = A1_ORD[s->lc];
+  s->av = A1_ORD[s->lv];
+  s->bv = B2_ORD[s->lv];
   s->nx = c->nx; s->ny = c->ny; s->nz = c->nz;
   s->px = c->nx + 2 * GH; s->py = c->ny + 2 * GH; s->pz = c->nz + 2 * GH;
   s->np = (size_t)s->px * s->py * s->pz;
@@ -236,9 +267,11 @@ static void prims(ws_t *s, const double *w) {
 }
 
 /* ---------------------------------------------------------- derivatives --- */
+/* derivatives of the viscous order (viscous terms and sensor) */
 static double d1(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  const double *A1 = s->av;
   double r = 0.0;
-  for (int l = 1; l <= 3; ++l) {
+  for (int l = 1; l <= s->lv; ++l) {
     if (dir == 0) r += A1[l] * (f[PI(s, i + l, j, k)] - f[PI(s, i - l, j, k)]);
     else if (dir == 1) r += A1[l] * (f[PI(s, i, j + l, k)] - f[PI(s, i, j - l, k)]);
     else r += A1[l] * (f[PI(s, i, j, k + l)] - f[PI(s, i, j, k - l)]);
@@ -250,8 +283,9 @@ static double d1(const ws_t *s, const double *f, int i, int j, int k, int dir) {
 
 /* derivative in index space (no metric) */
 static double d1_idx(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  const double *A1 = s->av;
   double r = 0.0;
-  for (int l = 1; l <= 3; ++l) {
+  for (int l = 1; l <= s->lv; ++l) {
     if (dir == 0) r += A1[l] * (f[PI(s, i + l, j, k)] - f[PI(s, i - l, j, k)]);
     else if (dir == 1) r += A1[l] * (f[PI(s, i, j + l, k)] - f[PI(s, i, j - l, k)]);
     else r += A1[l] * (f[PI(s, i, j, k + l)] - f[PI(s, i, j, k - l)]);
@@ -260,8 +294,9 @@ static double d1_idx(const ws_t *s, const double *f, int i, int j, int k, int di
 }
 
 static double d2(const ws_t *s, const double *f, int i, int j, int k, int dir) {
+  const double *B2 = s->bv;
   double r = B2[0] * f[PI(s, i, j, k)];
-  for (int l = 1; l <= 3; ++l) {
+  for (int l = 1; l <= s->lv; ++l) {
     if (dir == 0) r += B2[l] * (f[PI(s, i + l, j, k)] + f[PI(s, i - l, j, k)]);
     else if (dir == 1) r += B2[l] * (f[PI(s, i, j + l, k)] + f[PI(s, i, j - l, k)]);
     else r += B2[l] * (f[PI(s, i, j, k + l)] + f[PI(s, i, j, k - l)]);
@@ -342,8 +377,22 @@ static void sensor(ws_t *s) {
 #define WENO_EPS 1e-6
 
 /* Candidate values q_k and smoothness indicators beta_k of the r
- * substencils; returns r (0 for an unsupported order). */
+ * substencils; returns r (0 for an unsupported order).  Order 1 is the
+ * first-order upwind value, order 3 the two-stencil WENO3 (same Jiang-Shu
+ * construction). */
 int or_weno_parts(int order, const double *g, double *q, double *b) {
+  if (order == 1) { /* g[0] = f_i */
+    q[0] = g[0];
+    b[0] = 0.0;
+    return 1;
+  }
+  if (order == 3) { /* g[0..2] = f_{i-1} .. f_{i+1} */
+    q[0] = (-g[0] + 3.0 * g[1]) / 2.0;
+    q[1] = (g[1] + g[2]) / 2.0;
+    b[0] = (g[1] - g[0]) * (g[1] - g[0]);
+    b[1] = (g[2] - g[1]) * (g[2] - g[1]);
+    return 2;
+  }
   if (order == 5) { /* g[0..4] = f_{i-2} .. f_{i+2} */
     q[0] = (2.0 * g[0] - 7.0 * g[1] + 11.0 * g[2]) / 6.0;
     q[1] = (-g[1] + 5.0 * g[2] + 2.0 * g[3]) / 6.0;
@@ -384,6 +433,8 @@ int or_weno_parts(int order, const double *g, double *q, double *b) {
 }
 
 /* Optimal (linear) weights d_k. */
+static const double WENO1_D[1] = {1.0};
+static const double WENO3_D[2] = {1.0 / 3.0, 2.0 / 3.0};
 static const double WENO5_D[3] = {0.1, 0.6, 0.3};
 static const double WENO7_D[4] = {1.0 / 35.0, 12.0 / 35.0, 18.0 / 35.0, 4.0 / 35.0};
 
@@ -391,7 +442,7 @@ double or_weno_rec(int order, const double *f) {
   double q[4], b[4];
   int r = or_weno_parts(order, f, q, b);
   if (!r) return NAN;
-  const double *d = r == 3 ? WENO5_D : WENO7_D;
+  const double *d = r == 1 ? WENO1_D : (r == 2 ? WENO3_D : (r == 3 ? WENO5_D : WENO7_D));
   double a[4], sa = 0.0;
   for (int k = 0; k < r; ++k) { a[k] = d[k] / ((WENO_EPS + b[k]) * (WENO_EPS + b[k])); sa += a[k]; }
   double res = 0.0;
@@ -515,9 +566,10 @@ static void weno_flux(const ws_t *s, int dir, int pos, int i, int j, int k, doub
  * enters the normal momentum as sum_l a_l sum_{m<l} (p_a + p_b). */
 static void central_flux(const ws_t *s, int dir, int pos, int i, int j, int k, double *F) {
   const double *un = dir == 0 ? s->u : (dir == 1 ? s->v : s->w);
+  const double *A1 = s->ac;
   for (int f = 0; f < 5; ++f) F[f] = 0.0;
   double fp = 0.0;
-  for (int l = 1; l <= 3; ++l) {
+  for (int l = 1; l <= s->lc; ++l) {
     double acc[5] = {0, 0, 0, 0, 0}, pp = 0.0;
     for (int m = 0; m < l; ++m) {
       size_t a = at(s, dir, pos - m, i, j, k), b = at(s, dir, pos - m + l, i, j, k);
