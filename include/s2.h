@@ -90,8 +90,11 @@ typedef struct {
   int force_mass_flow;
 } s2_bcs;
 
-/* Scheme.  central_order and visc_order: 6.  weno_order: 0 (central
- * everywhere), 5 or 7.  An interface is WENO iff the sensor's maximum over
+/* Scheme (paper Sec. 2: central schemes up to 8th order, WENO up to 7th).
+ * central_order: 2, 4, 6 or 8 for the split-form convective flux;
+ * visc_order: 2, 4, 6 or 8 for the viscous terms and the sensor's
+ * derivatives (the y metric uses the higher of the two).  weno_order: 0
+ * (central everywhere), 1, 3, 5 or 7.  An interface is WENO iff the sensor's maximum over
  * its stencil exceeds sensor_threshold (strictly).  precision: S2_FP64 or
  * S2_MIXED (the sensor then decides in single precision).
  * dt: if cfl > 0 it is recomputed from the CFL condition (compute_dt of

@@ -30,10 +30,14 @@
 namespace s2 {
 namespace {
 
-// 6th-order central coefficients a_l (first derivative), l = 1..3.
-template <class R>
-__device__ __forceinline__ constexpr R ka(int l) {
-  return l == 1 ? R(3.0 / 4.0) : (l == 2 ? R(-3.0 / 20.0) : R(1.0 / 60.0));
+// Central first-derivative coefficients a_l of order 2 NP (l = 1..NP): the
+// split-form flux of order 2 NP uses the same weights (Pirozzoli 2010).
+template <int NP>
+__device__ __forceinline__ constexpr double acoef(int l) {
+  if constexpr (NP == 1) return 1.0 / 2.0;
+  else if constexpr (NP == 2) return l == 1 ? 2.0 / 3.0 : -1.0 / 12.0;
+  else if constexpr (NP == 3) return l == 1 ? 3.0 / 4.0 : (l == 2 ? -3.0 / 20.0 : 1.0 / 60.0);
+  else return l == 1 ? 4.0 / 5.0 : (l == 2 ? -1.0 / 5.0 : (l == 3 ? 4.0 / 105.0 : -1.0 / 280.0));
 }
 
 // Tile shapes (L points along the direction x W pencils, 256 threads):
@@ -69,14 +73,14 @@ struct Tile<2, 1> {  // z: 16 along z, 16 columns
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
-template <int DIR, int WR, class R, int TV>
+template <int DIR, bool HASW, class R, int TV, int NP>
 __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   constexpr int LE = L + 2 * GH;       // extended positions per pencil
-  constexpr int SF = LE * W;           // doubles per shared field
-  constexpr int LT = L + 3;            // pair-flux positions a = -3 .. L-1
-  constexpr int ST = LT * W;           // doubles per pair-flux slot
-  constexpr int NFLD = WR > 0 ? NF : F_S;  // the sensor is staged only for WENO
+  constexpr int SF = LE * W;           // words per shared field
+  constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
+  constexpr int ST = LT * W;           // words per pair-flux slot
+  constexpr int NFLD = HASW ? NF : F_S;  // the sensor is staged only for WENO
   // Shared layouts: for x the position index runs fastest (threads walk
   // along x, as the global rows do); for y and z the pencil index runs
   // fastest (threads walk across x).  Either way consecutive threads touch
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int SCT = DIR == 0 ? LT : 1;  // stride between pencils in TP
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *S = (R *)smem_raw;                // [NF][positions x pencils]
-  R *TP = S + NF * SF;                 // [3][5][positions x pencils]
+  R *TP = S + NF * SF;                 // [NP][5][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
 
@@ -120,17 +124,17 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   }
   __syncthreads();
 
-  // ---- 2. pair fluxes T_l(a), a = -3 .. L-1 ----
+  // ---- 2. pair fluxes T_l(a), a = -NP .. L-1 ----
   for (int idx = tid; idx < ST; idx += NTHREADS) {
-    int a, cc;                            // a in 0..LT-1 <-> position a-3
+    int a, cc;                            // a in 0..LT-1 <-> position a-NP
     if (DIR == 0) { a = idx % LT; cc = idx / LT; }
     else { a = idx / W; cc = idx % W; }
-    int ae = a - 3 + GH;                  // extended index of the position
+    int ae = a - NP + GH;                 // extended index of the position
     const R *Sr = S + F_RHO * SF, *Su = S + F_U * SF, *Sv = S + F_V * SF, *Sw = S + F_W * SF, *Sh = S + F_H * SF;
     int q0 = ae * SA + cc * SCS;
     R r0 = Sr[q0], u0 = Su[q0], v0 = Sv[q0], w0 = Sw[q0], h0 = Sh[q0];
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) {
+    for (int l = 1; l <= NP; ++l) {
       int q1 = q0 + l * SA;
       R su = u0 + Su[q1], sv = v0 + Sv[q1], sw = w0 + Sw[q1];
       R sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
@@ -147,10 +151,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   // ---- 4. flags of the interfaces this tile owns, global list ----
   // A tile owns the interfaces a+1/2 with a in 0..L-1, the first tile of a
   // pencil also the one before its first point (a = -1): every interface
-  // slot 0..n of a pencil is owned exactly once.
-  if constexpr (WR > 0) {
+  // slot 0..n of a pencil is owned exactly once.  The WENO stencil of
+  // interface a+1/2 spans a-r+1 .. a+r (r = (order+1)/2).
+  if constexpr (HASW) {
     const R *Ss = S + F_S * SF;
     const auto thr_bits = order_bits(K.thr);
+    const int wr = (d.weno + 1) / 2;
     constexpr int NI = (L + 1) * W;
     unsigned long long mycount = 0;
     for (int base = 0; base < NI; base += NTHREADS) {
@@ -168,9 +174,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
           // values: max and comparison run on the integer pipe
           decltype(order_bits(R(0))) mx = 0;
 #pragma unroll
-          for (int m = -WR + 1; m <= WR; ++m) {
-            auto b = order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
-            mx = b > mx ? b : mx;
+          for (int m = -3; m <= 4; ++m) {
+            if (m > -wr && m <= wr) {
+              auto b = order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
+              mx = b > mx ? b : mx;
+            }
           }
           flag = K.thr < R(0) || mx > thr_bits;
           if (flag && a >= 0) mycount++;
@@ -199,17 +207,17 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   if (DIR == 0) { a = tid % L; cc = tid / L; }
   else { cc = tid % W; a = tid / W; }
   if ((c0 + cc < nac) && (s0 + a < n)) {
-    const R c1[4] = {R(0), R(0.5 * 0.75), R(0.5 * -0.15), R(0.5 * (1.0 / 60.0))};
-    const R c2[4] = {R(0), R(0.25 * 0.75), R(0.25 * -0.15), R(0.25 * (1.0 / 60.0))};
     R D[5];
-    int at = (a + 3) * SA + cc * SCT;
+    int at = (a + NP) * SA + cc * SCT;
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       R acc = R(0);
 #pragma unroll
-      for (int l = 1; l <= 3; ++l) {
+      for (int l = 1; l <= NP; ++l) {
         const R *T = TP + ((l - 1) * 5 + f) * ST;
-        acc = fma(f == 0 ? c1[l] : c2[l], T[at] - T[at - l * SA], acc);
+        // 2 a_l times the pair means: (rho)(u)(phi) = sums / 8, (rho)(u) = sums / 4
+        const R cl = f == 0 ? R(0.5 * acoef<NP>(l)) : R(0.25 * acoef<NP>(l));
+        acc = fma(cl, T[at] - T[at - l * SA], acc);
       }
       D[f] = acc;
     }
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
     int ap = (a + GH) * SA + cc * SCS;
     R dp = R(0);
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) dp = fma(ka<R>(l), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
+    for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
     D[1 + DIR] += dp;
     int i = DIR == 0 ? x0 + a : x0 + cc;
     int j = DIR == 0 ? y0 + cc : (DIR == 1 ? y0 + a : y0);
@@ -287,9 +295,24 @@ __device__ __forceinline__ R weno7(const R *g) {
   return (a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3) / (a0 + a1 + a2 + a3);
 }
 
+// Order 3: two substencils, d = (1/3, 2/3), beta_k = (undivided difference)^2.
+template <class R>
+__device__ __forceinline__ R weno3(const R *g) {
+  const R eps = R(1e-6);
+  R q0 = R(-0.5) * g[0] + R(1.5) * g[1];
+  R q1 = R(0.5) * (g[1] + g[2]);
+  R t0 = g[1] - g[0], t1 = g[2] - g[1];
+  R s0 = eps + t0 * t0, s1 = eps + t1 * t1;
+  s0 *= s0; s1 *= s1;
+  R a0 = R(1.0 / 3.0) * s1, a1 = R(2.0 / 3.0) * s0;
+  return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+
 template <int WR, class R>
 __device__ __forceinline__ R weno_rec(const R *g) {
-  if constexpr (WR == 3) return weno5<R>(g);
+  if constexpr (WR == 1) return g[0];  // order 1: upwind value
+  else if constexpr (WR == 2) return weno3<R>(g);
+  else if constexpr (WR == 3) return weno5<R>(g);
   else return weno7<R>(g);
 }
 
@@ -342,10 +365,11 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     const long long stride = DIR == 0 ? 1 : (DIR == 1 ? d.sy : d.sz);
     const long long p0 = pidx(d, i, j, k);  // point s of the interface s+1/2
 
-    // --- central split-form flux at this interface
+    // --- central split-form flux at this interface (order 2 npc)
     R FC[5] = {R(0), R(0), R(0), R(0), R(0)}, fp = R(0);
 #pragma unroll
-    for (int l = 1; l <= 3; ++l) {
+    for (int l = 1; l <= 4; ++l) {
+      if (l > d.npc) break;
       R acc[5] = {R(0), R(0), R(0), R(0), R(0)}, ps = R(0);
 #pragma unroll
       for (int m = 0; m < l; ++m) {
@@ -363,7 +387,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
         acc[4] += mm * sh;
         ps += __ldg(V.p + a) + __ldg(V.p + b);
       }
-      R al = ka<R>(l);
+      R al = K.acen[l];
       FC[0] += R(0.5) * al * acc[0];
 #pragma unroll
       for (int f = 1; f < 5; ++f) FC[f] += R(0.25) * al * acc[f];
@@ -447,20 +471,37 @@ constexpr size_t flux_smem() {
   return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)15 * (L + 3) * W);
 }
 
-template <int DIR, int WR, class R, int TV>
+template <int DIR, class R, int TV, int NP>
+constexpr size_t flux_smem() {
+  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
+  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)5 * NP * (L + NP) * W);
+}
+
+template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t launch_one(const Dev &d, int accumulate, cudaStream_t st) {
   constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   dim3 grid;
   if (DIR == 0) grid = dim3((d.nx + L - 1) / L, (d.ny + W - 1) / W, d.nz);
   if (DIR == 1) grid = dim3((d.nx + W - 1) / W, (d.ny + L - 1) / L, d.nz);
   if (DIR == 2) grid = dim3((d.nx + W - 1) / W, (d.nz + L - 1) / L, d.ny);
-  k_flux<DIR, WR, R, TV><<<grid, NTHREADS, flux_smem<DIR, R, TV>(), st>>>(d, accumulate);
+  k_flux<DIR, HASW, R, TV, NP><<<grid, NTHREADS, flux_smem<DIR, R, TV, NP>(), st>>>(d, accumulate);
   return cudaGetLastError();
 }
 
-template <int DIR, int WR, class R>
+template <int DIR, bool HASW, class R, int TV>
+cudaError_t launch_np(const Dev &d, int accumulate, cudaStream_t st) {
+  switch (d.npc) {
+    case 1: return launch_one<DIR, HASW, R, TV, 1>(d, accumulate, st);
+    case 2: return launch_one<DIR, HASW, R, TV, 2>(d, accumulate, st);
+    case 3: return launch_one<DIR, HASW, R, TV, 3>(d, accumulate, st);
+    case 4: return launch_one<DIR, HASW, R, TV, 4>(d, accumulate, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DIR, bool HASW, class R>
 cudaError_t launch_tv(const Dev &d, int accumulate, cudaStream_t st) {
-  return d.tile[DIR] ? launch_one<DIR, WR, R, 1>(d, accumulate, st) : launch_one<DIR, WR, R, 0>(d, accumulate, st);
+  return d.tile[DIR] ? launch_np<DIR, HASW, R, 1>(d, accumulate, st) : launch_np<DIR, HASW, R, 0>(d, accumulate, st);
 }
 
 template <int DIR, int WR, class R>
@@ -476,40 +517,50 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int DIR, int WR, class R>
+template <int DIR, bool HASW, class R, int TV, int NP>
+cudaError_t set_attr_one() {
+  return cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)flux_smem<DIR, R, TV, NP>());
+}
+
+template <int DIR, class R>
 cudaError_t set_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_flux<DIR, WR, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)flux_smem<DIR, R, 0>());
-  cudaError_t e1 = cudaFuncSetAttribute(k_flux<DIR, WR, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)flux_smem<DIR, R, 1>());
-  return e != cudaSuccess ? e : e1;
+  cudaError_t e = cudaSuccess, r;
+#define S2_A(H, T, N) \
+  if ((r = set_attr_one<DIR, H, R, T, N>()) != cudaSuccess) e = r;
+  S2_A(false, 0, 1) S2_A(false, 0, 2) S2_A(false, 0, 3) S2_A(false, 0, 4)
+  S2_A(false, 1, 1) S2_A(false, 1, 2) S2_A(false, 1, 3) S2_A(false, 1, 4)
+  S2_A(true, 0, 1) S2_A(true, 0, 2) S2_A(true, 0, 3) S2_A(true, 0, 4)
+  S2_A(true, 1, 1) S2_A(true, 1, 2) S2_A(true, 1, 3) S2_A(true, 1, 4)
+#undef S2_A
+  return e;
 }
 
 template <class R>
 cudaError_t flux_dispatch(const Dev &d, int dir, int accumulate, cudaStream_t st) {
-  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
-  switch (dir * 10 + wr) {
-    case 0: return launch_tv<0, 0, R>(d, accumulate, st);
-    case 3: return launch_tv<0, 3, R>(d, accumulate, st);
-    case 4: return launch_tv<0, 4, R>(d, accumulate, st);
-    case 10: return launch_tv<1, 0, R>(d, accumulate, st);
-    case 13: return launch_tv<1, 3, R>(d, accumulate, st);
-    case 14: return launch_tv<1, 4, R>(d, accumulate, st);
-    case 20: return launch_tv<2, 0, R>(d, accumulate, st);
-    case 23: return launch_tv<2, 3, R>(d, accumulate, st);
-    case 24: return launch_tv<2, 4, R>(d, accumulate, st);
+  const bool w = d.weno > 0;
+  switch (dir) {
+    case 0: return w ? launch_tv<0, true, R>(d, accumulate, st) : launch_tv<0, false, R>(d, accumulate, st);
+    case 1: return w ? launch_tv<1, true, R>(d, accumulate, st) : launch_tv<1, false, R>(d, accumulate, st);
+    case 2: return w ? launch_tv<2, true, R>(d, accumulate, st) : launch_tv<2, false, R>(d, accumulate, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template <class R>
 cudaError_t weno_dispatch(const Dev &d, int dir, cudaStream_t st) {
-  int wr = d.weno == 5 ? 3 : (d.weno == 7 ? 4 : 0);
+  const int wr = (d.weno + 1) / 2;
   switch (dir * 10 + wr) {
+    case 1: return launch_weno_one<0, 1, R>(d, st);
+    case 2: return launch_weno_one<0, 2, R>(d, st);
     case 3: return launch_weno_one<0, 3, R>(d, st);
     case 4: return launch_weno_one<0, 4, R>(d, st);
+    case 11: return launch_weno_one<1, 1, R>(d, st);
+    case 12: return launch_weno_one<1, 2, R>(d, st);
     case 13: return launch_weno_one<1, 3, R>(d, st);
     case 14: return launch_weno_one<1, 4, R>(d, st);
+    case 21: return launch_weno_one<2, 1, R>(d, st);
+    case 22: return launch_weno_one<2, 2, R>(d, st);
     case 23: return launch_weno_one<2, 3, R>(d, st);
     case 24: return launch_weno_one<2, 4, R>(d, st);
   }
@@ -520,13 +571,12 @@ cudaError_t weno_dispatch(const Dev &d, int dir, cudaStream_t st) {
 
 cudaError_t flux_set_attributes() {
   cudaError_t e = cudaSuccess, r;
-#define S2_ATTR(D, W)                                     \
-  if ((r = set_attr<D, W, double>()) != cudaSuccess) e = r; \
-  if ((r = set_attr<D, W, float>()) != cudaSuccess) e = r;
-  S2_ATTR(0, 0) S2_ATTR(1, 0) S2_ATTR(2, 0)
-  S2_ATTR(0, 3) S2_ATTR(1, 3) S2_ATTR(2, 3)
-  S2_ATTR(0, 4) S2_ATTR(1, 4) S2_ATTR(2, 4)
-#undef S2_ATTR
+  if ((r = set_attr<0, double>()) != cudaSuccess) e = r;
+  if ((r = set_attr<1, double>()) != cudaSuccess) e = r;
+  if ((r = set_attr<2, double>()) != cudaSuccess) e = r;
+  if ((r = set_attr<0, float>()) != cudaSuccess) e = r;
+  if ((r = set_attr<1, float>()) != cudaSuccess) e = r;
+  if ((r = set_attr<2, float>()) != cudaSuccess) e = r;
   return e;
 }
 

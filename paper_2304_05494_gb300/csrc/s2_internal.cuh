@@ -34,8 +34,9 @@ constexpr int ERR_NONFINITE = 1;
 // FP64 path, float for the flux arithmetic of the mixed path).
 template <class R>
 struct Consts {
-  R ax[4], az[4];          // a_l/dx, a_l/dz (first derivative, l = 1..3)
-  R bx[4], bz[4];          // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..3)
+  R ax[5], az[5];          // a_l/dx, a_l/dz (first derivative of the viscous order, l = 1..4)
+  R bx[5], bz[5];          // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..4)
+  R acen[5];               // a_l of the central (convective) order, l = 1..4
   R idx, idz;              // 1/dx, 1/dz
   R R_gas, cp, gamma, gR, icv, visc_exp, inv_t_ref, t_wall, cp_over_pr, re, thr;
 };
@@ -48,8 +49,9 @@ struct Dev {
   long long off0;          // padded offset of interior point (0,0,0)
   long long n;             // nx*ny*nz
   double dx, dz, idx, idz;  // spacings and their inverses
-  double ax[4], az[4];     // a_l/dx, a_l/dz (first derivative, l = 1..3)
-  double bx[4], bz[4];     // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..3)
+  double ax[5], az[5];     // a_l/dx, a_l/dz (first derivative, viscous order, l = 1..4)
+  double bx[5], bz[5];     // b_l/dx^2, b_l/dz^2 (second derivative, viscous order, l = 0..4)
+  int npc, npv;            // stencil pairs of the central and the viscous order (order / 2)
   double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
   double gR;               // gamma R (c^2 = gamma R T)
   int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
@@ -72,7 +74,8 @@ struct Dev {
   void *mu;                // interior
   void *g;                 // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
   void *div, *sens;        // padded
-  // metrics (length ny): eta_y; a_l eta_y (3/j); b_l eta_y^2 (4/j); eta_yy/eta_y; 1/eta_y
+  // metrics (length ny): eta_y; a_l eta_y (4/j); b_l eta_y^2 (5/j); eta_yy/eta_y; 1/eta_y
+  // (a_l, b_l of the viscous order; the metric itself uses the higher order)
   const double *eta_y, *ay, *by, *ry, *dvy;
   const float *eta_yf, *ayf, *byf, *ryf;  // the same in single precision
   Scal *scal;

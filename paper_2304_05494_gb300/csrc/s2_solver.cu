@@ -30,9 +30,25 @@ namespace {
 constexpr int NT = 256;
 constexpr int NRED = 1024;  // blocks of the grid-stride reductions
 
-// 6th-order central coefficients (first derivative a_l, second b_l).
-const double A1[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
-const double B2[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+// Central coefficients of order 2L (L = 1..4): first derivative a_l,
+// second derivative b_l (b_0 the centre weight).
+const double A1_ORD[5][5] = {{0.0, 0.0, 0.0, 0.0, 0.0},
+                             {0.0, 1.0 / 2.0, 0.0, 0.0, 0.0},
+                             {0.0, 2.0 / 3.0, -1.0 / 12.0, 0.0, 0.0},
+                             {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0, 0.0},
+                             {0.0, 4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0}};
+const double B2_ORD[5][5] = {{0.0, 0.0, 0.0, 0.0, 0.0},
+                             {-2.0, 1.0, 0.0, 0.0, 0.0},
+                             {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0, 0.0, 0.0},
+                             {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0, 0.0},
+                             {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0}};
+
+// Stencil tables passed to the metric kernel.
+struct MetricCoef {
+  double am[5], bm[5];  // metric order (the higher of the two)
+  double av[5], bv[5];  // viscous order
+  int lm, lv;
+};
 // Wray's low-storage RK3 coefficients.
 const double RK_G[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double RK_R[4] = {0.0, -17.0 / 60.0, -5.0 / 12.0, 0.0};
@@ -85,12 +101,11 @@ __device__ void block_sum(double *v) {
 // stencil, eta_y = 1/y_eta, eta_yy = -y_etaeta/y_eta^3.  Also the
 // pre-scaled coefficient tables used by the stencil kernels, in double and
 // in single precision.
-__global__ void k_metric(const double *yn, int ny, double ly, int wall, double *eta_y, double *ay, double *by,
-                         double *ry, double *dvy, float *eta_yf, float *ayf, float *byf, float *ryf) {
+__global__ void k_metric(const double *yn, int ny, double ly, int wall, MetricCoef mc, double *eta_y, double *ay,
+                         double *by, double *ry, double *dvy, float *eta_yf, float *ayf, float *byf, float *ryf) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ny) return;
-  const double a[4] = {0.0, 3.0 / 4.0, -3.0 / 20.0, 1.0 / 60.0};
-  const double b[4] = {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0};
+  const double *a = mc.am, *b = mc.bm;
   auto ext = [&](int jj) -> double {
     if (jj >= 0 && jj < ny) return yn[jj];
     if (!wall) {
@@ -102,7 +117,7 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
     return ly - yn[2 * ny - 1 - jj];
   };
   double d1 = 0.0, d2 = b[0] * ext(j);
-  for (int l = 1; l <= 3; ++l) {
+  for (int l = 1; l <= mc.lm; ++l) {
     d1 += a[l] * (ext(j + l) - ext(j - l));
     d2 += b[l] * (ext(j + l) + ext(j - l));
   }
@@ -110,13 +125,13 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, double *
   double eyy = -d2 / (d1 * d1 * d1);
   eta_y[j] = ey;
   eta_yf[j] = (float)ey;
-  for (int l = 1; l <= 3; ++l) {
-    ay[3 * j + l - 1] = a[l] * ey;
-    ayf[3 * j + l - 1] = (float)(a[l] * ey);
+  for (int l = 1; l <= 4; ++l) {
+    ay[4 * j + l - 1] = mc.av[l] * ey;
+    ayf[4 * j + l - 1] = (float)(mc.av[l] * ey);
   }
-  for (int l = 0; l <= 3; ++l) {
-    by[4 * j + l] = b[l] * ey * ey;
-    byf[4 * j + l] = (float)(b[l] * ey * ey);
+  for (int l = 0; l <= 4; ++l) {
+    by[5 * j + l] = mc.bv[l] * ey * ey;
+    byf[5 * j + l] = (float)(mc.bv[l] * ey * ey);
   }
   ry[j] = eyy / ey;
   ryf[j] = (float)(eyy / ey);
@@ -782,8 +797,11 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (bcs->x != S2_BC_PERIODIC || bcs->z != S2_BC_PERIODIC) return S2_EINVAL;
   if (bcs->y != S2_BC_PERIODIC && bcs->y != S2_BC_ISOTHERMAL_WALL) return S2_EINVAL;
   if (bcs->y == S2_BC_ISOTHERMAL_WALL && (grid->ny < GH || !(bcs->t_wall > 0))) return S2_EINVAL;
-  if (scheme->central_order != 6 || scheme->visc_order != 6) return S2_EINVAL;
-  if (scheme->weno_order != 0 && scheme->weno_order != 5 && scheme->weno_order != 7) return S2_EINVAL;
+  auto valid_order = [](int o) { return o == 2 || o == 4 || o == 6 || o == 8; };
+  if (!valid_order(scheme->central_order) || !valid_order(scheme->visc_order)) return S2_EINVAL;
+  if (scheme->weno_order != 0 && scheme->weno_order != 1 && scheme->weno_order != 3 && scheme->weno_order != 5 &&
+      scheme->weno_order != 7)
+    return S2_EINVAL;
   if (scheme->precision != S2_FP64 && scheme->precision != S2_MIXED) return S2_EINVAL;
   if (!(scheme->cfl > 0) && !(scheme->dt_fixed > 0)) return S2_EINVAL;
   if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
@@ -857,13 +875,13 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.dz = grid->lz / grid->nz;
   d.idx = 1.0 / d.dx;
   d.idz = 1.0 / d.dz;
-  for (int l = 1; l <= 3; ++l) {
-    d.ax[l] = A1[l] / d.dx;
-    d.az[l] = A1[l] / d.dz;
-  }
-  for (int l = 0; l <= 3; ++l) {
-    d.bx[l] = B2[l] / (d.dx * d.dx);
-    d.bz[l] = B2[l] / (d.dz * d.dz);
+  d.npc = scheme->central_order / 2;
+  d.npv = scheme->visc_order / 2;
+  for (int l = 0; l <= 4; ++l) {
+    d.ax[l] = l ? A1_ORD[d.npv][l] / d.dx : 0.0;
+    d.az[l] = l ? A1_ORD[d.npv][l] / d.dz : 0.0;
+    d.bx[l] = B2_ORD[d.npv][l] / (d.dx * d.dx);
+    d.bz[l] = B2_ORD[d.npv][l] / (d.dz * d.dz);
   }
   set_gas(d, gas);
   d.t_wall = bcs->t_wall;
@@ -877,11 +895,12 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   // scheme constants in both arithmetic types
   {
     Consts<double> &k = d.kd;
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < 5; ++l) {
       k.ax[l] = d.ax[l];
       k.az[l] = d.az[l];
       k.bx[l] = d.bx[l];
       k.bz[l] = d.bz[l];
+      k.acen[l] = A1_ORD[d.npc][l];
     }
     k.idx = d.idx;
     k.idz = d.idz;
@@ -897,11 +916,12 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     k.re = d.re;
     k.thr = d.thr;
     Consts<float> &f = d.kf;
-    for (int l = 0; l < 4; ++l) {
+    for (int l = 0; l < 5; ++l) {
       f.ax[l] = (float)k.ax[l];
       f.az[l] = (float)k.az[l];
       f.bx[l] = (float)k.bx[l];
       f.bz[l] = (float)k.bz[l];
+      f.acen[l] = (float)k.acen[l];
     }
     f.idx = (float)k.idx;
     f.idz = (float)k.idz;
@@ -943,9 +963,9 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.g = AR(9 * nn);
   // s2_rhs stages its double output in fln when that is double, else here
   s->rhs_stage = d.mixed ? A(NV * nn) : (double *)d.fln;
-  double *eta = A(grid->ny), *ay = A(3 * grid->ny), *by = A(4 * grid->ny), *ry = A(grid->ny), *dvy = A(grid->ny);
-  float *etaf = (float *)dalloc(s, sizeof(float) * grid->ny), *ayf = (float *)dalloc(s, sizeof(float) * 3 * grid->ny);
-  float *byf = (float *)dalloc(s, sizeof(float) * 4 * grid->ny), *ryf = (float *)dalloc(s, sizeof(float) * grid->ny);
+  double *eta = A(grid->ny), *ay = A(4 * grid->ny), *by = A(5 * grid->ny), *ry = A(grid->ny), *dvy = A(grid->ny);
+  float *etaf = (float *)dalloc(s, sizeof(float) * grid->ny), *ayf = (float *)dalloc(s, sizeof(float) * 4 * grid->ny);
+  float *byf = (float *)dalloc(s, sizeof(float) * 5 * grid->ny), *ryf = (float *)dalloc(s, sizeof(float) * grid->ny);
   if (!etaf || !ayf || !byf || !ryf) ok = false;
   size_t nparts = (size_t)((n + NT - 1) / NT);
   if (nparts < (size_t)NRED * NSTAT) nparts = (size_t)NRED * NSTAT;
@@ -1001,7 +1021,16 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ynd, yn.data(), sizeof(double) * grid->ny, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) {
-    k_metric<<<(grid->ny + 127) / 128, 128, 0, s->stream>>>(ynd, grid->ny, grid->ly, d.wall_y, eta, ay, by, ry,
+    MetricCoef mc;
+    mc.lv = d.npv;
+    mc.lm = d.npc > d.npv ? d.npc : d.npv;
+    for (int l = 0; l < 5; ++l) {
+      mc.am[l] = A1_ORD[mc.lm][l];
+      mc.bm[l] = B2_ORD[mc.lm][l];
+      mc.av[l] = A1_ORD[mc.lv][l];
+      mc.bv[l] = B2_ORD[mc.lv][l];
+    }
+    k_metric<<<(grid->ny + 127) / 128, 128, 0, s->stream>>>(ynd, grid->ny, grid->ly, d.wall_y, mc, eta, ay, by, ry,
                                                              dvy, etaf, ayf, byf, ryf);
     e = cudaGetLastError();
   }

@@ -2,7 +2,8 @@
 //
 // Paper Sec. 2: the switch between central and WENO fluxes is a modified
 // Ducros sensor; the viscous terms are expanded in Laplacian form and
-// discretised with 6th-order central formulae (visflx_nosensor of Table 2).
+// discretised with central formulae of order 2, 4, 6 or 8 (visflx_nosensor
+// of Table 2; the sensor's derivatives use the same order).
 //
 // k_grad, one thread per interior point: the nine velocity gradients
 // d u_a / d x_b (stored, the viscous kernel reuses them), theta = div u
@@ -35,24 +36,40 @@ __device__ __forceinline__ void point_of(const Dev &d, long long q, int &i, int 
   j = (int)(t - (long long)k * d.ny);
 }
 
-// Pre-scaled stencil coefficients of one direction at one point.
+// Pre-scaled stencil coefficients of one direction at one point (c[0] is
+// the centre weight of a second derivative; c[1..NP] the pair weights).
 template <class R>
-struct C4 {
-  R c0, c1, c2, c3;
+struct C5 {
+  R c[5];
 };
 
-// first derivative: c1 (f+1 - f-1) + c2 (f+2 - f-2) + c3 (f+3 - f-3)
-template <class R>
-__device__ __forceinline__ R d1(const R *__restrict__ f, long long p, long long s, const C4<R> &c) {
-  return c.c1 * (__ldg(f + p + s) - __ldg(f + p - s)) + c.c2 * (__ldg(f + p + 2 * s) - __ldg(f + p - 2 * s)) +
-         c.c3 * (__ldg(f + p + 3 * s) - __ldg(f + p - 3 * s));
+// first derivative: sum_{l=1..NP} c_l (f_{+l} - f_{-l})
+template <int NP, class R>
+__device__ __forceinline__ R d1(const R *__restrict__ f, long long p, long long s, const C5<R> &c) {
+  R r = c.c[1] * (__ldg(f + p + s) - __ldg(f + p - s));
+#pragma unroll
+  for (int l = 2; l <= NP; ++l) r += c.c[l] * (__ldg(f + p + l * s) - __ldg(f + p - l * s));
+  return r;
 }
 
-// second derivative: c0 f + c1 (f+1 + f-1) + c2 (f+2 + f-2) + c3 (f+3 + f-3)
-template <class R>
-__device__ __forceinline__ R d2(const R *__restrict__ f, long long p, long long s, const C4<R> &c) {
-  return c.c0 * __ldg(f + p) + c.c1 * (__ldg(f + p + s) + __ldg(f + p - s)) +
-         c.c2 * (__ldg(f + p + 2 * s) + __ldg(f + p - 2 * s)) + c.c3 * (__ldg(f + p + 3 * s) + __ldg(f + p - 3 * s));
+// second derivative: c_0 f + sum_{l=1..NP} c_l (f_{+l} + f_{-l})
+template <int NP, class R>
+__device__ __forceinline__ R d2(const R *__restrict__ f, long long p, long long s, const C5<R> &c) {
+  R r = c.c[0] * __ldg(f + p);
+#pragma unroll
+  for (int l = 1; l <= NP; ++l) r += c.c[l] * (__ldg(f + p + l * s) + __ldg(f + p - l * s));
+  return r;
+}
+
+template <int NP, class R>
+__device__ __forceinline__ void coeffs(const Dev &d, const View<R> &V, int j, C5<R> &cx, C5<R> &cy, C5<R> &cz) {
+  const Consts<R> &K = consts<R>(d);
+#pragma unroll
+  for (int l = 0; l <= 4; ++l) {
+    cx.c[l] = l ? K.ax[l] : R(0);
+    cz.c[l] = l ? K.az[l] : R(0);
+    cy.c[l] = (l && l <= NP) ? __ldg(V.ay + 4 * j + l - 1) : R(0);
+  }
 }
 
 // Hybrid-scheme correction of point (i, j, k): R -= scale_d (dF_hi - dF_lo)
@@ -93,24 +110,23 @@ __global__ void __launch_bounds__(NT) k_apply(Dev d) {
   for (int f = 0; f < NV; ++f) V.fl[f * d.n + q] = Rv[f];
 }
 
-template <class R>
+template <class R, int NP>
 __global__ void __launch_bounds__(NT) k_grad(Dev d) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   if (q >= d.n) return;
   const View<R> V = view<R>(d);
-  const Consts<R> &K = consts<R>(d);
   int i, j, k;
   point_of(d, q, i, j, k);
   long long p = pidx(d, i, j, k);
-  const C4<R> cx = {R(0), K.ax[1], K.ax[2], K.ax[3]}, cz = {R(0), K.az[1], K.az[2], K.az[3]};
-  const C4<R> cy = {R(0), __ldg(V.ay + 3 * j), __ldg(V.ay + 3 * j + 1), __ldg(V.ay + 3 * j + 2)};
+  C5<R> cx, cy, cz;
+  coeffs<NP>(d, V, j, cx, cy, cz);
   const R *vel[3] = {V.u, V.v, V.ww};
   R g[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    g[a][0] = d1(vel[a], p, 1, cx);
-    g[a][1] = d1(vel[a], p, d.sy, cy);
-    g[a][2] = d1(vel[a], p, d.sz, cz);
+    g[a][0] = d1<NP>(vel[a], p, 1, cx);
+    g[a][1] = d1<NP>(vel[a], p, d.sy, cy);
+    g[a][2] = d1<NP>(vel[a], p, d.sz, cz);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -126,7 +142,7 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
   }
 }
 
-template <class R>
+template <class R, int NP>
 __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   if (q >= d.n) return;
@@ -135,10 +151,14 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   int i, j, k;
   point_of(d, q, i, j, k);
   long long p = pidx(d, i, j, k);
-  const C4<R> cx = {R(0), K.ax[1], K.ax[2], K.ax[3]}, cz = {R(0), K.az[1], K.az[2], K.az[3]};
-  const C4<R> cy = {R(0), __ldg(V.ay + 3 * j), __ldg(V.ay + 3 * j + 1), __ldg(V.ay + 3 * j + 2)};
-  const C4<R> bx = {K.bx[0], K.bx[1], K.bx[2], K.bx[3]}, bz = {K.bz[0], K.bz[1], K.bz[2], K.bz[3]};
-  const C4<R> by = {__ldg(V.by + 4 * j), __ldg(V.by + 4 * j + 1), __ldg(V.by + 4 * j + 2), __ldg(V.by + 4 * j + 3)};
+  C5<R> cx, cy, cz, bx, by, bz;
+  coeffs<NP>(d, V, j, cx, cy, cz);
+#pragma unroll
+  for (int l = 0; l <= 4; ++l) {
+    bx.c[l] = K.bx[l];
+    bz.c[l] = K.bz[l];
+    by.c[l] = l <= NP ? __ldg(V.by + 5 * j + l) : R(0);
+  }
   const R ry = __ldg(V.ry + j);  // eta_yy / eta_y
   R g[3][3];
 #pragma unroll
@@ -149,15 +169,15 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   R lap[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    lap[a] = d2(vel[a], p, 1, bx) + (d2(vel[a], p, d.sy, by) + ry * g[a][1]) + d2(vel[a], p, d.sz, bz);
+    lap[a] = d2<NP>(vel[a], p, 1, bx) + (d2<NP>(vel[a], p, d.sy, by) + ry * g[a][1]) + d2<NP>(vel[a], p, d.sz, bz);
   R gT[3], gth[3];
-  gT[0] = d1(V.T, p, 1, cx);
-  gT[1] = d1(V.T, p, d.sy, cy);
-  gT[2] = d1(V.T, p, d.sz, cz);
-  R lapT = d2(V.T, p, 1, bx) + (d2(V.T, p, d.sy, by) + ry * gT[1]) + d2(V.T, p, d.sz, bz);
-  gth[0] = d1(V.div, p, 1, cx);
-  gth[1] = d1(V.div, p, d.sy, cy);
-  gth[2] = d1(V.div, p, d.sz, cz);
+  gT[0] = d1<NP>(V.T, p, 1, cx);
+  gT[1] = d1<NP>(V.T, p, d.sy, cy);
+  gT[2] = d1<NP>(V.T, p, d.sz, cz);
+  R lapT = d2<NP>(V.T, p, 1, bx) + (d2<NP>(V.T, p, d.sy, by) + ry * gT[1]) + d2<NP>(V.T, p, d.sz, bz);
+  gth[0] = d1<NP>(V.div, p, 1, cx);
+  gth[1] = d1<NP>(V.div, p, d.sy, cy);
+  gth[2] = d1<NP>(V.div, p, d.sz, cz);
   const R T = __ldg(V.T + p);
   const R mu = __ldg(V.mu + q);
   const R mut = K.visc_exp * mu / T;
@@ -198,12 +218,32 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   for (int f = 1; f < NV; ++f) V.fl[f * d.n + q] = Rv[f];
 }
 
+template <class R>
+void grad_np(const Dev &d, unsigned nb, cudaStream_t st) {
+  switch (d.npv) {
+    case 1: k_grad<R, 1><<<nb, NT, 0, st>>>(d); break;
+    case 2: k_grad<R, 2><<<nb, NT, 0, st>>>(d); break;
+    case 3: k_grad<R, 3><<<nb, NT, 0, st>>>(d); break;
+    default: k_grad<R, 4><<<nb, NT, 0, st>>>(d); break;
+  }
+}
+
+template <class R>
+void visc_np(const Dev &d, unsigned nb, cudaStream_t st) {
+  switch (d.npv) {
+    case 1: k_visc<R, 1><<<nb, NT, 0, st>>>(d); break;
+    case 2: k_visc<R, 2><<<nb, NT, 0, st>>>(d); break;
+    case 3: k_visc<R, 3><<<nb, NT, 0, st>>>(d); break;
+    default: k_visc<R, 4><<<nb, NT, 0, st>>>(d); break;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_grad(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
-  if (d.mixed) k_grad<float><<<nb, NT, 0, st>>>(d);
-  else k_grad<double><<<nb, NT, 0, st>>>(d);
+  if (d.mixed) grad_np<float>(d, nb, st);
+  else grad_np<double>(d, nb, st);
   return cudaGetLastError();
 }
 
@@ -216,8 +256,8 @@ cudaError_t launch_apply(const Dev &d, cudaStream_t st) {
 
 cudaError_t launch_visc(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
-  if (d.mixed) k_visc<float><<<nb, NT, 0, st>>>(d);
-  else k_visc<double><<<nb, NT, 0, st>>>(d);
+  if (d.mixed) visc_np<float>(d, nb, st);
+  else visc_np<double>(d, nb, st);
   return cudaGetLastError();
 }
 

@@ -286,7 +286,8 @@ class Solver:
 
     def __init__(self, nx, ny, nz, lx, ly, lz, *, y=None, gamma=1.4, prandtl=0.72, mach=0.1, re=1600.0,
                  visc_exp=0.76, t_ref=1.0, wall_y=False, t_wall=1.0, force=False, weno_order=0,
-                 threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1, precision="fp64"):
+                 threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1, precision="fp64",
+                 central_order=6, visc_order=6):
         self.shape = (5, nz, ny, nx)
         self.n = nx * ny * nz
         grid = s2_grid(nx, ny, nz, lx, ly, lz)
@@ -299,7 +300,7 @@ class Solver:
         bcs = s2_bcs(S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL if wall_y else S2_BC_PERIODIC, S2_BC_PERIODIC,
                      t_wall, 1 if force else 0)
         prec = {"fp64": S2_FP64, "mixed": S2_MIXED}[precision]
-        sch = s2_scheme(6, weno_order, 6, threshold, prec, cfl, dt_fixed, dt_every)
+        sch = s2_scheme(central_order, weno_order, visc_order, threshold, prec, cfl, dt_fixed, dt_every)
         dev = s2_device()
         dev.stream = stream
         dev.device = device
@@ -310,7 +311,8 @@ class Solver:
         args = dict(y=case.y, gamma=case.gamma, prandtl=case.prandtl, mach=case.mach, re=case.re,
                     visc_exp=case.visc_exp, t_ref=case.t_ref, wall_y=case.wall_y, t_wall=case.t_wall,
                     force=case.force, weno_order=case.weno_order, threshold=case.threshold, cfl=case.cfl,
-                    dt_fixed=case.dt_fixed, dt_every=case.dt_every)
+                    dt_fixed=case.dt_fixed, dt_every=case.dt_every,
+                    central_order=getattr(case, "central_order", 6), visc_order=getattr(case, "visc_order", 6))
         args.update(kw)
         return cls(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, **args)
 

@@ -56,8 +56,9 @@ def test_strerror_and_invalid_arguments(lib):
     assert create(g__ly=-1.0) == s2.S2_EINVAL
     assert create(b__x=1) == s2.S2_EINVAL                  # walls only in y
     assert create(b__y=1, g__ny=2) == s2.S2_EINVAL         # walls need ny >= 4
-    assert create(sch__weno_order=3) == s2.S2_EINVAL
-    assert create(sch__central_order=4) == s2.S2_EINVAL
+    assert create(sch__weno_order=4) == s2.S2_EINVAL
+    assert create(sch__central_order=5) == s2.S2_EINVAL
+    assert create(sch__visc_order=10) == s2.S2_EINVAL
     assert create(sch__cfl=0.0, sch__dt_fixed=0.0) == s2.S2_EINVAL
     assert create(gas__gamma=1.0) == s2.S2_EINVAL
     # null arguments
