@@ -11,13 +11,20 @@
 // k_flux<DIR>  one CTA per tile of L points along DIR times W pencils:
 //   1. stage the primitives of the tile plus GH ghost points each side
 //      (coalesced: the x-contiguous index runs fastest);
-//   2. per position a the pair fluxes T_l(a) of the pairs (a, a+l), l=1..3:
-//      m = (rho_a+rho_b)(un_a+un_b), T = m (1, su, sv, sw, sH), s. = pair sums;
-//   3. the central flux difference D(a) = sum_l c_l [T_l(a) - T_l(a-l)]
-//      + sum_l a_l (p_{a+l} - p_{a-l}) equals F_{a+1/2} - F_{a-1/2} of the
-//      split-form interface flux; -scale D goes into the RHS;
-//   4. interface flags (max sensor over the WENO stencil > threshold) are
-//      stored and the flagged interfaces appended to a global list.
+//   2. per position a the weighted pair mass fluxes of the pairs (a, a+l),
+//      l = 1..NP: m_l(a) = (a_l/4) (rho_a+rho_b)(un_a+un_b);
+//   3. the central flux difference D(a) = F_{a+1/2} - F_{a-1/2} of the
+//      split-form interface flux.  The pair flux of field phi is
+//      m_l(a) (phi_a + phi_{a+l}), and the difference telescopes to
+//        D_rho = 2 M,  M = sum_l [m_l(a) - m_l(a-l)],
+//        D_phi = phi_a M + sum_l [m_l(a) phi_{a+l} - m_l(a-l) phi_{a-l}]
+//      (phi = u, v, w, H; plus sum_l a_l (p_{a+l} - p_{a-l}) on the normal
+//      momentum): two fused multiply-adds per field and pair instead of a
+//      pair product, a difference and a multiply-add.  -scale D goes into
+//      the RHS;
+//   4. interface flags (max sensor over the WENO stencil > threshold, from
+//      the per-point tests theta > threshold) are stored and the flagged
+//      interfaces appended to a global list.
 // k_weno<DIR>  one thread per listed interface (globally compacted, so
 //   shocks cause no divergence in the central kernel and no idle lanes
 //   here): F_weno - F_central at the interface.
@@ -79,7 +86,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int LE = L + 2 * GH;       // extended positions per pencil
   constexpr int SF = LE * W;           // words per shared field
   constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
-  constexpr int ST = LT * W;           // words per pair-flux slot
+  constexpr int ST = LT * W;           // words per pair mass-flux slot
   constexpr int NFLD = HASW ? NF : F_S;  // the sensor is staged only for WENO
   // Shared layouts: for x the position index runs fastest (threads walk
   // along x, as the global rows do); for y and z the pencil index runs
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   constexpr int SCT = DIR == 0 ? LT : 1;  // stride between pencils in TP
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *S = (R *)smem_raw;                // [NF][positions x pencils]
-  R *TP = S + NF * SF;                 // [NP][5][positions x pencils]
+  R *TP = S + NF * SF;                 // [NP][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
 
@@ -124,27 +131,19 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   }
   __syncthreads();
 
-  // ---- 2. pair fluxes T_l(a), a = -NP .. L-1 ----
+  // ---- 2. weighted pair mass fluxes m_l(a), a = -NP .. L-1 ----
   for (int idx = tid; idx < ST; idx += NTHREADS) {
     int a, cc;                            // a in 0..LT-1 <-> position a-NP
     if (DIR == 0) { a = idx % LT; cc = idx / LT; }
     else { a = idx / W; cc = idx % W; }
     int ae = a - NP + GH;                 // extended index of the position
-    const R *Sr = S + F_RHO * SF, *Su = S + F_U * SF, *Sv = S + F_V * SF, *Sw = S + F_W * SF, *Sh = S + F_H * SF;
+    const R *Sr = S + F_RHO * SF, *Sn = S + (F_U + DIR) * SF;
     int q0 = ae * SA + cc * SCS;
-    R r0 = Sr[q0], u0 = Su[q0], v0 = Sv[q0], w0 = Sw[q0], h0 = Sh[q0];
+    R r0 = Sr[q0], n0 = Sn[q0];
 #pragma unroll
     for (int l = 1; l <= NP; ++l) {
       int q1 = q0 + l * SA;
-      R su = u0 + Su[q1], sv = v0 + Sv[q1], sw = w0 + Sw[q1];
-      R sun = DIR == 0 ? su : (DIR == 1 ? sv : sw);
-      R m = (r0 + Sr[q1]) * sun;
-      R *T = TP + ((l - 1) * 5) * ST + a * SA + cc * SCT;
-      T[0] = m;
-      T[ST] = m * su;
-      T[2 * ST] = m * sv;
-      T[3 * ST] = m * sw;
-      T[4 * ST] = m * (h0 + Sh[q1]);
+      TP[(l - 1) * ST + a * SA + cc * SCT] = R(0.25 * acoef<NP>(l)) * ((r0 + Sr[q1]) * (n0 + Sn[q1]));
     }
   }
 
@@ -155,7 +154,6 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   // interface a+1/2 spans a-r+1 .. a+r (r = (order+1)/2).
   if constexpr (HASW) {
     const R *Ss = S + F_S * SF;
-    const auto thr_bits = order_bits(K.thr);
     const int wr = (d.weno + 1) / 2;
     constexpr int NI = (L + 1) * W;
     unsigned long long mycount = 0;
@@ -170,17 +168,14 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
         int s = s0 + a;
         bool own = (c0 + cc < nac) && s <= n - 1 && (a >= 0 || s == -1);
         if (own) {
-          // the sensor is >= 0, so its IEEE bit patterns order like the
-          // values: max and comparison run on the integer pipe
-          decltype(order_bits(R(0))) mx = 0;
+          // the stored per-point tests theta > thr are 1.0 or 0.0: the
+          // interface is flagged when any point of the stencil has it
+          // (max theta over the stencil > thr), ORed on the integer pipe
+          decltype(order_bits(R(0))) any = 0;
 #pragma unroll
-          for (int m = -3; m <= 4; ++m) {
-            if (m > -wr && m <= wr) {
-              auto b = order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
-              mx = b > mx ? b : mx;
-            }
-          }
-          flag = K.thr < R(0) || mx > thr_bits;
+          for (int m = -3; m <= 4; ++m)
+            if (m > -wr && m <= wr) any |= order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
+          flag = any != 0;
           if (flag && a >= 0) mycount++;
           int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
           slot = islot(d, DIR, s, i, j, k);
@@ -208,21 +203,29 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
   else { cc = tid % W; a = tid / W; }
   if ((c0 + cc < nac) && (s0 + a < n)) {
     R D[5];
-    int at = (a + NP) * SA + cc * SCT;
+    const int at = (a + NP) * SA + cc * SCT;
+    const int ap = (a + GH) * SA + cc * SCS;
+    R mp[NP], mm[NP];                     // m_l(a), m_l(a-l)
+    R M = R(0);
 #pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      R acc = R(0);
+    for (int l = 1; l <= NP; ++l) {
+      mp[l - 1] = TP[(l - 1) * ST + at];
+      mm[l - 1] = TP[(l - 1) * ST + at - l * SA];
+      M += mp[l - 1] - mm[l - 1];
+    }
+    D[0] = R(2) * M;
+#pragma unroll
+    for (int f = 1; f < 5; ++f) {
+      const R *Sf = S + f * SF;          // F_U .. F_H follow F_RHO
+      R acc = Sf[ap] * M;
 #pragma unroll
       for (int l = 1; l <= NP; ++l) {
-        const R *T = TP + ((l - 1) * 5 + f) * ST;
-        // 2 a_l times the pair means: (rho)(u)(phi) = sums / 8, (rho)(u) = sums / 4
-        const R cl = f == 0 ? R(0.5 * acoef<NP>(l)) : R(0.25 * acoef<NP>(l));
-        acc = fma(cl, T[at] - T[at - l * SA], acc);
+        acc = fma(mp[l - 1], Sf[ap + l * SA], acc);
+        acc = fma(-mm[l - 1], Sf[ap - l * SA], acc);
       }
       D[f] = acc;
     }
     const R *Sp = S + F_P * SF;
-    int ap = (a + GH) * SA + cc * SCS;
     R dp = R(0);
 #pragma unroll
     for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
@@ -465,16 +468,10 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
   }
 }
 
-template <int DIR, class R, int TV>
-constexpr size_t flux_smem() {
-  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
-  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)15 * (L + 3) * W);
-}
-
 template <int DIR, class R, int TV, int NP>
 constexpr size_t flux_smem() {
   constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
-  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)5 * NP * (L + NP) * W);
+  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)NP * (L + NP) * W);
 }
 
 template <int DIR, bool HASW, class R, int TV, int NP>

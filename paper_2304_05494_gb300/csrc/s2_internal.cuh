@@ -39,6 +39,8 @@ struct Consts {
   R acen[5];               // a_l of the central (convective) order, l = 1..4
   R idx, idz;              // 1/dx, 1/dz
   R R_gas, cp, gamma, gR, icv, visc_exp, inv_t_ref, t_wall, cp_over_pr, re, thr;
+  R thr2;                  // thr^2 (sensor test without a root)
+  R b0xz;                  // b_0/dx^2 + b_0/dz^2 (x and z centre weights of the Laplacian)
 };
 
 // Everything a kernel needs, passed by value.
@@ -53,6 +55,7 @@ struct Dev {
   double bx[5], bz[5];     // b_l/dx^2, b_l/dz^2 (second derivative, viscous order, l = 0..4)
   int npc, npv;            // stencil pairs of the central and the viscous order (order / 2)
   double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
+  double inv_re;           // 1 / Re
   double gR;               // gamma R (c^2 = gamma R T)
   int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
   double thr;              // sensor threshold
@@ -73,7 +76,7 @@ struct Dev {
   // auxiliary fields (R)
   void *mu;                // interior
   void *g;                 // 9 velocity gradients, interior, g[(3a+b)*n + q] = d u_a / d x_b
-  void *div, *sens;        // padded
+  void *div, *sens;        // padded; sens holds the sensor test theta > thr as 1 / 0
   // metrics (length ny): eta_y; a_l eta_y (4/j); b_l eta_y^2 (5/j); eta_yy/eta_y; 1/eta_y
   // (a_l, b_l of the viscous order; the metric itself uses the higher order)
   const double *eta_y, *ay, *by, *ry, *dvy;
@@ -149,11 +152,78 @@ __host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
 }
 
 // Integer power by repeated squaring (e >= 0).
+// IEEE-754 format conversions done with integer operations.  GB300 runs
+// double-precision arithmetic (and the F2F conversions) on its narrow FP64
+// pipe; these keep the mixed path's float<->double traffic on the integer
+// pipe.  Normal numbers only: zero and subnormals map to signed zero,
+// out-of-range magnitudes to infinity, NaN to NaN/infinity.
+//   double -> float, rounded to nearest (ties away from zero)
+__device__ __forceinline__ float d2f_int(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  b = (b & 0x7fffffffffffffffull) + (1ull << 28);  // round the 29 dropped bits
+  int e = (int)(b >> 52) - 1023 + 127;
+  unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | mant);
+}
+//   float -> double, exact
+__device__ __forceinline__ double f2d_int(float x) {
+  unsigned b = __float_as_uint(x);
+  unsigned sign = b & 0x80000000u;
+  unsigned e = (b >> 23) & 0xffu;
+  unsigned mant = b & 0x7fffffu;
+  if (e == 0) return __hiloint2double((int)sign, 0);
+  unsigned ed = e == 255u ? 2047u : e - 127u + 1023u;
+  return __hiloint2double((int)(sign | (ed << 20) | (mant >> 3)), (int)(mant << 29));
+}
+
+// 0 < x < infinity (false for NaN), tested on the bit pattern.
+__device__ __forceinline__ bool positive_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// x finite (false for infinities and NaN), tested on the bit pattern.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
+// 1/x for x > 0 in double precision by the Newton-Raphson iteration
+// r <- r + r (1 - x r) from a single-precision approximate reciprocal: the
+// relative error squares per step, ~2^-22 -> 2^-44 -> 2^-88, so two steps
+// leave only the final rounding (within 1 ulp of the quotient 1/x).  Four
+// FP64 fused multiply-adds; the seed and the conversions run on the
+// single-precision and integer pipes.  Magnitudes outside [2^-100, 2^100]
+// (where the single-precision seed could flush or overflow) take the
+// library division.
+__device__ __forceinline__ double rcp_pos(double x) {
+  const int ex = (int)(((unsigned)__double2hiint(x) >> 20) & 0x7ffu) - 1023;
+  if (ex < -100 || ex > 100) return 1.0 / x;
+  float xf = d2f_int(x), rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(xf));
+  double r = f2d_int(rf);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+__device__ __forceinline__ float rcp_pos(float x) { return 1.0f / x; }
+
+// x^e for e >= 0 by binary powering, starting from the lowest set bit
+// (no multiplications by 1, no square after the last bit).
 __device__ __forceinline__ double ipow(double x, int e) {
-  double r = 1.0;
-  while (e) {
-    if (e & 1) r *= x;
+  if (e <= 0) return 1.0;
+  while (!(e & 1)) {
     x *= x;
+    e >>= 1;
+  }
+  double r = x;
+  e >>= 1;
+  while (e) {
+    x *= x;
+    if (e & 1) r *= x;
     e >>= 1;
   }
   return r;
@@ -168,14 +238,14 @@ __device__ __forceinline__ double viscosity(const Dev &d, double T) {
   double x = T * d.inv_t_ref;
   double y;
   if (d.mu_q > 0) {
-    y = (double)powf((float)x, (float)d.visc_exp);
+    y = f2d_int(powf(d2f_int(x), d.kf.visc_exp));
     double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
     double q = (double)d.mu_q;
-    y = y * ((q - 1.0) * yq + (q + 1.0) * a) / ((q + 1.0) * yq + (q - 1.0) * a);
+    y = y * ((q - 1.0) * yq + (q + 1.0) * a) * rcp_pos((q + 1.0) * yq + (q - 1.0) * a);
   } else {
     y = pow(x, d.visc_exp);
   }
-  return y / d.re;
+  return y * d.inv_re;
 }
 
 // CFL spectral radius of one point (compute_dt of Table 2):

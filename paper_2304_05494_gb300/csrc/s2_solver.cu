@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
     long long p = pidx(d, i, j, k);
     const double *w = d.w;
     double rho = w[q];
-    double ri = 1.0 / rho;
+    double ri = rcp_pos(rho);
     double u = w[d.n + q] * ri, v = w[2 * d.n + q] * ri, ww = w[3 * d.n + q] * ri;
     double q2 = u * u + v * v + ww * ww;
     double T = (w[4 * d.n + q] * ri - 0.5 * q2) * d.icv;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
       mu = viscosity(d, T);
       V.mu[q] = mu;
     }
-    if (!(rho > 0.0) || !(T > 0.0) || !isfinite(rho) || !isfinite(T) || !isfinite(q2))
+    if (!positive_finite(rho) || !positive_finite(T) || !finite_bits(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
     if (want_dt) sr = spectral_radius(d, rho, u, v, ww, T, mu, d.eta_y[j]);
   }
@@ -208,13 +208,13 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
     long long p = pidx(d, i, j, k);
     const double *w = d.w;
     double rho = w[q], m1 = w[d.n + q], m2 = w[2 * d.n + q], m3 = w[3 * d.n + q], E = w[4 * d.n + q];
-    float rf = (float)rho;
+    float rf = d2f_int(rho);
     float rif = 1.0f / rf;
-    double ri = (double)rif;
+    double ri = f2d_int(rif);
     ri = ri * (2.0 - rho * ri);
     double e = (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * ri) * ri;
-    float T = (float)(e * d.icv);
-    float u = (float)m1 * rif, v = (float)m2 * rif, ww = (float)m3 * rif;
+    float T = d2f_int(e * d.icv);
+    float u = d2f_int(m1) * rif, v = d2f_int(m2) * rif, ww = d2f_int(m3) * rif;
     float q2 = u * u + v * v + ww * ww;
     V.rho[p] = rf;
     V.u[p] = u;
@@ -363,13 +363,21 @@ __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
 
 // ---------------------------------------------------------------- forcing
 // force_rhs_1: partial sums of R_rhou dV (dV ~ 1/eta_y), deterministic.
+// One warp per x-row (fixed j, k): the row is summed in the path's
+// precision and weighted by dy/deta once, so the loop carries no index
+// division.
 template <class R>
 __global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
   const View<R> V = view<R>(d);
+  const int lane = threadIdx.x & 31;
+  const long long rows = (long long)d.ny * d.nz;
   double s = 0.0;
-  for (long long q = (long long)blockIdx.x * NT + threadIdx.x; q < d.n; q += (long long)gridDim.x * NT) {
-    int j = (int)((q / d.nx) % d.ny);
-    s += (double)V.fl[d.n + q] * d.dvy[j];
+  for (long long r = (long long)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); r < rows;
+       r += (long long)gridDim.x * (NT / 32)) {
+    const R *row = V.fl + d.n + r * d.nx;
+    R sr = 0;
+    for (int i = lane; i < d.nx; i += 32) sr += row[i];
+    s += (double)sr * d.dvy[(int)(r % d.ny)];
   }
   double v[1] = {s};
   block_sum<1>(v);
@@ -766,6 +774,7 @@ void s2::set_gas(Dev &d, const s2_gas *gas) {
   d.cp = gas->gamma * d.cv;
   d.prandtl = gas->prandtl;
   d.re = gas->re_ref;
+  d.inv_re = 1.0 / gas->re_ref;
   d.visc_exp = gas->visc_exp;
   d.inv_t_ref = 1.0 / gas->t_ref;
   d.cp_over_pr = d.cp / gas->prandtl;
@@ -915,6 +924,8 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     k.cp_over_pr = d.cp_over_pr;
     k.re = d.re;
     k.thr = d.thr;
+    k.thr2 = d.thr * d.thr;
+    k.b0xz = d.bx[0] + d.bz[0];
     Consts<float> &f = d.kf;
     for (int l = 0; l < 5; ++l) {
       f.ax[l] = (float)k.ax[l];
@@ -936,6 +947,8 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     f.cp_over_pr = (float)k.cp_over_pr;
     f.re = (float)k.re;
     f.thr = (float)k.thr;
+    f.thr2 = f.thr * f.thr;
+    f.b0xz = (float)k.b0xz;
   }
 
   size_t np = (size_t)d.px * d.py * d.pz;

@@ -52,12 +52,18 @@ __device__ __forceinline__ R d1(const R *__restrict__ f, long long p, long long 
   return r;
 }
 
-// second derivative: c_0 f + sum_{l=1..NP} c_l (f_{+l} + f_{-l})
+// Laplacian of f in the computational coordinates, centre weight c0 of
+// all three directions together: c0 f + sum_d sum_l b_{d,l} (f_{+l} + f_{-l})
 template <int NP, class R>
-__device__ __forceinline__ R d2(const R *__restrict__ f, long long p, long long s, const C5<R> &c) {
-  R r = c.c[0] * __ldg(f + p);
+__device__ __forceinline__ R lap3(const R *__restrict__ f, long long p, long long sy, long long sz, R c0,
+                                  const C5<R> &bx, const C5<R> &by, const C5<R> &bz) {
+  R r = c0 * __ldg(f + p);
 #pragma unroll
-  for (int l = 1; l <= NP; ++l) r += c.c[l] * (__ldg(f + p + l * s) + __ldg(f + p - l * s));
+  for (int l = 1; l <= NP; ++l) r = fma(bx.c[l], __ldg(f + p + l) + __ldg(f + p - l), r);
+#pragma unroll
+  for (int l = 1; l <= NP; ++l) r = fma(by.c[l], __ldg(f + p + l * sy) + __ldg(f + p - l * sy), r);
+#pragma unroll
+  for (int l = 1; l <= NP; ++l) r = fma(bz.c[l], __ldg(f + p + l * sz) + __ldg(f + p - l * sz), r);
   return r;
 }
 
@@ -135,10 +141,16 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
   R th = g[0][0] + g[1][1] + g[2][2];
   V.div[p] = th;
   if (d.weno) {
+    // The Ducros sensor theta = max(-div / sqrt(div^2 + |omega|^2 + 1), 0)
+    // enters the scheme only through theta > thr; that test is stored
+    // (1 or 0), evaluated without a root or a division: for thr >= 0,
+    // theta > thr <=> div < 0 and div^2 > thr^2 (div^2 + |omega|^2 + 1).
+    const Consts<R> &K = consts<R>(d);
     R o1 = g[2][1] - g[1][2], o2 = g[0][2] - g[2][0], o3 = g[1][0] - g[0][1];
     R om2 = o1 * o1 + o2 * o2 + o3 * o3;
-    R sv = -th / sqrt(th * th + om2 + R(1));
-    V.sens[p] = sv > R(0) ? sv : R(0);
+    R th2 = th * th;
+    bool on = K.thr < R(0) || (th < R(0) && th2 > K.thr2 * (th2 + om2 + R(1)));
+    V.sens[p] = on ? R(1) : R(0);
   }
 }
 
@@ -160,53 +172,69 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
     by.c[l] = l <= NP ? __ldg(V.by + 5 * j + l) : R(0);
   }
   const R ry = __ldg(V.ry + j);  // eta_yy / eta_y
+  const R c0 = by.c[0] + K.b0xz;
   R g[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) g[a][b] = __ldg(V.g + (3 * a + b) * d.n + q);
   const R *vel[3] = {V.u, V.v, V.ww};
+  // Laplacians in physical coordinates: d2/dy2 = eta_y^2 d2/deta2 + eta_yy d/deta
   R lap[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-    lap[a] = d2<NP>(vel[a], p, 1, bx) + (d2<NP>(vel[a], p, d.sy, by) + ry * g[a][1]) + d2<NP>(vel[a], p, d.sz, bz);
+  for (int a = 0; a < 3; ++a) lap[a] = fma(ry, g[a][1], lap3<NP>(vel[a], p, d.sy, d.sz, c0, bx, by, bz));
   R gT[3], gth[3];
   gT[0] = d1<NP>(V.T, p, 1, cx);
   gT[1] = d1<NP>(V.T, p, d.sy, cy);
   gT[2] = d1<NP>(V.T, p, d.sz, cz);
-  R lapT = d2<NP>(V.T, p, 1, bx) + (d2<NP>(V.T, p, d.sy, by) + ry * gT[1]) + d2<NP>(V.T, p, d.sz, bz);
+  const R lapT = fma(ry, gT[1], lap3<NP>(V.T, p, d.sy, d.sz, c0, bx, by, bz));
   gth[0] = d1<NP>(V.div, p, 1, cx);
   gth[1] = d1<NP>(V.div, p, d.sy, cy);
   gth[2] = d1<NP>(V.div, p, d.sz, cz);
   const R T = __ldg(V.T + p);
   const R mu = __ldg(V.mu + q);
-  const R mut = K.visc_exp * mu / T;
-  const R kc = mu * K.cp_over_pr;
+  const R mut = K.visc_exp * mu * rcp_pos(T);  // d mu / d T of the power law
   R gmu[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) gmu[b] = mut * gT[b];
   const R th = __ldg(V.div + p);
   const R uv[3] = {__ldg(V.u + p), __ldg(V.v + p), __ldg(V.ww + p)};
-  R mom[3], en = R(0);
+  // tau / mu = S - (2/3) theta I with S_ab = g_ab + g_ba: its diagonal
+  // dg_a = 2 g_aa - (2/3) theta and the off-diagonal S_01, S_02, S_12.
+  const R tq = R(2.0 / 3.0) * th;
+  R dg[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dg[a] = fma(R(2), g[a][a], -tq);
+  const R s01 = g[0][1] + g[1][0], s02 = g[0][2] + g[2][0], s12 = g[1][2] + g[2][1];
+  const R so[3][3] = {{R(0), s01, s02}, {s01, R(0), s12}, {s02, s12, R(0)}};
+  // d_b tau_ab = mu (lap u_a + (1/3) d_a theta) + sum_b (d_b mu) tau_ab / mu
+  R mom[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    R m = mu * (lap[a] + gth[a] * R(1.0 / 3.0));
+    R m = mu * fma(gth[a], R(1.0 / 3.0), lap[a]);
+    m = fma(gmu[a], dg[a], m);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) m += gmu[b] * (g[a][b] + g[b][a]);
-    m -= R(2.0 / 3.0) * th * gmu[a];
+    for (int b = 0; b < 3; ++b)
+      if (b != a) m = fma(gmu[b], so[a][b], m);
     mom[a] = m;
-    en += uv[a] * m;
   }
-  // tau : grad u
-  R tg = R(0);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) tg += (g[a][b] + g[b][a]) * g[a][b];
-  tg -= R(2.0 / 3.0) * th * th;
-  en += mu * tg;
-  en += kc * lapT;
-  en += K.cp_over_pr * (gmu[0] * gT[0] + gmu[1] * gT[1] + gmu[2] * gT[2]);
+  // energy: u . div tau + tau : grad u + div(k grad T), k = mu cp / Pr;
+  // tau : grad u / mu = sum_a dg_a g_aa + S_01^2 + S_02^2 + S_12^2, and
+  // grad k . grad T = (cp/Pr) (d mu/dT) |grad T|^2
+  R en = uv[0] * mom[0];
+  en = fma(uv[1], mom[1], en);
+  en = fma(uv[2], mom[2], en);
+  R tg = dg[0] * g[0][0];
+  tg = fma(dg[1], g[1][1], tg);
+  tg = fma(dg[2], g[2][2], tg);
+  tg = fma(s01, s01, tg);
+  tg = fma(s02, s02, tg);
+  tg = fma(s12, s12, tg);
+  en = fma(mu, tg, en);
+  R gT2 = gT[0] * gT[0];
+  gT2 = fma(gT[1], gT[1], gT2);
+  gT2 = fma(gT[2], gT[2], gT2);
+  en = fma(K.cp_over_pr, fma(mut, gT2, mu * lapT), en);
   R Rv[NV];
   Rv[0] = V.fl[q];
 #pragma unroll
