@@ -109,7 +109,9 @@ typedef struct {
 } s2_scheme;
 
 /* Device options.  alloc/free: optional allocator callbacks (device
- * memory), both NULL = cudaMalloc/cudaFree.  stream: a cudaStream_t or
+ * memory, blocks aligned to at least 256 bytes as cudaMalloc's are;
+ * s2_create fails with S2_EINVAL otherwise), both NULL =
+ * cudaMalloc/cudaFree.  stream: a cudaStream_t or
  * NULL for the legacy default stream.  device: CUDA ordinal, or -1 for
  * the current device. */
 typedef struct {
@@ -140,7 +142,9 @@ typedef struct {
 /* Create a solver; allocates all device memory (state, RK register, RHS,
  * primitive and auxiliary fields with ghost layers) and computes the
  * metrics.  dev may be NULL.  On success *out owns the solver; release it
- * with s2_destroy.  S2_EINVAL for unsupported settings. */
+ * with s2_destroy.  S2_EINVAL for unsupported settings, and for grids with
+ * (nx+1)(ny+1)(nz+1) > 2^31 - 1 (point and interface indices are split
+ * in 32-bit arithmetic; such a grid would not fit in device memory). */
 int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas, const s2_bcs *bcs,
               const s2_scheme *scheme, const s2_device *dev, s2_solver **out);
 

@@ -80,167 +80,275 @@ struct Tile<2, 1> {  // z: 16 along z, 16 columns
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
+// ------------------------------------------------- asynchronous staging
+// Tiles arrive in shared memory by the tensor memory accelerator
+// (cp.async.bulk.tensor, one box per field), completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after a bounded number
+// of polls (each try_wait itself suspends for a short while).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Tiles of a direction: (n0, n1, n2) along the grid dimensions of the
+// tiling, tile t = (t0, t1, t2) with t0 fastest.
+template <int DIR, int TV>
+struct TileGrid {
+  static constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
+  int n0, n1, n2;
+  __host__ __device__ TileGrid(const Dev &d) {
+    if (DIR == 0) { n0 = (d.nx + L - 1) / L; n1 = (d.ny + W - 1) / W; n2 = d.nz; }
+    if (DIR == 1) { n0 = (d.nx + W - 1) / W; n1 = (d.ny + L - 1) / L; n2 = d.nz; }
+    if (DIR == 2) { n0 = (d.nx + W - 1) / W; n1 = (d.nz + L - 1) / L; n2 = d.ny; }
+  }
+  __host__ __device__ int count() const { return n0 * n1 * n2; }
+  // first interior point of the tile along (x, y, z)
+  __device__ void origin(int t, int &x0, int &y0, int &z0) const {
+    const int t0 = t % n0, r = t / n0, t1 = r % n1, t2 = r / n1;
+    if (DIR == 0) { x0 = t0 * L; y0 = t1 * W; z0 = t2; }
+    if (DIR == 1) { x0 = t0 * W; y0 = t1 * L; z0 = t2; }
+    if (DIR == 2) { x0 = t0 * W; z0 = t1 * L; y0 = t2; }
+  }
+};
+
+template <int DIR, class R, int TV>
+struct FluxLayout {
+  static constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
+  static constexpr int LE = L + 2 * GH;                          // extended positions per pencil
+  static constexpr int SF = LE * W;                              // words per staged field (one box)
+  static constexpr int SFA = (SF * (int)sizeof(R) + 127) / 128 * 128 / (int)sizeof(R);  // 128-B aligned
+  static constexpr int BAR_BYTES = 128;                          // two mbarriers, padded
+};
+
 template <int DIR, bool HASW, class R, int TV, int NP>
-__global__ void __launch_bounds__(NTHREADS, 3) k_flux(Dev d, int accumulate) {
-  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
-  constexpr int LE = L + 2 * GH;       // extended positions per pencil
-  constexpr int SF = LE * W;           // words per shared field
+constexpr size_t flux_smem() {
+  using Ly = FluxLayout<DIR, R, TV>;
+  constexpr int NFLD = HASW ? 7 : 6;
+  return Ly::BAR_BYTES + sizeof(R) * (2 * (size_t)NFLD * Ly::SFA + (size_t)NP * (Ly::L + NP) * Ly::W);
+}
+
+// Persistent CTAs walk the tiles of a direction (t = blockIdx.x,
+// + gridDim.x, ...).  While tile t is computed the tensor memory
+// accelerator fills the other staging buffer with tile t + gridDim.x, so
+// the HBM reads of one tile overlap the arithmetic of the previous one.
+template <int DIR, bool HASW, class R, int TV, int NP>
+__global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ FluxMaps maps, Dev d, int accumulate) {
+  using Ly = FluxLayout<DIR, R, TV>;
+  constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA;
   constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
   constexpr int ST = LT * W;           // words per pair mass-flux slot
   constexpr int NFLD = HASW ? NF : F_S;  // the sensor is staged only for WENO
-  // Shared layouts: for x the position index runs fastest (threads walk
-  // along x, as the global rows do); for y and z the pencil index runs
-  // fastest (threads walk across x).  Either way consecutive threads touch
-  // consecutive words: no bank conflicts.
+  constexpr unsigned TILE_BYTES = (unsigned)(NFLD * SF * sizeof(R));
+  // Shared layouts (as the boxes land): for x the position index runs
+  // fastest (threads walk along x, as the global rows do); for y and z the
+  // pencil index runs fastest (threads walk across x).  Either way
+  // consecutive threads touch consecutive words: no bank conflicts.
   constexpr int SA = DIR == 0 ? 1 : W;    // stride between positions
   constexpr int SCS = DIR == 0 ? LE : 1;  // stride between pencils in S
   constexpr int SCT = DIR == 0 ? LT : 1;  // stride between pencils in TP
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *S = (R *)smem_raw;                // [NF][positions x pencils]
-  R *TP = S + NF * SF;                 // [NP][positions x pencils]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long *bar = (unsigned long long *)smem_raw;      // [2]
+  R *Sbuf = (R *)(smem_raw + Ly::BAR_BYTES);                    // [2][NFLD][SFA]
+  R *TP = Sbuf + 2 * NFLD * SFA;                                // [NP][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
+  const TileGrid<DIR, TV> tg(d);
+  const int ntiles = tg.count();
 
   const int tid = threadIdx.x;
   const int n = DIR == 0 ? d.nx : (DIR == 1 ? d.ny : d.nz);
-  int x0 = 0, y0 = 0, z0 = 0;
-  if (DIR == 0) { x0 = blockIdx.x * L; y0 = blockIdx.y * W; z0 = blockIdx.z; }
-  if (DIR == 1) { x0 = blockIdx.x * W; y0 = blockIdx.y * L; z0 = blockIdx.z; }
-  if (DIR == 2) { x0 = blockIdx.x * W; z0 = blockIdx.y * L; y0 = blockIdx.z; }
-  const int s0 = DIR == 0 ? x0 : (DIR == 1 ? y0 : z0);
   const int nac = DIR == 0 ? d.ny : d.nx;   // extent across
-  const int c0 = DIR == 0 ? y0 : x0;
 
-  const R *src[NF] = {V.rho, V.u, V.v, V.ww, V.H, V.p, V.sens};
-
-  // ---- 1. stage the tile (positions s0-GH .. s0+L+GH-1) ----
-  for (int idx = tid; idx < SF; idx += NTHREADS) {
-    int a, cc;
-    if (DIR == 0) { a = idx % LE; cc = idx / LE; }
-    else { cc = idx % W; a = idx / W; }
-    int s = s0 + a - GH;
-    bool ok = (c0 + cc < nac) && (s < n + GH);
-    long long g = 0;
-    if (ok) {
-      if (DIR == 0) g = pidx(d, s, y0 + cc, z0);
-      else if (DIR == 1) g = pidx(d, x0 + cc, s, z0);
-      else g = pidx(d, x0 + cc, y0, s);
-    }
+  // box origin of a tile in padded coordinates (interior point i sits at i + GH)
+  auto issue = [&](int t, int buf) {
+    int x0, y0, z0;
+    tg.origin(t, x0, y0, z0);
+    int bx = DIR == 0 ? x0 : x0 + GH, by = DIR == 1 ? y0 : y0 + GH, bz = DIR == 2 ? z0 : z0 + GH;
+    mbar_expect_tx(&bar[buf], TILE_BYTES);
 #pragma unroll
-    for (int f = 0; f < NFLD; ++f) S[f * SF + a * SA + cc * SCS] = ok ? __ldg(src[f] + g) : R(1);
+    for (int f = 0; f < NFLD; ++f) tma_load_3d(Sbuf + (buf * NFLD + f) * SFA, &maps.m[f], bx, by, bz, &bar[buf]);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
   }
   __syncthreads();
 
-  // ---- 2. weighted pair mass fluxes m_l(a), a = -NP .. L-1 ----
-  for (int idx = tid; idx < ST; idx += NTHREADS) {
-    int a, cc;                            // a in 0..LT-1 <-> position a-NP
-    if (DIR == 0) { a = idx % LT; cc = idx / LT; }
-    else { a = idx / W; cc = idx % W; }
-    int ae = a - NP + GH;                 // extended index of the position
-    const R *Sr = S + F_RHO * SF, *Sn = S + (F_U + DIR) * SF;
-    int q0 = ae * SA + cc * SCS;
-    R r0 = Sr[q0], n0 = Sn[q0];
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int buf = it & 1;
+    // the other buffer was released by the barrier that ended the previous tile
+    if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, buf ^ 1);
+    int x0, y0, z0;
+    tg.origin(t, x0, y0, z0);
+    const int s0 = DIR == 0 ? x0 : (DIR == 1 ? y0 : z0);
+    const int c0 = DIR == 0 ? y0 : x0;
+    // this thread's point and, for y and z, its RHS so far (loaded while
+    // the tile is in flight)
+    int ta, tc;
+    if (DIR == 0) { ta = tid % L; tc = tid / L; }
+    else { tc = tid % W; ta = tid / W; }
+    const bool mine = (c0 + tc < nac) && (s0 + ta < n);
+    const int pi = DIR == 0 ? x0 + ta : x0 + tc;
+    const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta : y0);
+    const int pk = DIR == 2 ? z0 + ta : z0;
+    const long long q = ((long long)pk * d.ny + pj) * d.nx + pi;
+    R prev[5] = {R(0), R(0), R(0), R(0), R(0)};
+    if (mine && accumulate) {
 #pragma unroll
-    for (int l = 1; l <= NP; ++l) {
-      int q1 = q0 + l * SA;
-      TP[(l - 1) * ST + a * SA + cc * SCT] = R(0.25 * acoef<NP>(l)) * ((r0 + Sr[q1]) * (n0 + Sn[q1]));
+      for (int f = 0; f < 5; ++f) prev[f] = V.fl[f * d.n + q];
     }
-  }
-
-  // ---- 4. flags of the interfaces this tile owns, global list ----
-  // A tile owns the interfaces a+1/2 with a in 0..L-1, the first tile of a
-  // pencil also the one before its first point (a = -1): every interface
-  // slot 0..n of a pencil is owned exactly once.  The WENO stencil of
-  // interface a+1/2 spans a-r+1 .. a+r (r = (order+1)/2).
-  if constexpr (HASW) {
-    const R *Ss = S + F_S * SF;
-    const int wr = (d.weno + 1) / 2;
-    constexpr int NI = (L + 1) * W;
-    unsigned long long mycount = 0;
-    for (int base = 0; base < NI; base += NTHREADS) {
-      int idx = base + tid;
-      bool flag = false;
-      long long slot = 0;
-      if (idx < NI) {
-        int a, cc;
-        if (DIR == 0) { a = idx % (L + 1) - 1; cc = idx / (L + 1); }
-        else { a = idx / W - 1; cc = idx % W; }
-        int s = s0 + a;
-        bool own = (c0 + cc < nac) && s <= n - 1 && (a >= 0 || s == -1);
-        if (own) {
-          // the stored per-point tests theta > thr are 1.0 or 0.0: the
-          // interface is flagged when any point of the stencil has it
-          // (max theta over the stencil > thr), ORed on the integer pipe
-          decltype(order_bits(R(0))) any = 0;
-#pragma unroll
-          for (int m = -3; m <= 4; ++m)
-            if (m > -wr && m <= wr) any |= order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
-          flag = any != 0;
-          if (flag && a >= 0) mycount++;
-          int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
-          slot = islot(d, DIR, s, i, j, k);
-          d.flag[DIR][slot] = flag;
-        }
+    bool late = false;
+    if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it >> 1) & 1u);
+    if (__syncthreads_or(late)) {
+      if (tid == 0) {
+        atomicOr(&d.scal->status, ERR_TIMEOUT);
+        // let the copy already issued for the next tile land (bounded)
+        if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[buf ^ 1], (unsigned)((it + 1) >> 1) & 1u);
       }
-      unsigned bal = __ballot_sync(0xffffffffu, flag);
-      if (bal) {
-        int lane = tid & 31;
-        int leader = __ffs(bal) - 1;
-        unsigned off = 0;
-        if (lane == leader) off = atomicAdd(&d.scal->nlist[DIR], (unsigned)__popc(bal));
-        off = __shfl_sync(0xffffffffu, off, leader);
-        if (flag) d.wlist[DIR][off + __popc(bal & ((1u << lane) - 1u))] = (unsigned)slot;
-      }
+      return;
     }
-    for (int o = 16; o > 0; o >>= 1) mycount += __shfl_xor_sync(0xffffffffu, mycount, o);
-    if ((tid & 31) == 0 && mycount) atomicAdd(&d.scal->wcount, mycount);
-  }
-  __syncthreads();
+    const R *S = Sbuf + buf * NFLD * SFA;
+    static_assert(SFA >= SF, "staging layout");
 
-  // ---- 3. central flux difference of the thread's point -> RHS ----
-  int a, cc;
-  if (DIR == 0) { a = tid % L; cc = tid / L; }
-  else { cc = tid % W; a = tid / W; }
-  if ((c0 + cc < nac) && (s0 + a < n)) {
-    R D[5];
-    const int at = (a + NP) * SA + cc * SCT;
-    const int ap = (a + GH) * SA + cc * SCS;
-    R mp[NP], mm[NP];                     // m_l(a), m_l(a-l)
-    R M = R(0);
-#pragma unroll
-    for (int l = 1; l <= NP; ++l) {
-      mp[l - 1] = TP[(l - 1) * ST + at];
-      mm[l - 1] = TP[(l - 1) * ST + at - l * SA];
-      M += mp[l - 1] - mm[l - 1];
-    }
-    D[0] = R(2) * M;
-#pragma unroll
-    for (int f = 1; f < 5; ++f) {
-      const R *Sf = S + f * SF;          // F_U .. F_H follow F_RHO
-      R acc = Sf[ap] * M;
+    // ---- 2. weighted pair mass fluxes m_l(a), a = -NP .. L-1 ----
+    for (int idx = tid; idx < ST; idx += NTHREADS) {
+      int a, cc;                            // a in 0..LT-1 <-> position a-NP
+      if (DIR == 0) { a = idx % LT; cc = idx / LT; }
+      else { a = idx / W; cc = idx % W; }
+      int ae = a - NP + GH;                 // extended index of the position
+      const R *Sr = S + F_RHO * SFA, *Sn = S + (F_U + DIR) * SFA;
+      int q0 = ae * SA + cc * SCS;
+      R r0 = Sr[q0], n0 = Sn[q0];
 #pragma unroll
       for (int l = 1; l <= NP; ++l) {
-        acc = fma(mp[l - 1], Sf[ap + l * SA], acc);
-        acc = fma(-mm[l - 1], Sf[ap - l * SA], acc);
+        int q1 = q0 + l * SA;
+        TP[(l - 1) * ST + a * SA + cc * SCT] = R(0.25 * acoef<NP>(l)) * ((r0 + Sr[q1]) * (n0 + Sn[q1]));
       }
-      D[f] = acc;
     }
-    const R *Sp = S + F_P * SF;
-    R dp = R(0);
+
+    // ---- 4. flags of the interfaces this tile owns, global list ----
+    // A tile owns the interfaces a+1/2 with a in 0..L-1, the first tile of a
+    // pencil also the one before its first point (a = -1): every interface
+    // slot 0..n of a pencil is owned exactly once.  The WENO stencil of
+    // interface a+1/2 spans a-r+1 .. a+r (r = (order+1)/2).
+    if constexpr (HASW) {
+      const R *Ss = S + F_S * SFA;
+      const int wr = (d.weno + 1) / 2;
+      constexpr int NI = (L + 1) * W;
+      unsigned long long mycount = 0;
+      for (int base = 0; base < NI; base += NTHREADS) {
+        int idx = base + tid;
+        bool flag = false;
+        long long slot = 0;
+        if (idx < NI) {
+          int a, cc;
+          if (DIR == 0) { a = idx % (L + 1) - 1; cc = idx / (L + 1); }
+          else { a = idx / W - 1; cc = idx % W; }
+          int s = s0 + a;
+          bool own = (c0 + cc < nac) && s <= n - 1 && (a >= 0 || s == -1);
+          if (own) {
+            // the stored per-point tests theta > thr are 1.0 or 0.0: the
+            // interface is flagged when any point of the stencil has it
+            // (max theta over the stencil > thr), ORed on the integer pipe
+            decltype(order_bits(R(0))) any = 0;
 #pragma unroll
-    for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
-    D[1 + DIR] += dp;
-    int i = DIR == 0 ? x0 + a : x0 + cc;
-    int j = DIR == 0 ? y0 + cc : (DIR == 1 ? y0 + a : y0);
-    int k = DIR == 2 ? z0 + a : z0;
-    R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + j) : K.idz);
-    long long q = ((long long)k * d.ny + j) * d.nx + i;
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      R *o = V.fl + f * d.n + q;
-      R prev = accumulate ? *o : R(0);
-      *o = fma(-scale, D[f], prev);
+            for (int m = -3; m <= 4; ++m)
+              if (m > -wr && m <= wr) any |= order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
+            flag = any != 0;
+            if (flag && a >= 0) mycount++;
+            int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
+            slot = islot(d, DIR, s, i, j, k);
+            d.flag[DIR][slot] = flag;
+          }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, flag);
+        if (bal) {
+          int lane = tid & 31;
+          int leader = __ffs(bal) - 1;
+          unsigned off = 0;
+          if (lane == leader) off = atomicAdd(&d.scal->nlist[DIR], (unsigned)__popc(bal));
+          off = __shfl_sync(0xffffffffu, off, leader);
+          if (flag) d.wlist[DIR][off + __popc(bal & ((1u << lane) - 1u))] = (unsigned)slot;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) mycount += __shfl_xor_sync(0xffffffffu, mycount, o);
+      if ((tid & 31) == 0 && mycount) atomicAdd(&d.scal->wcount, mycount);
     }
+    __syncthreads();
+
+    // ---- 3. central flux difference of the thread's point -> RHS ----
+    if (mine) {
+      R D[5];
+      const int at = (ta + NP) * SA + tc * SCT;
+      const int ap = (ta + GH) * SA + tc * SCS;
+      R mp[NP], mm[NP];                     // m_l(a), m_l(a-l)
+      R M = R(0);
+#pragma unroll
+      for (int l = 1; l <= NP; ++l) {
+        mp[l - 1] = TP[(l - 1) * ST + at];
+        mm[l - 1] = TP[(l - 1) * ST + at - l * SA];
+        M += mp[l - 1] - mm[l - 1];
+      }
+      D[0] = R(2) * M;
+#pragma unroll
+      for (int f = 1; f < 5; ++f) {
+        const R *Sf = S + f * SFA;         // F_U .. F_H follow F_RHO
+        R acc = Sf[ap] * M;
+#pragma unroll
+        for (int l = 1; l <= NP; ++l) {
+          acc = fma(mp[l - 1], Sf[ap + l * SA], acc);
+          acc = fma(-mm[l - 1], Sf[ap - l * SA], acc);
+        }
+        D[f] = acc;
+      }
+      const R *Sp = S + F_P * SFA;
+      R dp = R(0);
+#pragma unroll
+      for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
+      D[1 + DIR] += dp;
+      R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + pj) : K.idz);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) V.fl[f * d.n + q] = fma(-scale, D[f], prev[f]);
+    }
+    __syncthreads();  // staging buffer and TP free for the next tile
   }
 }
 
@@ -346,23 +454,24 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
   for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < cnt; e0 += gridDim.x * blockDim.x) {
     const long long slot = d.wlist[DIR][e0];
     int i = 0, j = 0, k = 0, s;
+    const unsigned us = (unsigned)slot;
     if (DIR == 0) {
-      long long t = slot / (d.nx + 1);
-      s = (int)(slot - t * (d.nx + 1)) - 1;
-      j = (int)(t % d.ny);
-      k = (int)(t / d.ny);
+      unsigned t = d.fnx1.div(us), kk = d.fny.div(t);
+      s = (int)(us - t * (unsigned)(d.nx + 1)) - 1;
+      j = (int)(t - kk * (unsigned)d.ny);
+      k = (int)kk;
       i = s;
     } else if (DIR == 1) {
-      long long t = slot / d.nx;
-      i = (int)(slot - t * d.nx);
-      s = (int)(t % (d.ny + 1)) - 1;
-      k = (int)(t / (d.ny + 1));
+      unsigned t = d.fnx.div(us), kk = d.fny1.div(t);
+      i = (int)(us - t * (unsigned)d.nx);
+      s = (int)(t - kk * (unsigned)(d.ny + 1)) - 1;
+      k = (int)kk;
       j = s;
     } else {
-      long long t = slot / d.nx;
-      i = (int)(slot - t * d.nx);
-      j = (int)(t % d.ny);
-      s = (int)(t / d.ny) - 1;
+      unsigned t = d.fnx.div(us), kk = d.fny.div(t);
+      i = (int)(us - t * (unsigned)d.nx);
+      j = (int)(t - kk * (unsigned)d.ny);
+      s = (int)kk - 1;
       k = s;
     }
     const long long stride = DIR == 0 ? 1 : (DIR == 1 ? d.sy : d.sz);
@@ -468,37 +577,43 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
   }
 }
 
-template <int DIR, class R, int TV, int NP>
-constexpr size_t flux_smem() {
-  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
-  return sizeof(R) * ((size_t)NF * (L + 2 * GH) * W + (size_t)NP * (L + NP) * W);
-}
-
+// Single precision (bound by memory traffic): a persistent grid, as many
+// CTAs as fit on the device at once, each prefetching its next tile.
+// Double precision (bound by the double-precision unit): one tile per CTA,
+// so that more CTAs at different phases share each multiprocessor and keep
+// that unit busy (measured faster than the persistent loop).
 template <int DIR, bool HASW, class R, int TV, int NP>
-cudaError_t launch_one(const Dev &d, int accumulate, cudaStream_t st) {
-  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
-  dim3 grid;
-  if (DIR == 0) grid = dim3((d.nx + L - 1) / L, (d.ny + W - 1) / W, d.nz);
-  if (DIR == 1) grid = dim3((d.nx + W - 1) / W, (d.ny + L - 1) / L, d.nz);
-  if (DIR == 2) grid = dim3((d.nx + W - 1) / W, (d.nz + L - 1) / L, d.ny);
-  k_flux<DIR, HASW, R, TV, NP><<<grid, NTHREADS, flux_smem<DIR, R, TV, NP>(), st>>>(d, accumulate);
+cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaStream_t st) {
+  static int per_sm = 0;  // resident CTAs per multiprocessor (per instantiation)
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flux<DIR, HASW, R, TV, NP>, NTHREADS,
+                                                      flux_smem<DIR, HASW, R, TV, NP>()) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  const int ntiles = TileGrid<DIR, TV>(d).count();
+  const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm * d.nsm ? ntiles : per_sm * d.nsm);
+  k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(maps, d, accumulate);
   return cudaGetLastError();
 }
 
 template <int DIR, bool HASW, class R, int TV>
-cudaError_t launch_np(const Dev &d, int accumulate, cudaStream_t st) {
+cudaError_t launch_np(const Dev &d, const FluxMaps &maps, int accumulate, cudaStream_t st) {
   switch (d.npc) {
-    case 1: return launch_one<DIR, HASW, R, TV, 1>(d, accumulate, st);
-    case 2: return launch_one<DIR, HASW, R, TV, 2>(d, accumulate, st);
-    case 3: return launch_one<DIR, HASW, R, TV, 3>(d, accumulate, st);
-    case 4: return launch_one<DIR, HASW, R, TV, 4>(d, accumulate, st);
+    case 1: return launch_one<DIR, HASW, R, TV, 1>(d, maps, accumulate, st);
+    case 2: return launch_one<DIR, HASW, R, TV, 2>(d, maps, accumulate, st);
+    case 3: return launch_one<DIR, HASW, R, TV, 3>(d, maps, accumulate, st);
+    case 4: return launch_one<DIR, HASW, R, TV, 4>(d, maps, accumulate, st);
   }
   return cudaErrorInvalidValue;
 }
 
 template <int DIR, bool HASW, class R>
-cudaError_t launch_tv(const Dev &d, int accumulate, cudaStream_t st) {
-  return d.tile[DIR] ? launch_np<DIR, HASW, R, 1>(d, accumulate, st) : launch_np<DIR, HASW, R, 0>(d, accumulate, st);
+cudaError_t launch_tv(const Dev &d, const FluxMaps (&maps)[2], int accumulate, cudaStream_t st) {
+  return d.tile[DIR] ? launch_np<DIR, HASW, R, 1>(d, maps[1], accumulate, st)
+                     : launch_np<DIR, HASW, R, 0>(d, maps[0], accumulate, st);
 }
 
 template <int DIR, int WR, class R>
@@ -517,7 +632,7 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t set_attr_one() {
   return cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)flux_smem<DIR, R, TV, NP>());
+                              (int)flux_smem<DIR, HASW, R, TV, NP>());
 }
 
 template <int DIR, class R>
@@ -534,14 +649,52 @@ cudaError_t set_attr() {
 }
 
 template <class R>
-cudaError_t flux_dispatch(const Dev &d, int dir, int accumulate, cudaStream_t st) {
+cudaError_t flux_dispatch(const Dev &d, const FluxMaps (&maps)[2], int dir, int accumulate, cudaStream_t st) {
   const bool w = d.weno > 0;
   switch (dir) {
-    case 0: return w ? launch_tv<0, true, R>(d, accumulate, st) : launch_tv<0, false, R>(d, accumulate, st);
-    case 1: return w ? launch_tv<1, true, R>(d, accumulate, st) : launch_tv<1, false, R>(d, accumulate, st);
-    case 2: return w ? launch_tv<2, true, R>(d, accumulate, st) : launch_tv<2, false, R>(d, accumulate, st);
+    case 0: return w ? launch_tv<0, true, R>(d, maps, accumulate, st) : launch_tv<0, false, R>(d, maps, accumulate, st);
+    case 1: return w ? launch_tv<1, true, R>(d, maps, accumulate, st) : launch_tv<1, false, R>(d, maps, accumulate, st);
+    case 2: return w ? launch_tv<2, true, R>(d, maps, accumulate, st) : launch_tv<2, false, R>(d, maps, accumulate, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Tensor map of one padded field (extent px x py x pz, x contiguous) with
+// the tile box of direction DIR, variant TV.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+template <int DIR, int TV>
+cudaError_t make_map(const Dev &d, void *base, bool dbl, CUtensorMap *out) {
+  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W, LE = L + 2 * GH;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t es = dbl ? 8 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)d.px, (cuuint64_t)d.py, (cuuint64_t)d.pz};
+  cuuint64_t strides[2] = {(cuuint64_t)d.px * es, (cuuint64_t)d.px * d.py * es};
+  cuuint32_t box[3];
+  if (DIR == 0) { box[0] = LE; box[1] = W; box[2] = 1; }
+  if (DIR == 1) { box[0] = W; box[1] = LE; box[2] = 1; }
+  if (DIR == 2) { box[0] = W; box[1] = 1; box[2] = LE; }
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(out, dbl ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 template <class R>
@@ -577,8 +730,25 @@ cudaError_t flux_set_attributes() {
   return e;
 }
 
-cudaError_t launch_flux(const Dev &d, int dir, int accumulate, cudaStream_t st) {
-  return d.mixed ? flux_dispatch<float>(d, dir, accumulate, st) : flux_dispatch<double>(d, dir, accumulate, st);
+cudaError_t launch_flux(const Dev &d, const FluxMaps (&maps)[2], int dir, int accumulate, cudaStream_t st) {
+  return d.mixed ? flux_dispatch<float>(d, maps, dir, accumulate, st)
+                 : flux_dispatch<double>(d, maps, dir, accumulate, st);
+}
+
+cudaError_t flux_make_maps(const Dev &d, FluxMaps (&maps)[3][2]) {
+  void *fields[7] = {d.rho, d.u, d.v, d.ww, d.H, d.p, d.sens};
+  const bool dbl = !d.mixed;
+  cudaError_t e = cudaSuccess;
+  for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
+    if ((uintptr_t)fields[f] % 16) return cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = make_map<0, 0>(d, fields[f], dbl, &maps[0][0].m[f]);
+    if (e == cudaSuccess) e = make_map<0, 1>(d, fields[f], dbl, &maps[0][1].m[f]);
+    if (e == cudaSuccess) e = make_map<1, 0>(d, fields[f], dbl, &maps[1][0].m[f]);
+    if (e == cudaSuccess) e = make_map<1, 1>(d, fields[f], dbl, &maps[1][1].m[f]);
+    if (e == cudaSuccess) e = make_map<2, 0>(d, fields[f], dbl, &maps[2][0].m[f]);
+    if (e == cudaSuccess) e = make_map<2, 1>(d, fields[f], dbl, &maps[2][1].m[f]);
+  }
+  return e;
 }
 
 cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libs2.so.
 // Not part of the public ABI (include/s2.h).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the tensor-memory-access descriptor type)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,7 @@ struct Scal {
 
 // Error bits written by kernels (mapped to S2_ENONFINITE on the host).
 constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_TIMEOUT = 2;  // a bounded wait on an asynchronous copy gave up
 
 // Scheme constants in the arithmetic type R of a kernel (double for the
 // FP64 path, float for the flux arithmetic of the mixed path).
@@ -43,19 +45,44 @@ struct Consts {
   R b0xz;                  // b_0/dx^2 + b_0/dz^2 (x and z centre weights of the Laplacian)
 };
 
+// Division of 32-bit unsigned integers by a run-time constant d >= 1 as a
+// multiply-high and shifts (Granlund & Montgomery, PLDI 1994, round-up
+// method): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, and
+// n / d = (t + ((n - t) >> 1)) >> (l - 1) with t = mulhi(m, n), exact for
+// every n < 2^32.  Point and slot indices are split with it: on GB300 a
+// 64-bit integer division goes through the double-precision unit, which
+// the mixed path otherwise leaves idle and the FP64 path needs for its
+// arithmetic.
+struct FastDiv {
+  unsigned d, m, l;
+  __host__ void init(unsigned dv) {
+    d = dv;
+    l = 0;
+    while ((1ull << l) < dv) ++l;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - dv)) / dv + 1);
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    if (l == 0) return n;
+    unsigned t = __umulhi(m, n);
+    return (t + ((n - t) >> 1)) >> (l - 1);
+  }
+};
+
 // Everything a kernel needs, passed by value.
 struct Dev {
   int nx, ny, nz;
   int px, py, pz;          // padded extents (x pitch rounded up)
   long long sy, sz;        // padded strides
   long long off0;          // padded offset of interior point (0,0,0)
-  long long n;             // nx*ny*nz
+  long long n;             // nx*ny*nz (< 2^31; slot counts < 2^32)
+  FastDiv fnx, fny, fnx1, fny1;  // divisions by nx, ny, nx+1, ny+1
   double dx, dz, idx, idz;  // spacings and their inverses
   double ax[5], az[5];     // a_l/dx, a_l/dz (first derivative, viscous order, l = 1..4)
   double bx[5], bz[5];     // b_l/dx^2, b_l/dz^2 (second derivative, viscous order, l = 0..4)
   int npc, npv;            // stencil pairs of the central and the viscous order (order / 2)
   double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
   double inv_re;           // 1 / Re
+  float visc_exp_f;        // omega in single precision (seed of the viscosity law)
   double gR;               // gamma R (c^2 = gamma R T)
   int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
   double thr;              // sensor threshold
@@ -65,6 +92,7 @@ struct Dev {
   int viscous, wall_y, weno, force;
   int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
   int tile[3];             // flux tile variant per direction (0 default, 1 narrow)
+  int nsm;                 // multiprocessors of the device
   Consts<double> kd;
   Consts<float> kf;
   // state (FP64 in both modes; interior layout [v][k][j][i])
@@ -149,6 +177,21 @@ __device__ __forceinline__ int order_bits(float x) { return __float_as_int(x); }
 
 __host__ __device__ inline long long pidx(const Dev &d, int i, int j, int k) {
   return d.off0 + (long long)k * d.sz + (long long)j * d.sy + i;
+}
+
+// (i, j, k) of interior point q = (k ny + j) nx + i.
+__device__ __forceinline__ void point_of(const Dev &d, long long q, int &i, int &j, int &k) {
+  const unsigned u = (unsigned)q, t = d.fnx.div(u);
+  i = (int)(u - t * (unsigned)d.nx);
+  const unsigned kk = d.fny.div(t);
+  j = (int)(t - kk * (unsigned)d.ny);
+  k = (int)kk;
+}
+
+// j of interior point q.
+__device__ __forceinline__ int row_of(const Dev &d, long long q) {
+  const unsigned t = d.fnx.div((unsigned)q);
+  return (int)(t - d.fny.div(t) * (unsigned)d.ny);
 }
 
 // Integer power by repeated squaring (e >= 0).
@@ -238,7 +281,7 @@ __device__ __forceinline__ double viscosity(const Dev &d, double T) {
   double x = T * d.inv_t_ref;
   double y;
   if (d.mu_q > 0) {
-    y = f2d_int(powf(d2f_int(x), d.kf.visc_exp));
+    y = f2d_int(powf(d2f_int(x), d.visc_exp_f));
     double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
     double q = (double)d.mu_q;
     y = y * ((q - 1.0) * yq + (q + 1.0) * a) * rcp_pos((q + 1.0) * yq + (q - 1.0) * a);
@@ -278,8 +321,15 @@ __device__ __forceinline__ bool dt_due(const Dev &d) {
   return d.cfl > 0.0 && (d.scal->nstep % d.dt_every) == 0;
 }
 
+// Tensor maps of the staged primitive fields (rho, u, v, w, H, p, sensor)
+// for the tile box of one direction and tile variant.
+struct FluxMaps {
+  CUtensorMap m[7];
+};
+
 // Launch helpers (defined in the kernel translation units).
-cudaError_t launch_flux(const Dev &d, int dir, int accumulate, cudaStream_t st);
+cudaError_t flux_make_maps(const Dev &d, FluxMaps (&maps)[3][2]);
+cudaError_t launch_flux(const Dev &d, const FluxMaps (&maps)[2], int dir, int accumulate, cudaStream_t st);
 cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st);
 cudaError_t launch_grad(const Dev &d, cudaStream_t st);
 cudaError_t launch_visc(const Dev &d, cudaStream_t st);

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(NT) k_cfl_parts(Dev d, const double *__restric
   for (int t = 0; t < PTS_PER_THREAD; ++t) {
     long long q = base + (long long)t * NT + threadIdx.x;
     if (q >= d.n) break;
-    int j = (int)((q / d.nx) % d.ny);
+    int j = row_of(d, q);
     double rho = w[q];
     double ri = 1.0 / rho;
     double u = w[d.n + q] * ri, v = w[2 * d.n + q] * ri, ww = w[3 * d.n + q] * ri;
@@ -117,6 +117,8 @@ extern "C" int s2_cfl_dt_noalloc(const s2_grid *grid, const s2_gas *gas, const d
   d.ny = grid->ny;
   d.nz = grid->nz;
   d.n = n;
+  d.fnx.init((unsigned)grid->nx);
+  d.fny.init((unsigned)grid->ny);
   d.dx = grid->lx / grid->nx;
   d.dz = grid->lz / grid->nz;
   set_gas(d, gas);

@@ -53,12 +53,6 @@ struct MetricCoef {
 const double RK_G[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
 const double RK_R[4] = {0.0, -17.0 / 60.0, -5.0 / 12.0, 0.0};
 
-__device__ __forceinline__ void point_of(const Dev &d, long long q, int &i, int &j, int &k) {
-  long long t = q / d.nx;
-  i = (int)(q - t * d.nx);
-  k = (int)(t / d.ny);
-  j = (int)(t - (long long)k * d.ny);
-}
 
 __device__ __forceinline__ int imod(int a, int n) {
   int r = a % n;
@@ -152,6 +146,16 @@ __device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_d
   }
 }
 
+// Whether this launch computes the CFL partials: decided once per CTA (the
+// step counter is 64-bit, and a 64-bit remainder per thread would go
+// through the double-precision unit).
+__device__ __forceinline__ int block_want_dt(const Dev &d, int stage0) {
+  __shared__ int want;
+  if (threadIdx.x == 0) want = stage0 && dt_due(d);
+  __syncthreads();
+  return want;
+}
+
 // ------------------------------------------------------------- primitives
 // rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v, p = rho R T,
 // H = c_p T + |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the
@@ -159,7 +163,7 @@ __device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_d
 __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<double> V = view<double>(d);
-  const int want_dt = stage0 && dt_due(d);
+  const int want_dt = block_want_dt(d, stage0);
   double sr = 0.0;
   if (q < d.n) {
     int i, j, k;
@@ -191,15 +195,17 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
   dt_block_max(d, sr, want_dt);
 }
 
-// Mixed path: the internal energy comes from E - |m|^2/(2 rho) in double
-// precision (E and the kinetic energy nearly cancel at high speed and the
-// temperature carries the pressure), with 1/rho from a single-precision
-// reciprocal refined by one Newton step; everything stored is single
-// precision, as is the rest of the arithmetic.
+// Mixed path: the internal energy per volume rho e = E - rho |u|^2 / 2 is
+// formed by a double-precision subtraction (E and the kinetic energy nearly
+// cancel at high speed), the kinetic part itself to single-precision
+// relative accuracy: the relative error of rho e is then about
+// 2^-24 (1 + KE / (rho e)), KE/(rho e) = gamma (gamma-1) M^2 / 2.  Everything
+// else, and everything stored, is single precision; the one double
+// operation per point leaves the kernel bound by memory traffic.
 __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<float> V = view<float>(d);
-  const int want_dt = stage0 && dt_due(d);
+  const int want_dt = block_want_dt(d, stage0);
   const Consts<float> &K = d.kf;
   double sr = 0.0;
   if (q < d.n) {
@@ -207,15 +213,12 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
     point_of(d, q, i, j, k);
     long long p = pidx(d, i, j, k);
     const double *w = d.w;
-    double rho = w[q], m1 = w[d.n + q], m2 = w[2 * d.n + q], m3 = w[3 * d.n + q], E = w[4 * d.n + q];
-    float rf = d2f_int(rho);
-    float rif = 1.0f / rf;
-    double ri = f2d_int(rif);
-    ri = ri * (2.0 - rho * ri);
-    double e = (E - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * ri) * ri;
-    float T = d2f_int(e * d.icv);
-    float u = d2f_int(m1) * rif, v = d2f_int(m2) * rif, ww = d2f_int(m3) * rif;
+    const float rf = d2f_int(w[q]);
+    const float rif = 1.0f / rf;
+    float u = d2f_int(w[d.n + q]) * rif, v = d2f_int(w[2 * d.n + q]) * rif, ww = d2f_int(w[3 * d.n + q]) * rif;
     float q2 = u * u + v * v + ww * ww;
+    const float rhoe = d2f_int(w[4 * d.n + q] - f2d_int(0.5f * rf * q2));
+    float T = rhoe * rif * K.icv;
     V.rho[p] = rf;
     V.u[p] = u;
     V.v[p] = v;
@@ -266,19 +269,20 @@ __global__ void k_dt_final(Dev d, int nparts) {
 // Face ghost (GH deep) t of the three face sets -> destination and source.
 __device__ __forceinline__ bool ghost_map(const Dev &d, long long t, int &di, int &dj, int &dk, int &si, int &sj,
                                           int &sk) {
-  long long nxf = 2LL * GH * d.ny * d.nz, nyf = 2LL * GH * d.nx * d.nz;
+  const unsigned nxf = 2u * GH * d.ny * d.nz, nyf = 2u * GH * d.nx * d.nz;
+  unsigned u = (unsigned)t;
   bool wall = false;
-  if (t < nxf) {
-    int g = (int)(t % (2 * GH));
-    long long r = t / (2 * GH);
-    dj = (int)(r % d.ny);
-    dk = (int)(r / d.ny);
+  if (u < nxf) {
+    int g = (int)(u % (2 * GH));
+    unsigned r = u / (2 * GH), kk = d.fny.div(r);
+    dj = (int)(r - kk * (unsigned)d.ny);
+    dk = (int)kk;
     di = g < GH ? -1 - g : d.nx + (g - GH);
     si = imod(di, d.nx); sj = dj; sk = dk;
-  } else if (t < nxf + nyf) {
-    t -= nxf;
-    di = (int)(t % d.nx);
-    long long r = t / d.nx;
+  } else if (u < nxf + nyf) {
+    u -= nxf;
+    unsigned r = d.fnx.div(u);
+    di = (int)(u - r * (unsigned)d.nx);
     int g = (int)(r % (2 * GH));
     dk = (int)(r / (2 * GH));
     dj = g < GH ? -1 - g : d.ny + (g - GH);
@@ -290,9 +294,9 @@ __device__ __forceinline__ bool ghost_map(const Dev &d, long long t, int &di, in
       sj = imod(dj, d.ny);
     }
   } else {
-    t -= nxf + nyf;
-    di = (int)(t % d.nx);
-    long long r = t / d.nx;
+    u -= nxf + nyf;
+    unsigned r = d.fnx.div(u);
+    di = (int)(u - r * (unsigned)d.nx);
     int g = (int)(r % (2 * GH));
     dj = (int)(r / (2 * GH));
     dk = g < GH ? -1 - g : d.nz + (g - GH);
@@ -354,7 +358,7 @@ __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
   V.sens[dp] = V.sens[sp];
   if (!wall) {
     V.div[dp] = V.div[sp];
-  } else {
+  } else if (!d.mixed) {  // the mixed path's gradient pass writes these itself
     long long q = ((long long)sk * d.ny + sj) * d.nx + si;
     R ux = V.g[0 * d.n + q], vy = V.g[4 * d.n + q], wz = V.g[8 * d.n + q];
     V.div[dp] = -ux + vy - wz;
@@ -377,7 +381,8 @@ __global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
     const R *row = V.fl + d.n + r * d.nx;
     R sr = 0;
     for (int i = lane; i < d.nx; i += 32) sr += row[i];
-    s += (double)sr * d.dvy[(int)(r % d.ny)];
+    const unsigned ru = (unsigned)r;
+    s += (double)sr * d.dvy[(int)(ru - d.fny.div(ru) * (unsigned)d.ny)];
   }
   double v[1] = {s};
   block_sum<1>(v);
@@ -492,7 +497,7 @@ __global__ void __launch_bounds__(NT) k_stats_partial(Dev d) {
   double v[NSTAT] = {0, 0, 0, 0, 0, 0, 0};
   double f = d.force ? d.scal->force : 0.0;
   for (long long q = (long long)blockIdx.x * NT + threadIdx.x; q < d.n; q += (long long)gridDim.x * NT) {
-    int j = (int)((q / d.nx) % d.ny);
+    int j = row_of(d, q);
     double dv = d.dvy[j] * d.dx * d.dz;
     double rho = d.w[q], mx = d.w[d.n + q], my = d.w[2 * d.n + q], mz = d.w[3 * d.n + q];
     v[0] += rho * dv;
@@ -548,6 +553,7 @@ struct s2_solver {
   long long launches;
   size_t rsize;         // bytes of the arithmetic type (8 FP64, 4 mixed)
   double *rhs_stage;    // staging of s2_rhs output
+  FluxMaps fmaps[3][2];  // tensor maps of the staged fields, per direction and tile variant
 };
 
 namespace {
@@ -651,7 +657,7 @@ cudaError_t enqueue_rhs(s2_solver *s, int stage0, Trace *tr) {
       return e;
   }
   for (int dir = 0; dir < 3; ++dir) {
-    e = run(tr, st, S2_PROF_FLUX_X + dir, 1, [&] { return launch_flux(d, dir, dir > 0, st); });
+    e = run(tr, st, S2_PROF_FLUX_X + dir, 1, [&] { return launch_flux(d, s->fmaps[dir], dir, dir > 0, st); });
     if (e != cudaSuccess) return e;
   }
   if (d.weno) {
@@ -736,6 +742,7 @@ int read_status(s2_solver *s) {
     return S2_ECUDA;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
   if (st & ERR_NONFINITE) return S2_ENONFINITE;
+  if (st & ERR_TIMEOUT) return S2_ETIMEOUT;
   return S2_OK;
 }
 
@@ -775,6 +782,7 @@ void s2::set_gas(Dev &d, const s2_gas *gas) {
   d.prandtl = gas->prandtl;
   d.re = gas->re_ref;
   d.inv_re = 1.0 / gas->re_ref;
+  d.visc_exp_f = (float)gas->visc_exp;
   d.visc_exp = gas->visc_exp;
   d.inv_t_ref = 1.0 / gas->t_ref;
   d.cp_over_pr = d.cp / gas->prandtl;
@@ -815,10 +823,8 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (!(scheme->cfl > 0) && !(scheme->dt_fixed > 0)) return S2_EINVAL;
   if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
-  if (n > (1LL << 40)) return S2_EINVAL;
-  // interface slots of a direction are listed as 32-bit indices
-  if (scheme->weno_order && (long long)(grid->nx + 1) * (grid->ny + 1) * (long long)(grid->nz + 1) > 0xffffffffLL)
-    return S2_EINVAL;
+  // point and interface-slot indices are split in 32-bit unsigned arithmetic
+  if ((long long)(grid->nx + 1) * (grid->ny + 1) * (long long)(grid->nz + 1) > 0x7fffffffLL) return S2_EINVAL;
   if (metrics && metrics->y) {
     for (int j = 1; j < grid->ny; ++j)
       if (!(metrics->y[j] > metrics->y[j - 1])) return S2_EINVAL;
@@ -880,6 +886,11 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.sz = (long long)d.px * d.py;
   d.off0 = GH * d.sz + GH * d.sy + GH;
   d.n = n;
+  d.fnx.init((unsigned)grid->nx);
+  d.fny.init((unsigned)grid->ny);
+  d.fnx1.init((unsigned)grid->nx + 1u);
+  d.fny1.init((unsigned)grid->ny + 1u);
+  if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || d.nsm < 1) d.nsm = 1;
   d.dx = grid->lx / grid->nx;
   d.dz = grid->lz / grid->nz;
   d.idx = 1.0 / d.dx;
@@ -1000,6 +1011,14 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     release(s);
     delete s;
     return S2_ENOMEM;
+  }
+  // tile boxes of the convective kernels (fields 16-byte aligned, as the
+  // tensor memory accelerator requires)
+  if (flux_make_maps(d, s->fmaps) != cudaSuccess) {
+    cudaGetLastError();
+    release(s);
+    delete s;
+    return S2_EINVAL;
   }
   d.eta_y = eta;
   d.ay = ay;
@@ -1210,7 +1229,7 @@ int s2_stats(s2_solver *s, s2_stats_t *out) {
   out->weno_frac = s->d.weno ? (double)h.wcount / (3.0 * (double)s->d.n) : 0.0;
   out->forcing = h.force;
   out->launches = s->launches;
-  out->status = (h.status & ERR_NONFINITE) ? S2_ENONFINITE : S2_OK;
+  out->status = (h.status & ERR_NONFINITE) ? S2_ENONFINITE : (h.status & ERR_TIMEOUT) ? S2_ETIMEOUT : S2_OK;
   return out->status;
 }
 

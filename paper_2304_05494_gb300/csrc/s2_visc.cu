@@ -29,12 +29,6 @@ namespace {
 
 constexpr int NT = 256;
 
-__device__ __forceinline__ void point_of(const Dev &d, long long q, int &i, int &j, int &k) {
-  long long t = q / d.nx;
-  i = (int)(q - t * d.nx);
-  k = (int)(t / d.ny);
-  j = (int)(t - (long long)k * d.ny);
-}
 
 // Pre-scaled stencil coefficients of one direction at one point (c[0] is
 // the centre weight of a second derivative; c[1..NP] the pair weights).
@@ -101,6 +95,67 @@ __device__ __forceinline__ void weno_correction(const Dev &d, const View<R> &V, 
   }
 }
 
+// The Ducros sensor theta = max(-div / sqrt(div^2 + |omega|^2 + 1), 0)
+// enters the scheme only through theta > thr; that test is stored (1 or
+// 0), evaluated without a root or a division: for thr >= 0,
+// theta > thr <=> div < 0 and div^2 > thr^2 (div^2 + |omega|^2 + 1).
+template <class R>
+__device__ __forceinline__ R sensor_test(const Consts<R> &K, const R (&g)[3][3], R th) {
+  R o1 = g[2][1] - g[1][2], o2 = g[0][2] - g[2][0], o3 = g[1][0] - g[0][1];
+  R om2 = o1 * o1 + o2 * o2 + o3 * o3;
+  R th2 = th * th;
+  bool on = K.thr < R(0) || (th < R(0) && th2 > K.thr2 * (th2 + om2 + R(1)));
+  return on ? R(1) : R(0);
+}
+
+// Viscous momentum and energy terms of one point from its derivatives:
+// velocity gradient g[a][b] = d u_a / d x_b, Laplacians lap[a] and lapT,
+// grad T, grad theta; T, mu, theta and u at the point.
+template <class R>
+__device__ __forceinline__ void visc_terms(const Consts<R> &K, const R (&g)[3][3], const R (&lap)[3], const R (&gT)[3],
+                                           R lapT, const R (&gth)[3], R T, R mu, R th, const R (&uv)[3], R (&mom)[3],
+                                           R &en) {
+  const R mut = K.visc_exp * mu * rcp_pos(T);  // d mu / d T of the power law
+  R gmu[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) gmu[b] = mut * gT[b];
+  // tau / mu = S - (2/3) theta I with S_ab = g_ab + g_ba: its diagonal
+  // dg_a = 2 g_aa - (2/3) theta and the off-diagonal S_01, S_02, S_12.
+  const R tq = R(2.0 / 3.0) * th;
+  R dg[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dg[a] = fma(R(2), g[a][a], -tq);
+  const R s01 = g[0][1] + g[1][0], s02 = g[0][2] + g[2][0], s12 = g[1][2] + g[2][1];
+  const R so[3][3] = {{R(0), s01, s02}, {s01, R(0), s12}, {s02, s12, R(0)}};
+  // d_b tau_ab = mu (lap u_a + (1/3) d_a theta) + sum_b (d_b mu) tau_ab / mu
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R m = mu * fma(gth[a], R(1.0 / 3.0), lap[a]);
+    m = fma(gmu[a], dg[a], m);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (b != a) m = fma(gmu[b], so[a][b], m);
+    mom[a] = m;
+  }
+  // energy: u . div tau + tau : grad u + div(k grad T), k = mu cp / Pr;
+  // tau : grad u / mu = sum_a dg_a g_aa + S_01^2 + S_02^2 + S_12^2, and
+  // grad k . grad T = (cp/Pr) (d mu/dT) |grad T|^2
+  R e = uv[0] * mom[0];
+  e = fma(uv[1], mom[1], e);
+  e = fma(uv[2], mom[2], e);
+  R tg = dg[0] * g[0][0];
+  tg = fma(dg[1], g[1][1], tg);
+  tg = fma(dg[2], g[2][2], tg);
+  tg = fma(s01, s01, tg);
+  tg = fma(s02, s02, tg);
+  tg = fma(s12, s12, tg);
+  e = fma(mu, tg, e);
+  R gT2 = gT[0] * gT[0];
+  gT2 = fma(gT[1], gT[1], gT2);
+  gT2 = fma(gT[2], gT[2], gT2);
+  en = fma(K.cp_over_pr, fma(mut, gT2, mu * lapT), e);
+}
+
 template <class R>
 __global__ void __launch_bounds__(NT) k_apply(Dev d) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
@@ -140,18 +195,7 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
     for (int b = 0; b < 3; ++b) V.g[(3 * a + b) * d.n + q] = g[a][b];
   R th = g[0][0] + g[1][1] + g[2][2];
   V.div[p] = th;
-  if (d.weno) {
-    // The Ducros sensor theta = max(-div / sqrt(div^2 + |omega|^2 + 1), 0)
-    // enters the scheme only through theta > thr; that test is stored
-    // (1 or 0), evaluated without a root or a division: for thr >= 0,
-    // theta > thr <=> div < 0 and div^2 > thr^2 (div^2 + |omega|^2 + 1).
-    const Consts<R> &K = consts<R>(d);
-    R o1 = g[2][1] - g[1][2], o2 = g[0][2] - g[2][0], o3 = g[1][0] - g[0][1];
-    R om2 = o1 * o1 + o2 * o2 + o3 * o3;
-    R th2 = th * th;
-    bool on = K.thr < R(0) || (th < R(0) && th2 > K.thr2 * (th2 + om2 + R(1)));
-    V.sens[p] = on ? R(1) : R(0);
-  }
+  if (d.weno) V.sens[p] = sensor_test(consts<R>(d), g, th);
 }
 
 template <class R, int NP>
@@ -191,50 +235,9 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   gth[0] = d1<NP>(V.div, p, 1, cx);
   gth[1] = d1<NP>(V.div, p, d.sy, cy);
   gth[2] = d1<NP>(V.div, p, d.sz, cz);
-  const R T = __ldg(V.T + p);
-  const R mu = __ldg(V.mu + q);
-  const R mut = K.visc_exp * mu * rcp_pos(T);  // d mu / d T of the power law
-  R gmu[3];
-#pragma unroll
-  for (int b = 0; b < 3; ++b) gmu[b] = mut * gT[b];
-  const R th = __ldg(V.div + p);
   const R uv[3] = {__ldg(V.u + p), __ldg(V.v + p), __ldg(V.ww + p)};
-  // tau / mu = S - (2/3) theta I with S_ab = g_ab + g_ba: its diagonal
-  // dg_a = 2 g_aa - (2/3) theta and the off-diagonal S_01, S_02, S_12.
-  const R tq = R(2.0 / 3.0) * th;
-  R dg[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dg[a] = fma(R(2), g[a][a], -tq);
-  const R s01 = g[0][1] + g[1][0], s02 = g[0][2] + g[2][0], s12 = g[1][2] + g[2][1];
-  const R so[3][3] = {{R(0), s01, s02}, {s01, R(0), s12}, {s02, s12, R(0)}};
-  // d_b tau_ab = mu (lap u_a + (1/3) d_a theta) + sum_b (d_b mu) tau_ab / mu
-  R mom[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    R m = mu * fma(gth[a], R(1.0 / 3.0), lap[a]);
-    m = fma(gmu[a], dg[a], m);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      if (b != a) m = fma(gmu[b], so[a][b], m);
-    mom[a] = m;
-  }
-  // energy: u . div tau + tau : grad u + div(k grad T), k = mu cp / Pr;
-  // tau : grad u / mu = sum_a dg_a g_aa + S_01^2 + S_02^2 + S_12^2, and
-  // grad k . grad T = (cp/Pr) (d mu/dT) |grad T|^2
-  R en = uv[0] * mom[0];
-  en = fma(uv[1], mom[1], en);
-  en = fma(uv[2], mom[2], en);
-  R tg = dg[0] * g[0][0];
-  tg = fma(dg[1], g[1][1], tg);
-  tg = fma(dg[2], g[2][2], tg);
-  tg = fma(s01, s01, tg);
-  tg = fma(s02, s02, tg);
-  tg = fma(s12, s12, tg);
-  en = fma(mu, tg, en);
-  R gT2 = gT[0] * gT[0];
-  gT2 = fma(gT[1], gT[1], gT2);
-  gT2 = fma(gT[2], gT[2], gT2);
-  en = fma(K.cp_over_pr, fma(mut, gT2, mu * lapT), en);
+  R mom[3], en;
+  visc_terms(K, g, lap, gT, lapT, gth, __ldg(V.T + p), __ldg(V.mu + q), __ldg(V.div + p), uv, mom, en);
   R Rv[NV];
   Rv[0] = V.fl[q];
 #pragma unroll
@@ -244,6 +247,284 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   if (d.weno) V.fl[q] = Rv[0];
 #pragma unroll
   for (int f = 1; f < NV; ++f) V.fl[f * d.n + q] = Rv[f];
+}
+
+// ------------------------------------------------ z-marching (mixed path)
+// The single-precision path is bound by memory traffic, not arithmetic, so
+// its gradient and viscous kernels march through z instead of giving each
+// point its own 3-D stencil gathers.  A CTA owns a ZTX x ZTY tile of x-y
+// columns over ZS consecutive z-planes.  Per plane, the fields are staged
+// once in shared memory with an NP-point x-y halo (x and y derivatives);
+// along z each thread keeps its column's 2 NP + 1 values in registers
+// (z derivatives).  The next plane's column values and halo values are
+// loaded while the current plane is computed, and the staging buffer is
+// double-buffered, so one barrier per plane suffices.  The viscous pass
+// recomputes the velocity gradients from the staged values rather than
+// reading nine stored ones.
+constexpr int ZTX = 32, ZTY = 8, ZS = 16;
+
+template <int NP>
+struct ZGeom {
+  static constexpr int SX = ZTX + 2 * NP, SY = ZTY + 2 * NP, SIZE = SX * SY;
+  static constexpr int NH = SIZE - ZTX * ZTY;          // halo positions per plane
+  static constexpr int HPT = (NH + NT - 1) / NT;        // halo slots per thread
+};
+
+// Shared-memory position (hx, hy) of halo slot h: NP full rows above the
+// tile, NP columns each side of its ZTY rows, NP full rows below.
+template <int NP>
+__device__ __forceinline__ void zhalo_pos(int h, int &hx, int &hy) {
+  constexpr int SX = ZGeom<NP>::SX;
+  constexpr int TOP = NP * SX, MID = ZTY * 2 * NP;
+  if (h < TOP) {
+    hy = h / SX;
+    hx = h - hy * SX;
+  } else if (h < TOP + MID) {
+    h -= TOP;
+    hy = NP + h / (2 * NP);
+    int r = h - (hy - NP) * 2 * NP;
+    hx = r < NP ? r : ZTX + r;
+  } else {
+    h -= TOP + MID;
+    hy = NP + ZTY + h / SX;
+    hx = h - (hy - NP - ZTY) * SX;
+  }
+}
+
+// Per-thread addressing of a z-marching tile: the thread's own column and
+// its halo slots, as padded offsets without the z term (valid when inside
+// the padded box; out-of-box slots are never read by an active point).
+template <int NP>
+struct ZTile {
+  int i, j, x0, y0, z0, z1;
+  bool active, cvalid;
+  long long cbase;                      // padded offset of (i, j, 0)
+  long long hbase[ZGeom<NP>::HPT];
+  int hoff[ZGeom<NP>::HPT];             // shared offset, -1 when unused
+  __device__ __forceinline__ ZTile(const Dev &d) {
+    constexpr int SX = ZGeom<NP>::SX;
+    const int tid = threadIdx.x;
+    x0 = blockIdx.x * ZTX;
+    y0 = blockIdx.y * ZTY;
+    z0 = blockIdx.z * ZS;
+    z1 = min(z0 + ZS, d.nz);
+    i = x0 + tid % ZTX;
+    j = y0 + tid / ZTX;
+    active = i < d.nx && j < d.ny;
+    cvalid = i < d.nx + GH && j < d.ny + GH;
+    cbase = cvalid ? pidx(d, i, j, 0) : 0;
+#pragma unroll
+    for (int s = 0; s < ZGeom<NP>::HPT; ++s) {
+      int h = tid + s * NT, hx = 0, hy = 0;
+      hoff[s] = -1;
+      hbase[s] = 0;
+      if (h < ZGeom<NP>::NH) {
+        zhalo_pos<NP>(h, hx, hy);
+        int ii = x0 - NP + hx, jj = y0 - NP + hy;
+        if (ii < d.nx + GH && jj < d.ny + GH) {
+          hoff[s] = hy * SX + hx;
+          hbase[s] = pidx(d, ii, jj, 0);
+        }
+      }
+    }
+  }
+  __device__ __forceinline__ int centre() const {
+    return (threadIdx.x / ZTX + NP) * ZGeom<NP>::SX + threadIdx.x % ZTX + NP;
+  }
+};
+
+// z-marching gradient pass: theta = div u (with ghosts at walls) and the
+// sensor test.  NF = 3 staged fields (u, v, w).
+template <int NP>
+__global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
+  using R = float;
+  constexpr int NF = 3, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
+  __shared__ R sm[2][NF][SZ];
+  const View<R> V = view<R>(d);
+  const Consts<R> &K = consts<R>(d);
+  const ZTile<NP> t(d);
+  const R *src[NF] = {V.u, V.v, V.ww};
+  const long long sz = d.sz;
+  C5<R> cx, cy, cz;
+  coeffs<NP>(d, V, t.active ? t.j : 0, cx, cy, cz);
+  R q[NF][NQ], pf[NF], hr[NF][HPT];
+  // prologue: the column's planes z0-NP .. z0+NP, the halo of plane z0
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int m = 0; m < NQ - 1; ++m) q[f][m] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 - NP + m) * sz) : R(0);
+    pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 + NP) * sz) : R(0);
+#pragma unroll
+    for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + t.z0 * sz) : R(0);
+  }
+  const int c = t.centre();
+  for (int k = t.z0; k < t.z1; ++k) {
+    const int b = (k - t.z0) & 1;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      q[f][NQ - 1] = pf[f];
+      sm[b][f][c] = q[f][NP];
+#pragma unroll
+      for (int s = 0; s < HPT; ++s)
+        if (t.hoff[s] >= 0) sm[b][f][t.hoff[s]] = hr[f][s];
+    }
+    if (k + 1 < t.z1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (k + 1 + NP) * sz) : R(0);
+#pragma unroll
+        for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + (k + 1) * sz) : R(0);
+      }
+    }
+    __syncthreads();
+    if (t.active) {
+      R g[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const R *S = sm[b][a];
+        R gx = cx.c[1] * (S[c + 1] - S[c - 1]);
+        R gy = cy.c[1] * (S[c + SX] - S[c - SX]);
+        R gz = cz.c[1] * (q[a][NP + 1] - q[a][NP - 1]);
+#pragma unroll
+        for (int l = 2; l <= NP; ++l) {
+          gx = fma(cx.c[l], S[c + l] - S[c - l], gx);
+          gy = fma(cy.c[l], S[c + l * SX] - S[c - l * SX], gy);
+          gz = fma(cz.c[l], q[a][NP + l] - q[a][NP - l], gz);
+        }
+        g[a][0] = gx;
+        g[a][1] = gy;
+        g[a][2] = gz;
+      }
+      const R th = g[0][0] + g[1][1] + g[2][2];
+      const long long p = t.cbase + k * sz;
+      V.div[p] = th;
+      // wall ghosts of theta: the divergence of the mirrored velocity
+      // field at the mirror node is -u_x + v_y - w_z
+      if (d.wall_y) {
+        if (t.j < GH) V.div[pidx(d, t.i, -1 - t.j, k)] = -g[0][0] + g[1][1] - g[2][2];
+        if (t.j >= d.ny - GH) V.div[pidx(d, t.i, 2 * d.ny - 1 - t.j, k)] = -g[0][0] + g[1][1] - g[2][2];
+      }
+      if (d.weno) V.sens[p] = sensor_test(K, g, th);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int m = 0; m < NQ - 1; ++m) q[f][m] = q[f][m + 1];
+  }
+}
+
+// z-marching viscous pass (velocity gradients recomputed), plus the WENO
+// corrections.  NF = 5 staged fields (u, v, w, T, theta).
+template <int NP>
+__global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
+  using R = float;
+  constexpr int NF = 5, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
+  __shared__ R sm[2][NF][SZ];
+  const View<R> V = view<R>(d);
+  const Consts<R> &K = consts<R>(d);
+  const ZTile<NP> t(d);
+  const R *src[NF] = {V.u, V.v, V.ww, V.T, V.div};
+  const long long sz = d.sz;
+  const int jc = t.active ? t.j : 0;
+  C5<R> cx, cy, cz, bx, by, bz;
+  coeffs<NP>(d, V, jc, cx, cy, cz);
+#pragma unroll
+  for (int l = 0; l <= 4; ++l) {
+    bx.c[l] = K.bx[l];
+    bz.c[l] = K.bz[l];
+    by.c[l] = l <= NP ? __ldg(V.by + 5 * jc + l) : R(0);
+  }
+  const R ry = __ldg(V.ry + jc);
+  const R c0 = by.c[0] + K.b0xz;
+  R q[NF][NQ], pf[NF], hr[NF][HPT];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+#pragma unroll
+    for (int m = 0; m < NQ - 1; ++m) q[f][m] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 - NP + m) * sz) : R(0);
+    pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 + NP) * sz) : R(0);
+#pragma unroll
+    for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + t.z0 * sz) : R(0);
+  }
+  const int c = t.centre();
+  for (int k = t.z0; k < t.z1; ++k) {
+    const int b = (k - t.z0) & 1;
+    const long long qi = ((long long)k * d.ny + t.j) * d.nx + t.i;  // interior index
+    R Rv[NV], mu = R(0);
+    if (t.active) {
+      mu = __ldg(V.mu + qi);
+#pragma unroll
+      for (int f = 0; f < NV; ++f) Rv[f] = V.fl[f * d.n + qi];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      q[f][NQ - 1] = pf[f];
+      sm[b][f][c] = q[f][NP];
+#pragma unroll
+      for (int s = 0; s < HPT; ++s)
+        if (t.hoff[s] >= 0) sm[b][f][t.hoff[s]] = hr[f][s];
+    }
+    if (k + 1 < t.z1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (k + 1 + NP) * sz) : R(0);
+#pragma unroll
+        for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + (k + 1) * sz) : R(0);
+      }
+    }
+    __syncthreads();
+    if (t.active) {
+      // first derivatives (x, y from shared memory, z from the column)
+      R gd[NF][3];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const R *S = sm[b][f];
+        R gx = cx.c[1] * (S[c + 1] - S[c - 1]);
+        R gy = cy.c[1] * (S[c + SX] - S[c - SX]);
+        R gz = cz.c[1] * (q[f][NP + 1] - q[f][NP - 1]);
+#pragma unroll
+        for (int l = 2; l <= NP; ++l) {
+          gx = fma(cx.c[l], S[c + l] - S[c - l], gx);
+          gy = fma(cy.c[l], S[c + l * SX] - S[c - l * SX], gy);
+          gz = fma(cz.c[l], q[f][NP + l] - q[f][NP - l], gz);
+        }
+        gd[f][0] = gx;
+        gd[f][1] = gy;
+        gd[f][2] = gz;
+      }
+      // Laplacians of u, v, w, T: d2/dy2 = eta_y^2 d2/deta2 + eta_yy d/deta
+      R lp[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const R *S = sm[b][f];
+        R r = c0 * q[f][NP];
+#pragma unroll
+        for (int l = 1; l <= NP; ++l) r = fma(bx.c[l], S[c + l] + S[c - l], r);
+#pragma unroll
+        for (int l = 1; l <= NP; ++l) r = fma(by.c[l], S[c + l * SX] + S[c - l * SX], r);
+#pragma unroll
+        for (int l = 1; l <= NP; ++l) r = fma(bz.c[l], q[f][NP + l] + q[f][NP - l], r);
+        lp[f] = fma(ry, gd[f][1], r);
+      }
+      const R g[3][3] = {{gd[0][0], gd[0][1], gd[0][2]}, {gd[1][0], gd[1][1], gd[1][2]}, {gd[2][0], gd[2][1], gd[2][2]}};
+      const R lap[3] = {lp[0], lp[1], lp[2]};
+      const R gT[3] = {gd[3][0], gd[3][1], gd[3][2]};
+      const R gth[3] = {gd[4][0], gd[4][1], gd[4][2]};
+      const R uv[3] = {q[0][NP], q[1][NP], q[2][NP]};
+      R mom[3], en;
+      visc_terms(K, g, lap, gT, lp[3], gth, q[3][NP], mu, q[4][NP], uv, mom, en);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Rv[1 + a] += mom[a];
+      Rv[4] += en;
+      if (d.weno) weno_correction(d, V, t.i, t.j, k, Rv);
+      if (d.weno) V.fl[qi] = Rv[0];
+#pragma unroll
+      for (int f = 1; f < NV; ++f) V.fl[f * d.n + qi] = Rv[f];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int m = 0; m < NQ - 1; ++m) q[f][m] = q[f][m + 1];
+  }
 }
 
 template <class R>
@@ -268,10 +549,22 @@ void visc_np(const Dev &d, unsigned nb, cudaStream_t st) {
 
 }  // namespace
 
+static dim3 zgrid(const Dev &d) {
+  return dim3((d.nx + ZTX - 1) / ZTX, (d.ny + ZTY - 1) / ZTY, (d.nz + ZS - 1) / ZS);
+}
+
 cudaError_t launch_grad(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
-  if (d.mixed) grad_np<float>(d, nb, st);
-  else grad_np<double>(d, nb, st);
+  if (d.mixed) {
+    switch (d.npv) {
+      case 1: k_grad_z<1><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 2: k_grad_z<2><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 3: k_grad_z<3><<<zgrid(d), NT, 0, st>>>(d); break;
+      default: k_grad_z<4><<<zgrid(d), NT, 0, st>>>(d); break;
+    }
+  } else {
+    grad_np<double>(d, nb, st);
+  }
   return cudaGetLastError();
 }
 
@@ -284,8 +577,16 @@ cudaError_t launch_apply(const Dev &d, cudaStream_t st) {
 
 cudaError_t launch_visc(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
-  if (d.mixed) visc_np<float>(d, nb, st);
-  else visc_np<double>(d, nb, st);
+  if (d.mixed) {
+    switch (d.npv) {
+      case 1: k_visc_z<1><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 2: k_visc_z<2><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 3: k_visc_z<3><<<zgrid(d), NT, 0, st>>>(d); break;
+      default: k_visc_z<4><<<zgrid(d), NT, 0, st>>>(d); break;
+    }
+  } else {
+    visc_np<double>(d, nb, st);
+  }
   return cudaGetLastError();
 }
 

@@ -114,3 +114,18 @@ def test_mixed_conservation_periodic(s2):
     drift = {k: abs(s1[k] - s0[k]) / abs(s0[k]) for k in ("mass", "energy")}
     print("mixed conservation drift over 20 steps:", drift)
     assert drift["mass"] < 1e-6 and drift["energy"] < 1e-6
+
+
+@pytest.mark.parametrize("orders", [(2, 2, 3), (4, 4, 5), (8, 8, 7)])
+def test_mixed_rhs_orders_walls_ragged(s2, orders):
+    """Mixed path at other central / viscous / WENO orders on a channel
+    whose sizes are not multiples of any tile (walls, stretched y,
+    forcing): every stencil width of the single-precision kernels,
+    including the divergence ghosts they write at the walls."""
+    co, vo, wo = orders
+    c = W.channel(45, 30, 21, seed=17)
+    kw = case_kw(c)
+    kw.update(central_order=co, visc_order=vo, weno_order=wo, threshold=0.05)
+    e, flips, total = mixed_rhs_err(s2, c.w0, (c.nx, c.ny, c.nz, c.lx, c.ly, c.lz), kw)
+    assert np.all(e < MIX_RHS_TOL), e
+    assert flips <= 1e-3 * total
