@@ -35,15 +35,29 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point RK3 steps/s"
 UNIT = "point-steps/s"
 
-# Algorithmic FP64 flops per interior point of one launch (FMA = 2), counted
-# from the kernel arithmetic; WENO adds WENO5_FLOPS per flagged interface.
-ALG_FLOPS = {"prims": 25, "grad": 92, "flux_x": 95, "flux_y": 95, "flux_z": 95, "visc": 280, "update": 23}
-WENO5_FLOPS = 2000
+# FP64 work per interior point of one launch of each kernel as formulated
+# (ncu, channel 256x128x128 hybrid: dadd + dmul + 2 dfma thread
+# instructions / points for FLOPS; every FP64-pipe instruction for OPS).
+# The FP64 unit issues one add, multiply or fused multiply-add per slot,
+# so OPS against the slot rate is the pipe utilisation and FLOPS against
+# 2 flop/slot the flop-rate fraction.
+ALG_FLOPS = {"prims": 63.0, "grad": 84.0, "flux_x": 91.6, "flux_y": 92.1, "flux_z": 92.1, "visc": 252.7, "update": 20.0}
+FP64_OPS = {"prims": 51.1, "grad": 69.0, "flux_x": 60.5, "flux_y": 60.5, "flux_z": 60.5, "visc": 170.4, "update": 15.0}
+# DRAM bytes per interior point of one launch from the same ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured.
+DRAM_BYTES = {"prims": 92.1, "grad": 102.2, "flux_x": 89.7, "flux_y": 134.7, "flux_z": 134.7, "visc": 207.4, "update": 155.0}
 # FP64 peak: 152 SMs x 2 DFMA/clk (4 flop) x 2070 MHz maximum SM clock.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
+FP64_PEAK_GOPS = FP64_PEAK_GFLOPS / 2
 # Mixed path: algorithmic HBM bytes per interior point of one launch
-# (single-precision primitives and RHS, double-precision state).
-MIXED_BYTES = {"prims": 72, "grad": 56, "flux_x": 52, "flux_y": 72, "flux_z": 72, "visc": 100, "update": 144}
+# (single-precision primitives and RHS, double-precision state; each field
+# read or written once, halos not counted):
+#   prims  w (40) -> rho, u, v, w, T, p, H, mu (32)
+#   grad   u, v, w (12) -> div u, sensor test (8)
+#   flux   rho, u, v, w, H, p, sensor (28) + RHS write (20), y and z also read it (20)
+#   visc   u, v, w, T, div u, mu (24) + RHS read and write (40)
+#   update w read/write (80), RHS (20), RK register read and write on 2 of 3 stages (26.7), u (4)
+MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68, "visc": 64, "update": 130.7}
 
 
 def hbm_peak_gbs():
@@ -247,12 +261,14 @@ def our_arm(args):
     name, (kms, kl) = dom
     per_launch_ms = kms / max(kl, 1)
     flops = ALG_FLOPS[name] * case.points
-    if name.startswith("flux_"):
-        flops += WENO5_FLOPS * weno_frac * case.points
     achieved = flops / (per_launch_ms * 1e-3) / 1e9
+    ops = FP64_OPS[name] * case.points / (per_launch_ms * 1e-3) / 1e9
+    traffic = DRAM_BYTES.get(name)
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None, "kernel": name,
+                "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": traffic * case.points if traffic is not None else None, "kernel": name,
                 "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2070 MHz (measured FMA loop: 1204 GFLOP/s)",
+                "fp64_pipe_frac": ops / FP64_PEAK_GOPS,
                 "per_launch_ms": per_launch_ms,
                 "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1]}}
 

@@ -984,7 +984,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.T = AR(np); d.p = AR(np); d.H = AR(np);
   d.div = AR(np); d.sens = AR(np);
   d.mu = AR(nn);
-  d.g = AR(9 * nn);
+  d.g = d.mixed ? nullptr : AR(9 * nn);  // the mixed viscous pass recomputes the gradients
   // s2_rhs stages its double output in fln when that is double, else here
   s->rhs_stage = d.mixed ? A(NV * nn) : (double *)d.fln;
   double *eta = A(grid->ny), *ay = A(4 * grid->ny), *by = A(5 * grid->ny), *ry = A(grid->ny), *dvy = A(grid->ny);

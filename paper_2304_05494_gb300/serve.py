@@ -33,7 +33,7 @@ from . import workloads as W
 SIZES = (32, 48, 64, 96, 128)
 # device bytes per grid point (state, registers, padded primitives,
 # gradients, hybrid-scheme lists), measured from s2_create's allocations
-BYTES_PER_POINT = {"fp64": 560, "mixed": 330}
+BYTES_PER_POINT = {"fp64": 560, "mixed": 294}
 
 
 @dataclass
