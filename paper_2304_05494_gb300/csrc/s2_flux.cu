@@ -80,50 +80,6 @@ struct Tile<2, 1> {  // z: 16 along z, 16 columns
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
-// ------------------------------------------------- asynchronous staging
-// Tiles arrive in shared memory by the tensor memory accelerator
-// (cp.async.bulk.tensor, one box per field), completing on an mbarrier.
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase with the given parity; gives up after a bounded number
-// of polls (each try_wait itself suspends for a short while).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-          "r"(smem_addr(dst)),
-      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-
 // Tiles of a direction: (n0, n1, n2) along the grid dimensions of the
 // tiling, tile t = (t0, t1, t2) with t0 fastest.
 template <int DIR, int TV>
@@ -354,15 +310,23 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ Fl
 
 // ------------------------------------------------------------------ WENO
 // Reconstruction at i+1/2 from 2r-1 values g[0..2r-2] centred on g[r-1]:
-// Jiang & Shu (r=3), Balsara & Shu (r=4), alpha_k = d_k/(eps+beta_k)^2;
-// the normalisation sum alpha_k q_k / sum alpha_k is evaluated with one
-// division by multiplying through by prod_k (eps+beta_k)^2.
+// Jiang & Shu (r=3), Balsara & Shu (r=4), alpha_k = d_k/(eps+beta_k)^2.
+// The normalisation sum alpha_k q_k / sum alpha_k is evaluated with one
+// reciprocal by multiplying through by prod_k (eps+beta_k)^2, and the
+// substencil polynomials' common denominator (6, 12) joins that
+// reciprocal.  The caller passes eps: reconstructing 2 g with eps' = 4 eps
+// gives exactly twice the reconstruction of g with eps (beta is quadratic
+// in g), which lets the flux splitting skip its factor 1/2.
 template <class R>
-__device__ __forceinline__ R weno5(const R *g) {
-  const R eps = R(1e-6);
-  R q0 = (R(2) * g[0] - R(7) * g[1] + R(11) * g[2]) * R(1.0 / 6.0);
-  R q1 = (-g[1] + R(5) * g[2] + R(2) * g[3]) * R(1.0 / 6.0);
-  R q2 = (R(2) * g[2] + R(5) * g[3] - g[4]) * R(1.0 / 6.0);
+__device__ __forceinline__ R recip_pos(R x) {
+  return rcp_pos(x);
+}
+
+template <class R>
+__device__ __forceinline__ R weno5(const R *g, R eps) {
+  R q0 = R(2) * g[0] - R(7) * g[1] + R(11) * g[2];
+  R q1 = -g[1] + R(5) * g[2] + R(2) * g[3];
+  R q2 = R(2) * g[2] + R(5) * g[3] - g[4];
   R t, b0, b1, b2;
   t = g[0] - R(2) * g[1] + g[2]; b0 = R(13.0 / 12.0) * t * t;
   t = g[0] - R(4) * g[1] + R(3) * g[2]; b0 += R(0.25) * t * t;
@@ -373,16 +337,15 @@ __device__ __forceinline__ R weno5(const R *g) {
   R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
   s0 *= s0; s1 *= s1; s2 *= s2;
   R a0 = R(0.1) * s1 * s2, a1 = R(0.6) * s0 * s2, a2 = R(0.3) * s0 * s1;
-  return (a0 * q0 + a1 * q1 + a2 * q2) / (a0 + a1 + a2);
+  return (a0 * q0 + a1 * q1 + a2 * q2) * recip_pos(R(6) * (a0 + a1 + a2));
 }
 
 template <class R>
-__device__ __forceinline__ R weno7(const R *g) {
-  const R eps = R(1e-6);
-  R q0 = (R(-3) * g[0] + R(13) * g[1] - R(23) * g[2] + R(25) * g[3]) * R(1.0 / 12.0);
-  R q1 = (g[1] - R(5) * g[2] + R(13) * g[3] + R(3) * g[4]) * R(1.0 / 12.0);
-  R q2 = (-g[2] + R(7) * g[3] + R(7) * g[4] - g[5]) * R(1.0 / 12.0);
-  R q3 = (R(3) * g[3] + R(13) * g[4] - R(5) * g[5] + g[6]) * R(1.0 / 12.0);
+__device__ __forceinline__ R weno7(const R *g, R eps) {
+  R q0 = R(-3) * g[0] + R(13) * g[1] - R(23) * g[2] + R(25) * g[3];
+  R q1 = g[1] - R(5) * g[2] + R(13) * g[3] + R(3) * g[4];
+  R q2 = -g[2] + R(7) * g[3] + R(7) * g[4] - g[5];
+  R q3 = R(3) * g[3] + R(13) * g[4] - R(5) * g[5] + g[6];
   // smoothness indicators: 240 x the Jiang-Shu measure as sums of squares
   // of the undivided differences of each 4-point substencil
   R bk[4];
@@ -403,28 +366,27 @@ __device__ __forceinline__ R weno7(const R *g) {
   R p01 = s0 * s1, p23 = s2 * s3;
   R a0 = R(1.0 / 35.0) * s1 * p23, a1 = R(12.0 / 35.0) * s0 * p23;
   R a2 = R(18.0 / 35.0) * p01 * s3, a3 = R(4.0 / 35.0) * p01 * s2;
-  return (a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3) / (a0 + a1 + a2 + a3);
+  return (a0 * q0 + a1 * q1 + a2 * q2 + a3 * q3) * recip_pos(R(12) * (a0 + a1 + a2 + a3));
 }
 
 // Order 3: two substencils, d = (1/3, 2/3), beta_k = (undivided difference)^2.
 template <class R>
-__device__ __forceinline__ R weno3(const R *g) {
-  const R eps = R(1e-6);
-  R q0 = R(-0.5) * g[0] + R(1.5) * g[1];
-  R q1 = R(0.5) * (g[1] + g[2]);
+__device__ __forceinline__ R weno3(const R *g, R eps) {
+  R q0 = -g[0] + R(3) * g[1];
+  R q1 = g[1] + g[2];
   R t0 = g[1] - g[0], t1 = g[2] - g[1];
   R s0 = eps + t0 * t0, s1 = eps + t1 * t1;
   s0 *= s0; s1 *= s1;
   R a0 = R(1.0 / 3.0) * s1, a1 = R(2.0 / 3.0) * s0;
-  return (a0 * q0 + a1 * q1) / (a0 + a1);
+  return (a0 * q0 + a1 * q1) * recip_pos(R(2) * (a0 + a1));
 }
 
 template <int WR, class R>
-__device__ __forceinline__ R weno_rec(const R *g) {
+__device__ __forceinline__ R weno_rec(const R *g, R eps) {
   if constexpr (WR == 1) return g[0];  // order 1: upwind value
-  else if constexpr (WR == 2) return weno3<R>(g);
-  else if constexpr (WR == 3) return weno5<R>(g);
-  else return weno7<R>(g);
+  else if constexpr (WR == 2) return weno3<R>(g, eps);
+  else if constexpr (WR == 3) return weno5<R>(g, eps);
+  else return weno7<R>(g, eps);
 }
 
 // F_weno - F_central at every listed interface of direction DIR.
@@ -510,7 +472,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     // --- Roe average of the two interface states
     const long long ia = p0, ib = p0 + stride;
     R ra = sqrt(__ldg(V.rho + ia)), rb = sqrt(__ldg(V.rho + ib));
-    R inv = R(1) / (ra + rb);
+    R inv = recip_pos(ra + rb);
     R un = (ra * __ldg(vel[DIR] + ia) + rb * __ldg(vel[DIR] + ib)) * inv;
     R ut1 = (ra * __ldg(vel[T1] + ia) + rb * __ldg(vel[T1] + ib)) * inv;
     R ut2 = (ra * __ldg(vel[T2] + ia) + rb * __ldg(vel[T2] + ib)) * inv;
@@ -518,7 +480,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     R q2 = un * un + ut1 * ut1 + ut2 * ut2;
     R c2 = bq * (Ht - R(0.5) * q2);
     R cs = sqrt(c2);
-    R h2 = R(0.5) / c2;
+    R h2 = R(0.5) * recip_pos(c2);
     R hb = h2 * bq, hc = h2 * cs;
 
     // --- per stencil point: l_e W and l_e F for the five fields
@@ -549,18 +511,21 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
       al1 = fmax(al1, fabs(unm));
       al4 = fmax(al4, fabs(unm + cm));
     }
+    // Lax-Friedrichs split g+- = (G +- alpha V) / 2, reconstructed as
+    // G +- alpha V with 4 eps (exactly twice the result), halved once
     R gh[5];
+    const R eps4 = R(4e-6);
 #pragma unroll
     for (int e = 0; e < 5; ++e) {
       R alpha = e == 0 ? al0 : (e == 4 ? al4 : al1);
       R gp[2 * WR - 1], gmn[2 * WR - 1];
 #pragma unroll
       for (int m = 0; m < 2 * WR - 1; ++m) {
-        gp[m] = R(0.5) * (G[e][m] + alpha * Vv[e][m]);
+        gp[m] = fma(alpha, Vv[e][m], G[e][m]);
         int mm = NP - 1 - m;
-        gmn[m] = R(0.5) * (G[e][mm] - alpha * Vv[e][mm]);
+        gmn[m] = fma(-alpha, Vv[e][mm], G[e][mm]);
       }
-      gh[e] = weno_rec<WR, R>(gp) + weno_rec<WR, R>(gmn);
+      gh[e] = R(0.5) * (weno_rec<WR, R>(gp, eps4) + weno_rec<WR, R>(gmn, eps4));
     }
     // --- back to conserved fluxes with the right eigenvectors
     R s014 = gh[0] + gh[1] + gh[4];

@@ -85,6 +85,7 @@ struct Dev {
   float visc_exp_f;        // omega in single precision (seed of the viscosity law)
   double gR;               // gamma R (c^2 = gamma R T)
   int mu_p, mu_q;          // visc_exp = mu_p/mu_q when rational with small terms, else mu_q = 0
+  double mu_qm1, mu_qp1;   // mu_q - 1, mu_q + 1
   double thr;              // sensor threshold
   double cfl;
   int dt_every;            // recompute dt at steps that are multiples of this (cfl > 0)
@@ -283,8 +284,7 @@ __device__ __forceinline__ double viscosity(const Dev &d, double T) {
   if (d.mu_q > 0) {
     y = f2d_int(powf(d2f_int(x), d.visc_exp_f));
     double a = ipow(x, d.mu_p), yq = ipow(y, d.mu_q);
-    double q = (double)d.mu_q;
-    y = y * ((q - 1.0) * yq + (q + 1.0) * a) * rcp_pos((q + 1.0) * yq + (q - 1.0) * a);
+    y = y * (d.mu_qm1 * yq + d.mu_qp1 * a) * rcp_pos(d.mu_qp1 * yq + d.mu_qm1 * a);
   } else {
     y = pow(x, d.visc_exp);
   }
@@ -319,6 +319,50 @@ __device__ __forceinline__ float viscosity(const Dev &d, float T) {
 // device from the step counter, so one captured graph serves every step).
 __device__ __forceinline__ bool dt_due(const Dev &d) {
   return d.cfl > 0.0 && (d.scal->nstep % d.dt_every) == 0;
+}
+
+// Asynchronous staging: tiles arrive in shared memory by the tensor memory
+// accelerator (cp.async.bulk.tensor, one box per field), completing on an
+// mbarrier.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity; gives up after a bounded number
+// of polls (each try_wait itself suspends for a short while).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // Tensor maps of the staged primitive fields (rho, u, v, w, H, p, sensor)

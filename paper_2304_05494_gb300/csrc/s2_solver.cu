@@ -773,6 +773,8 @@ void s2::set_gas(Dev &d, const s2_gas *gas) {
     if (fabs(pq - r) <= 1e-12 * q && r <= 64.0) {
       d.mu_p = (int)r;
       d.mu_q = q;
+      d.mu_qm1 = q - 1.0;
+      d.mu_qp1 = q + 1.0;
       break;
     }
   }

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
 // double-buffered, so one barrier per plane suffices.  The viscous pass
 // recomputes the velocity gradients from the staged values rather than
 // reading nine stored ones.
-constexpr int ZTX = 32, ZTY = 8, ZS = 16;
+constexpr int ZTX = 32, ZTY = 8, ZS = 12;
 
 template <int NP>
 struct ZGeom {
