@@ -61,9 +61,13 @@ struct FastDiv {
     while ((1ull << l) < dv) ++l;
     m = (unsigned)(((1ull << 32) * ((1ull << l) - dv)) / dv + 1);
   }
-  __device__ __forceinline__ unsigned div(unsigned n) const {
+  __host__ __device__ __forceinline__ unsigned div(unsigned n) const {
     if (l == 0) return n;
-    unsigned t = __umulhi(m, n);
+#ifdef __CUDA_ARCH__
+    const unsigned t = __umulhi(m, n);
+#else
+    const unsigned t = (unsigned)(((unsigned long long)m * n) >> 32);
+#endif
     return (t + ((n - t) >> 1)) >> (l - 1);
   }
 };

@@ -61,6 +61,8 @@ def test_strerror_and_invalid_arguments(lib):
     assert create(sch__visc_order=10) == s2.S2_EINVAL
     assert create(sch__cfl=0.0, sch__dt_fixed=0.0) == s2.S2_EINVAL
     assert create(gas__gamma=1.0) == s2.S2_EINVAL
+    # point and interface indices are split in 32-bit arithmetic
+    assert create(g__nx=2000, g__ny=1100, g__nz=1000) == s2.S2_EINVAL
     # null arguments
     h = C.c_void_p()
     assert s2._lib.s2_create(None, None, None, None, None, None, C.byref(h)) == s2.S2_EINVAL

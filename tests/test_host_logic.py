@@ -32,3 +32,60 @@ def test_autotune_choice_and_cache(tmp_path):
     assert autotune.load_cache(p)["k"]["tiles"] == [0, 1, 0]
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
     assert autotune.key((32, 48, 64), "mixed", 5, "G").startswith("32x48x64|mixed|weno5|G")
+
+
+def test_fast_division_exact(tmp_path):
+    """The multiply-high division the kernels split point and slot indices
+    with (FastDiv in the kernels' shared header, host build of the same
+    code) equals integer division: every divisor up to 1100 and the grid
+    extents' neighbourhood of powers of two, dividends at 0, near every
+    multiple boundary sampled, random, and at 2^32 - 1."""
+    import os
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "fastdiv.cu"
+    src.write_text(r'''
+#include <cstdio>
+#include <cstdlib>
+#include "s2_internal.cuh"
+int main() {
+  unsigned divs[2000];
+  int nd = 0;
+  for (unsigned d = 1; d <= 1100; ++d) divs[nd++] = d;
+  for (int e = 11; e <= 31; ++e)
+    for (int o = -2; o <= 2; ++o) divs[nd++] = (1u << e) + o;
+  unsigned long long seed = 12345;
+  long long checked = 0;
+  for (int a = 0; a < nd; ++a) {
+    s2::FastDiv f;
+    f.init(divs[a]);
+    const unsigned d = divs[a];
+    unsigned ns[64];
+    int k = 0;
+    ns[k++] = 0; ns[k++] = 1; ns[k++] = 0xffffffffu; ns[k++] = 0xfffffffeu; ns[k++] = 0x7fffffffu;
+    for (int r = 0; r < 30; ++r) {
+      seed = seed * 6364136223846793005ull + 1442695040888963407ull;
+      unsigned x = (unsigned)(seed >> 32);
+      ns[k++] = x;
+      unsigned q = x / d;
+      if (q > 0) ns[k++] = q * d - 1;
+      if (q > 0) ns[k++] = q * d;
+    }
+    for (int b = 0; b < k; ++b) {
+      ++checked;
+      if (f.div(ns[b]) != ns[b] / d) { printf("FAIL d=%u n=%u got %u\n", d, ns[b], f.div(ns[b])); return 1; }
+    }
+  }
+  printf("ok %lld\n", checked);
+  return 0;
+}
+''')
+    exe = tmp_path / "fastdiv"
+    r = subprocess.run([nvcc, "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
+                        "-I", root + "/paper_2304_05494_gb300/csrc", "-I", root + "/include",
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0 and out.stdout.startswith("ok"), out.stdout + out.stderr
