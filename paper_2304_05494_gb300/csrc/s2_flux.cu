@@ -107,24 +107,27 @@ struct FluxLayout {
   static constexpr int LE = L + 2 * GH;                          // extended positions per pencil
   static constexpr int SF = LE * W;                              // words per staged field (one box)
   static constexpr int SFA = (SF * (int)sizeof(R) + 127) / 128 * 128 / (int)sizeof(R);  // 128-B aligned
-  static constexpr int BAR_BYTES = 128;                          // two mbarriers, padded
+  static constexpr int BAR_BYTES = 128;                          // mbarriers, padded
+  // staging buffers: single precision prefetches two tiles ahead; double
+  // precision runs one tile per CTA and stages it once
+  static constexpr int NBUF = sizeof(R) == 4 ? 3 : 1;
 };
 
 template <int DIR, bool HASW, class R, int TV, int NP>
 constexpr size_t flux_smem() {
   using Ly = FluxLayout<DIR, R, TV>;
   constexpr int NFLD = HASW ? 7 : 6;
-  return Ly::BAR_BYTES + sizeof(R) * (2 * (size_t)NFLD * Ly::SFA + (size_t)NP * (Ly::L + NP) * Ly::W);
+  return Ly::BAR_BYTES + sizeof(R) * ((size_t)Ly::NBUF * NFLD * Ly::SFA + (size_t)NP * (Ly::L + NP) * Ly::W);
 }
 
-// Persistent CTAs walk the tiles of a direction (t = blockIdx.x,
-// + gridDim.x, ...).  While tile t is computed the tensor memory
-// accelerator fills the other staging buffer with tile t + gridDim.x, so
-// the HBM reads of one tile overlap the arithmetic of the previous one.
+// CTAs walk the tiles of a direction (t = blockIdx.x, + gridDim.x, ...).
+// With NBUF staging buffers, the tensor memory accelerator fills the
+// buffers of the next NBUF - 1 tiles while tile t is computed, so the HBM
+// reads of later tiles overlap the arithmetic of the current one.
 template <int DIR, bool HASW, class R, int TV, int NP>
-__global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ FluxMaps maps, Dev d, int accumulate) {
+__global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d, int accumulate) {
   using Ly = FluxLayout<DIR, R, TV>;
-  constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA;
+  constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA, NBUF = Ly::NBUF;
   constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
   constexpr int ST = LT * W;           // words per pair mass-flux slot
   constexpr int NFLD = HASW ? NF : F_S;  // the sensor is staged only for WENO
@@ -137,9 +140,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ Fl
   constexpr int SCS = DIR == 0 ? LE : 1;  // stride between pencils in S
   constexpr int SCT = DIR == 0 ? LT : 1;  // stride between pencils in TP
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned long long *bar = (unsigned long long *)smem_raw;      // [2]
-  R *Sbuf = (R *)(smem_raw + Ly::BAR_BYTES);                    // [2][NFLD][SFA]
-  R *TP = Sbuf + 2 * NFLD * SFA;                                // [NP][positions x pencils]
+  unsigned long long *bar = (unsigned long long *)smem_raw;      // [NBUF]
+  R *Sbuf = (R *)(smem_raw + Ly::BAR_BYTES);                    // [NBUF][NFLD][SFA]
+  R *TP = Sbuf + NBUF * NFLD * SFA;                             // [NP][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
   const TileGrid<DIR, TV> tg(d);
@@ -158,20 +161,23 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ Fl
 #pragma unroll
     for (int f = 0; f < NFLD; ++f) tma_load_3d(Sbuf + (buf * NFLD + f) * SFA, &maps.m[f], bx, by, bz, &bar[buf]);
   };
+  // tile of this CTA's iteration it, its buffer and that buffer's use count
+  const int G = gridDim.x;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    for (int j = 0; j < NBUF - 1; ++j)
+      if ((int)blockIdx.x + j * G < ntiles) issue(blockIdx.x + j * G, j);
   }
   __syncthreads();
 
   int it = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-    const int buf = it & 1;
-    // the other buffer was released by the barrier that ended the previous tile
-    if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x, buf ^ 1);
+  for (int t = blockIdx.x; t < ntiles; t += G, ++it) {
+    const int buf = it % NBUF;
+    // the buffer of tile it + NBUF - 1 was released by the barrier that
+    // ended the previous tile
+    if (tid == 0 && t + (NBUF - 1) * G < ntiles) issue(t + (NBUF - 1) * G, (it + NBUF - 1) % NBUF);
     int x0, y0, z0;
     tg.origin(t, x0, y0, z0);
     const int s0 = DIR == 0 ? x0 : (DIR == 1 ? y0 : z0);
@@ -192,12 +198,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_flux(const __grid_constant__ Fl
       for (int f = 0; f < 5; ++f) prev[f] = V.fl[f * d.n + q];
     }
     bool late = false;
-    if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it >> 1) & 1u);
+    if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it / NBUF) & 1u);
     if (__syncthreads_or(late)) {
       if (tid == 0) {
         atomicOr(&d.scal->status, ERR_TIMEOUT);
-        // let the copy already issued for the next tile land (bounded)
-        if (t + (int)gridDim.x < ntiles) mbar_wait_bounded(&bar[buf ^ 1], (unsigned)((it + 1) >> 1) & 1u);
+        // let the copies already issued for the next tiles land (bounded)
+        for (int j = 1; j < NBUF; ++j)
+          if (t + j * G < ntiles) mbar_wait_bounded(&bar[(it + j) % NBUF], (unsigned)((it + j) / NBUF) & 1u);
       }
       return;
     }
@@ -543,7 +550,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
 }
 
 // Single precision (bound by memory traffic): a persistent grid, as many
-// CTAs as fit on the device at once, each prefetching its next tile.
+// CTAs as fit on the device at once, each prefetching its next two tiles.
 // Double precision (bound by the double-precision unit): one tile per CTA,
 // so that more CTAs at different phases share each multiprocessor and keep
 // that unit busy (measured faster than the persistent loop).
