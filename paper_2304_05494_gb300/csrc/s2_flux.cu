@@ -86,18 +86,22 @@ template <int DIR, int TV>
 struct TileGrid {
   static constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
   int n0, n1, n2;
-  __host__ __device__ TileGrid(const Dev &d) {
+  FastDiv f0, f1;  // divisions by n0 and n1 (set on the host)
+  __host__ TileGrid(const Dev &d) {
     if (DIR == 0) { n0 = (d.nx + L - 1) / L; n1 = (d.ny + W - 1) / W; n2 = d.nz; }
     if (DIR == 1) { n0 = (d.nx + W - 1) / W; n1 = (d.ny + L - 1) / L; n2 = d.nz; }
     if (DIR == 2) { n0 = (d.nx + W - 1) / W; n1 = (d.nz + L - 1) / L; n2 = d.ny; }
+    f0.init((unsigned)n0);
+    f1.init((unsigned)n1);
   }
   __host__ __device__ int count() const { return n0 * n1 * n2; }
   // first interior point of the tile along (x, y, z)
-  __device__ void origin(int t, int &x0, int &y0, int &z0) const {
-    const int t0 = t % n0, r = t / n0, t1 = r % n1, t2 = r / n1;
-    if (DIR == 0) { x0 = t0 * L; y0 = t1 * W; z0 = t2; }
-    if (DIR == 1) { x0 = t0 * W; y0 = t1 * L; z0 = t2; }
-    if (DIR == 2) { x0 = t0 * W; z0 = t1 * L; y0 = t2; }
+  __device__ __forceinline__ void origin(int t, int &x0, int &y0, int &z0) const {
+    const unsigned r = f0.div((unsigned)t), t2 = f1.div(r);
+    const int t0 = t - (int)r * n0, t1 = (int)r - (int)t2 * n1;
+    if (DIR == 0) { x0 = t0 * L; y0 = t1 * W; z0 = (int)t2; }
+    if (DIR == 1) { x0 = t0 * W; y0 = t1 * L; z0 = (int)t2; }
+    if (DIR == 2) { x0 = t0 * W; z0 = t1 * L; y0 = (int)t2; }
   }
 };
 
@@ -125,7 +129,8 @@ constexpr size_t flux_smem() {
 // buffers of the next NBUF - 1 tiles while tile t is computed, so the HBM
 // reads of later tiles overlap the arithmetic of the current one.
 template <int DIR, bool HASW, class R, int TV, int NP>
-__global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d, int accumulate) {
+__global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d,
+                                                      const TileGrid<DIR, TV> tg, int accumulate) {
   using Ly = FluxLayout<DIR, R, TV>;
   constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA, NBUF = Ly::NBUF;
   constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
@@ -145,7 +150,6 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
   R *TP = Sbuf + NBUF * NFLD * SFA;                             // [NP][positions x pencils]
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
-  const TileGrid<DIR, TV> tg(d);
   const int ntiles = tg.count();
 
   const int tid = threadIdx.x;
@@ -565,9 +569,10 @@ cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaS
       b = 1;
     per_sm = b;
   }
-  const int ntiles = TileGrid<DIR, TV>(d).count();
+  const TileGrid<DIR, TV> tg(d);
+  const int ntiles = tg.count();
   const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm * d.nsm ? ntiles : per_sm * d.nsm);
-  k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(maps, d, accumulate);
+  k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(maps, d, tg, accumulate);
   return cudaGetLastError();
 }
 
