@@ -80,11 +80,23 @@ struct Tile<2, 1> {  // z: 16 along z, 16 columns
 constexpr int NTHREADS = 256;
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
+// The tile a kernel of arithmetic type R works on.  Double precision uses
+// the shapes above, one point per thread.  Single precision gives each
+// thread PPT = 2 points along the direction (half the per-tile overhead
+// per point) and, for y and z, twice the pencils across (64-byte rows in
+// place of 32-byte ones per box row).
+template <int DIR, int TV, class R>
+struct TileR {
+  static constexpr int PPT = sizeof(R) == 4 ? 2 : 1;
+  static constexpr int L = Tile<DIR, TV>::L * (sizeof(R) == 4 && DIR == 0 ? 2 : 1);
+  static constexpr int W = Tile<DIR, TV>::W * (sizeof(R) == 4 && DIR != 0 ? 2 : 1);
+};
+
 // Tiles of a direction: (n0, n1, n2) along the grid dimensions of the
 // tiling, tile t = (t0, t1, t2) with t0 fastest.
-template <int DIR, int TV>
+template <int DIR, int TV, class R>
 struct TileGrid {
-  static constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
+  static constexpr int L = TileR<DIR, TV, R>::L, W = TileR<DIR, TV, R>::W;
   int n0, n1, n2;
   FastDiv f0, f1;  // divisions by n0 and n1 (set on the host)
   __host__ TileGrid(const Dev &d) {
@@ -107,14 +119,16 @@ struct TileGrid {
 
 template <int DIR, class R, int TV>
 struct FluxLayout {
-  static constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W;
+  static constexpr int L = TileR<DIR, TV, R>::L, W = TileR<DIR, TV, R>::W;
+  static constexpr int PPT = TileR<DIR, TV, R>::PPT;
   static constexpr int LE = L + 2 * GH;                          // extended positions per pencil
   static constexpr int SF = LE * W;                              // words per staged field (one box)
   static constexpr int SFA = (SF * (int)sizeof(R) + 127) / 128 * 128 / (int)sizeof(R);  // 128-B aligned
   static constexpr int BAR_BYTES = 128;                          // mbarriers, padded
-  // staging buffers: single precision prefetches two tiles ahead; double
-  // precision runs one tile per CTA and stages it once
-  static constexpr int NBUF = sizeof(R) == 4 ? 3 : 1;
+  // staging buffers: single precision prefetches two tiles ahead in x and
+  // one in y and z (larger tiles); double precision runs one tile per CTA
+  // and stages it once
+  static constexpr int NBUF = sizeof(R) == 4 ? (DIR == 0 ? 3 : 2) : 1;
 };
 
 template <int DIR, bool HASW, class R, int TV, int NP>
@@ -130,9 +144,10 @@ constexpr size_t flux_smem() {
 // reads of later tiles overlap the arithmetic of the current one.
 template <int DIR, bool HASW, class R, int TV, int NP>
 __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d,
-                                                      const TileGrid<DIR, TV> tg, int accumulate) {
+                                                      const TileGrid<DIR, TV, R> tg, int accumulate) {
   using Ly = FluxLayout<DIR, R, TV>;
-  constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA, NBUF = Ly::NBUF;
+  constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA, NBUF = Ly::NBUF, PPT = Ly::PPT;
+  constexpr int LP = L / PPT;          // positions per pass of the CTA's threads
   constexpr int LT = L + NP;           // pair-flux positions a = -NP .. L-1
   constexpr int ST = LT * W;           // words per pair mass-flux slot
   constexpr int NFLD = HASW ? NF : F_S;  // the sensor is staged only for WENO
@@ -186,20 +201,25 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
     tg.origin(t, x0, y0, z0);
     const int s0 = DIR == 0 ? x0 : (DIR == 1 ? y0 : z0);
     const int c0 = DIR == 0 ? y0 : x0;
-    // this thread's point and, for y and z, its RHS so far (loaded while
-    // the tile is in flight)
-    int ta, tc;
-    if (DIR == 0) { ta = tid % L; tc = tid / L; }
-    else { tc = tid % W; ta = tid / W; }
-    const bool mine = (c0 + tc < nac) && (s0 + ta < n);
-    const int pi = DIR == 0 ? x0 + ta : x0 + tc;
-    const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta : y0);
-    const int pk = DIR == 2 ? z0 + ta : z0;
-    const long long q = ((long long)pk * d.ny + pj) * d.nx + pi;
-    R prev[5] = {R(0), R(0), R(0), R(0), R(0)};
-    if (mine && accumulate) {
+    // this thread's points (ta[p], tc) and, for y and z, their RHS so far
+    // (loaded while the tile is in flight)
+    int ta[PPT], tc;
+    if (DIR == 0) { ta[0] = tid % LP; tc = tid / LP; }
+    else { tc = tid % W; ta[0] = tid / W; }
 #pragma unroll
-      for (int f = 0; f < 5; ++f) prev[f] = V.fl[f * d.n + q];
+    for (int pp = 1; pp < PPT; ++pp) ta[pp] = ta[0] + pp * LP;
+    bool mine[PPT];
+    long long q[PPT];
+    R prev[PPT][5];
+#pragma unroll
+    for (int pp = 0; pp < PPT; ++pp) {
+      mine[pp] = (c0 + tc < nac) && (s0 + ta[pp] < n);
+      const int pi = DIR == 0 ? x0 + ta[pp] : x0 + tc;
+      const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
+      const int pk = DIR == 2 ? z0 + ta[pp] : z0;
+      q[pp] = ((long long)pk * d.ny + pj) * d.nx + pi;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) prev[pp][f] = (mine[pp] && accumulate) ? V.fl[f * d.n + q[pp]] : R(0);
     }
     bool late = false;
     if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it / NBUF) & 1u);
@@ -281,11 +301,13 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
     }
     __syncthreads();
 
-    // ---- 3. central flux difference of the thread's point -> RHS ----
-    if (mine) {
+    // ---- 3. central flux difference of the thread's points -> RHS ----
+#pragma unroll
+    for (int pp = 0; pp < PPT; ++pp) {
+      if (!mine[pp]) continue;
       R D[5];
-      const int at = (ta + NP) * SA + tc * SCT;
-      const int ap = (ta + GH) * SA + tc * SCS;
+      const int at = (ta[pp] + NP) * SA + tc * SCT;
+      const int ap = (ta[pp] + GH) * SA + tc * SCS;
       R mp[NP], mm[NP];                     // m_l(a), m_l(a-l)
       R M = R(0);
 #pragma unroll
@@ -311,9 +333,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
 #pragma unroll
       for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
       D[1 + DIR] += dp;
+      const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
       R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + pj) : K.idz);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) V.fl[f * d.n + q] = fma(-scale, D[f], prev[f]);
+      for (int f = 0; f < 5; ++f) V.fl[f * d.n + q[pp]] = fma(-scale, D[f], prev[pp][f]);
     }
     __syncthreads();  // staging buffer and TP free for the next tile
   }
@@ -569,7 +592,7 @@ cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaS
       b = 1;
     per_sm = b;
   }
-  const TileGrid<DIR, TV> tg(d);
+  const TileGrid<DIR, TV, R> tg(d);
   const int ntiles = tg.count();
   const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm * d.nsm ? ntiles : per_sm * d.nsm);
   k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(maps, d, tg, accumulate);
@@ -655,9 +678,10 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int DIR, int TV>
-cudaError_t make_map(const Dev &d, void *base, bool dbl, CUtensorMap *out) {
-  constexpr int L = Tile<DIR, TV>::L, W = Tile<DIR, TV>::W, LE = L + 2 * GH;
+template <int DIR, int TV, class R>
+cudaError_t make_map(const Dev &d, void *base, CUtensorMap *out) {
+  constexpr int L = TileR<DIR, TV, R>::L, W = TileR<DIR, TV, R>::W, LE = L + 2 * GH;
+  constexpr bool dbl = sizeof(R) == 8;
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const cuuint64_t es = dbl ? 8 : 4;
@@ -712,18 +736,25 @@ cudaError_t launch_flux(const Dev &d, const FluxMaps (&maps)[2], int dir, int ac
                  : flux_dispatch<double>(d, maps, dir, accumulate, st);
 }
 
+template <class R>
+cudaError_t make_maps_dir(const Dev &d, void *field, int f, FluxMaps (&maps)[3][2]) {
+  cudaError_t e = make_map<0, 0, R>(d, field, &maps[0][0].m[f]);
+  if (e == cudaSuccess) e = make_map<0, 1, R>(d, field, &maps[0][1].m[f]);
+  if (e == cudaSuccess) e = make_map<1, 0, R>(d, field, &maps[1][0].m[f]);
+  if (e == cudaSuccess) e = make_map<1, 1, R>(d, field, &maps[1][1].m[f]);
+  if (e == cudaSuccess) e = make_map<2, 0, R>(d, field, &maps[2][0].m[f]);
+  if (e == cudaSuccess) e = make_map<2, 1, R>(d, field, &maps[2][1].m[f]);
+  return e;
+}
+
 cudaError_t flux_make_maps(const Dev &d, FluxMaps (&maps)[3][2]) {
   void *fields[7] = {d.rho, d.u, d.v, d.ww, d.H, d.p, d.sens};
   const bool dbl = !d.mixed;
   cudaError_t e = cudaSuccess;
   for (int f = 0; f < 7 && e == cudaSuccess; ++f) {
     if ((uintptr_t)fields[f] % 16) return cudaErrorInvalidValue;
-    if (e == cudaSuccess) e = make_map<0, 0>(d, fields[f], dbl, &maps[0][0].m[f]);
-    if (e == cudaSuccess) e = make_map<0, 1>(d, fields[f], dbl, &maps[0][1].m[f]);
-    if (e == cudaSuccess) e = make_map<1, 0>(d, fields[f], dbl, &maps[1][0].m[f]);
-    if (e == cudaSuccess) e = make_map<1, 1>(d, fields[f], dbl, &maps[1][1].m[f]);
-    if (e == cudaSuccess) e = make_map<2, 0>(d, fields[f], dbl, &maps[2][0].m[f]);
-    if (e == cudaSuccess) e = make_map<2, 1>(d, fields[f], dbl, &maps[2][1].m[f]);
+    if (dbl) e = make_maps_dir<double>(d, fields[f], f, maps);
+    else e = make_maps_dir<float>(d, fields[f], f, maps);
   }
   return e;
 }
