@@ -297,6 +297,9 @@ def our_arm(args):
         per_launch = mms / max(ml, 1)
         peak, src = hbm_peak_gbs()
         ach = MIXED_BYTES[mname] * case.points / (per_launch * 1e-3) / 1e9
+        # every mixed kernel against the same HBM peak (algorithmic bytes)
+        kfrac = {k: MIXED_BYTES[k] * case.points / (v[0] / v[1] * 1e-3) / 1e9 / peak
+                 for k, v in prof_m.items() if k in MIXED_BYTES and v[1]}
         # error of the mixed path against the FP64 path after 10 steps from w0
         sm.set_state(case.w0)
         sm.set_clock(0.0, 0, 0.0)
@@ -313,7 +316,7 @@ def our_arm(args):
                  "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state",
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                               "traffic": None, "kernel": mname, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
-                              "per_launch_ms": per_launch,
+                              "per_launch_ms": per_launch, "hbm_frac_per_kernel": kfrac,
                               "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_m.items() if v[1]}},
                  "err_vs_fp64_after_10_steps": err}
 
