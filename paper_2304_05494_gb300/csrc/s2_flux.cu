@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
     int x0, y0, z0;
     tg.origin(t, x0, y0, z0);
     int bx = DIR == 0 ? x0 : x0 + GH, by = DIR == 1 ? y0 : y0 + GH, bz = DIR == 2 ? z0 : z0 + GH;
-    mbar_expect_tx(&bar[buf], TILE_BYTES);
+    mbar_expect_tx(&bar[buf], TILE_BYTES + d.tx_extra);
 #pragma unroll
     for (int f = 0; f < NFLD; ++f) tma_load_3d(Sbuf + (buf * NFLD + f) * SFA, &maps.m[f], bx, by, bz, &bar[buf]);
   };
@@ -222,13 +222,13 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       for (int f = 0; f < 5; ++f) prev[pp][f] = (mine[pp] && accumulate) ? V.fl[f * d.n + q[pp]] : R(0);
     }
     bool late = false;
-    if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it / NBUF) & 1u);
+    if (tid == 0) late = !mbar_wait_bounded(&bar[buf], (unsigned)(it / NBUF) & 1u, d.wait_ns);
     if (__syncthreads_or(late)) {
       if (tid == 0) {
         atomicOr(&d.scal->status, ERR_TIMEOUT);
         // let the copies already issued for the next tiles land (bounded)
         for (int j = 1; j < NBUF; ++j)
-          if (t + j * G < ntiles) mbar_wait_bounded(&bar[(it + j) % NBUF], (unsigned)((it + j) / NBUF) & 1u);
+          if (t + j * G < ntiles) mbar_wait_bounded(&bar[(it + j) % NBUF], (unsigned)((it + j) / NBUF) & 1u, d.wait_ns);
       }
       return;
     }

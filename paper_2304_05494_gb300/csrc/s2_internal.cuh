@@ -98,6 +98,8 @@ struct Dev {
   int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
   int tile[3];             // flux tile variant per direction (0 default, 1 narrow)
   int nsm;                 // multiprocessors of the device
+  unsigned long long wait_ns;  // limit of a kernel's wait for an asynchronous copy
+  unsigned tx_extra;       // bytes a staging barrier expects beyond its copies (0; test hook)
   Consts<double> kd;
   Consts<float> kf;
   // state (FP64 in both modes; interior layout [v][k][j][i])
@@ -352,12 +354,24 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
   return ok != 0;
 }
 
-// Wait for the phase with the given parity; gives up after a bounded number
-// of polls (each try_wait itself suspends for a short while).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+// Wait for the phase with the given parity; gives up (false) once limit_ns
+// of global time have passed, so a copy that never completes cannot hang
+// the kernel.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
@@ -381,6 +395,10 @@ cudaError_t launch_flux(const Dev &d, const FluxMaps (&maps)[2], int dir, int ac
 cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st);
 cudaError_t launch_grad(const Dev &d, cudaStream_t st);
 cudaError_t launch_visc(const Dev &d, cudaStream_t st);
+// Forcing partials the viscous launch writes itself (mixed path), else 0;
+// CTAs of the mixed path's z-marching passes.
+int visc_force_partials(const Dev &d);
+long long z_pass_blocks(const Dev &d);
 cudaError_t launch_apply(const Dev &d, cudaStream_t st);
 cudaError_t flux_set_attributes();
 

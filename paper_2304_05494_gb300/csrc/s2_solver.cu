@@ -676,7 +676,12 @@ cudaError_t enqueue_rhs(s2_solver *s, int stage0, Trace *tr) {
     if (e != cudaSuccess) return e;
   }
   if (d.force) {
-    e = run(tr, st, S2_PROF_FORCE, 2, [&] {
+    const int fused = visc_force_partials(d);  // partials already written by the viscous pass
+    e = run(tr, st, S2_PROF_FORCE, fused ? 1 : 2, [&] {
+      if (fused) {
+        k_force_final<<<1, NT, 0, st>>>(d, fused);
+        return cudaGetLastError();
+      }
       if (d.mixed) k_force_partial<float><<<NRED, NT, 0, st>>>(d);
       else k_force_partial<double><<<NRED, NT, 0, st>>>(d);
       k_force_final<<<1, NT, 0, st>>>(d, NRED);
@@ -893,6 +898,19 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.fnx1.init((unsigned)grid->nx + 1u);
   d.fny1.init((unsigned)grid->ny + 1u);
   if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || d.nsm < 1) d.nsm = 1;
+  // bounded waits for asynchronous copies: 2 s.  S2_TEST_STALL_COPIES=1 in
+  // the environment makes every staging barrier expect 16 bytes more than
+  // its copies deliver, with a 20 ms limit: the waits run out, the kernels
+  // return and the step reports S2_ETIMEOUT (failure-detection test; no
+  // fault, the copies themselves complete).
+  d.wait_ns = 2000000000ull;
+  d.tx_extra = 0;
+  if (const char *ev = getenv("S2_TEST_STALL_COPIES")) {
+    if (atoi(ev) > 0) {
+      d.tx_extra = 16;
+      d.wait_ns = 20000000ull;
+    }
+  }
   d.dx = grid->lx / grid->nx;
   d.dz = grid->lz / grid->nz;
   d.idx = 1.0 / d.dx;
@@ -995,6 +1013,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (!etaf || !ayf || !byf || !ryf) ok = false;
   size_t nparts = (size_t)((n + NT - 1) / NT);
   if (nparts < (size_t)NRED * NSTAT) nparts = (size_t)NRED * NSTAT;
+  if (nparts < (size_t)z_pass_blocks(d)) nparts = (size_t)z_pass_blocks(d);  // forcing partials of k_visc_z
   d.part = A(nparts);
   d.scal = (Scal *)dalloc(s, sizeof(Scal));
   if (!d.scal) ok = false;

@@ -446,6 +446,7 @@ __global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
     for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + t.z0 * sz) : R(0);
   }
   const int c = t.centre();
+  R fsum = R(0);  // the column's R_rho u, for the bulk forcing
   for (int k = t.z0; k < t.z1; ++k) {
     const int b = (k - t.z0) & 1;
     const long long qi = ((long long)k * d.ny + t.j) * d.nx + t.i;  // interior index
@@ -519,13 +520,31 @@ __global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
       if (d.weno) V.fl[qi] = Rv[0];
 #pragma unroll
       for (int f = 1; f < NV; ++f) V.fl[f * d.n + qi] = Rv[f];
+      fsum += Rv[1];
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int m = 0; m < NQ - 1; ++m) q[f][m] = q[f][m + 1];
   }
+  // forcing: this CTA's share of sum R_rho u dV (dV ~ dy/deta), summed in
+  // double in a fixed order into part[CTA]
+  if (d.force) {
+    double v = t.active ? (double)fsum * d.dvy[t.j] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double wsum[NT / 32];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < NT / 32; ++w) tot += wsum[w];
+      d.part[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+    }
+  }
 }
+
 
 template <class R>
 void grad_np(const Dev &d, unsigned nb, cudaStream_t st) {
@@ -573,6 +592,16 @@ cudaError_t launch_apply(const Dev &d, cudaStream_t st) {
   if (d.mixed) k_apply<float><<<nb, NT, 0, st>>>(d);
   else k_apply<double><<<nb, NT, 0, st>>>(d);
   return cudaGetLastError();
+}
+
+long long z_pass_blocks(const Dev &d) {
+  dim3 g = zgrid(d);
+  return (long long)g.x * g.y * g.z;
+}
+
+int visc_force_partials(const Dev &d) {
+  if (!(d.mixed && d.force && d.viscous)) return 0;
+  return (int)z_pass_blocks(d);
 }
 
 cudaError_t launch_visc(const Dev &d, cudaStream_t st) {

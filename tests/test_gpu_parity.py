@@ -319,3 +319,28 @@ def test_scheme_variants_channel_10_steps(s2, orders):
     err = field_err(w, ref)
     print("orders %s: state error after 10 steps" % (orders,), err)
     assert np.all(err < STEP_TOL), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stalled_copy_reported_as_timeout(s2, monkeypatch, precision):
+    """Failure detection without a fault: with S2_TEST_STALL_COPIES=1 every
+    staging barrier of the convective kernels expects 16 bytes more than
+    its tensor-memory copies deliver (a completion that never comes), the
+    kernels' bounded waits (20 ms) run out, the kernels return, and the
+    step reports S2_ETIMEOUT.  The context stays usable: a solver created
+    afterwards steps normally and matches a clean run."""
+    c = W.taylor_green(16)
+    monkeypatch.setenv("S2_TEST_STALL_COPIES", "1")
+    with s2.Solver.from_case(c, cfl=0.0, dt_fixed=1e-3, precision=precision) as sv:
+        sv.set_state(c.w0)
+        sv.step(1)
+        with pytest.raises(s2.S2Error) as ei:
+            sv.sync()
+        assert ei.value.code == s2.S2_ETIMEOUT
+    monkeypatch.delenv("S2_TEST_STALL_COPIES")
+    with s2.Solver.from_case(c, cfl=0.0, dt_fixed=1e-3, precision=precision) as sv:
+        sv.set_state(c.w0)
+        sv.step(2)
+        sv.sync()
+        w = sv.get_state()
+    assert np.all(np.isfinite(w))
