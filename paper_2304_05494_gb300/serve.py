@@ -13,7 +13,10 @@ buffers, deterministic kernels), so a result is the same alone and in the
 mix.
 
 Reported: throughput (point-steps/s over the run), p50/p99 of the per-step
-latency seen by requests (tick time / steps per tick), queueing delay.
+latency seen by requests (tick time / steps per tick), queueing delay.  A
+request whose solve fails on the device (e.g. a non-positive density,
+S2_ENONFINITE) is retired with that status and a request its client
+cancels is retired at the next tick; the others continue unaffected.
 """
 from __future__ import annotations
 
@@ -47,9 +50,12 @@ class Request:
     precision: str     # "fp64" or "mixed"
     seed: int
     arrival: float = 0.0
+    cancel_after: Optional[int] = None  # the client cancels after this many steps (None: never)
+    corrupt: bool = False               # fault injection: a negative density in the initial state
     # filled by the server
     admitted: Optional[float] = None
     finished: Optional[float] = None
+    status: str = "pending"             # "done", "cancelled" or "failed: <error>"
     result: Optional[np.ndarray] = field(default=None, repr=False)
 
     @property
@@ -90,6 +96,9 @@ def initial_case(req: Request) -> W.Case:
     c.threshold = 0.2
     c.cfl = 0.8
     c.dt_every = 10
+    if req.corrupt:
+        c.w0 = c.w0.copy()
+        c.w0[0, req.n // 2, req.n // 3, req.n // 4] = -1.0
     return c
 
 
@@ -108,6 +117,14 @@ class Server:
         self.k = steps_per_tick
         self.keep = keep_results
         self.stream = stream
+
+    @staticmethod
+    def _left(a) -> int:
+        """Steps the tick may take for one active entry (request, solver, remaining)."""
+        r, left = a[0], a[2]
+        if r.cancel_after is not None:
+            left = min(left, max(r.cancel_after - (r.steps - a[2]), 1))
+        return left
 
     def _bytes(self, req: Request) -> float:
         n = req.n
@@ -148,27 +165,42 @@ class Server:
                     batch.close()
                 batch = s2.Batch([a[1] for a in active], self.stream)
                 changed = False
-            k = min(self.k, min(a[2] for a in active))
+            # a tick never runs past a request's end or its client's cancel
+            k = min(self.k, min(self._left(a) for a in active))
             ts = time.perf_counter()
             batch.step(k)
-            batch.sync()
+            try:
+                batch.sync()
+                failed = []
+            except s2.S2Error:
+                # find the members whose device status is bad; the others'
+                # buffers are their own, so they continue unaffected
+                failed = []
+                for a in active:
+                    try:
+                        a[1].sync()
+                    except s2.S2Error as e:
+                        failed.append((a, e))
             dt_tick = time.perf_counter() - ts
             ticks += 1
             lat.append((dt_tick / k, len(active), k))
             for a in active:
                 a[2] -= k
                 done_points += a[0].points * k
-            finished = [a for a in active if a[2] == 0]
-            if finished:
+            bad = {id(a) for a, _ in failed}
+            retire = [(a, "failed: " + s2.s2_strerror(e.code)) for a, e in failed]
+            retire += [(a, "done") for a in active if a[2] == 0 and id(a) not in bad]
+            retire += [(a, "cancelled") for a in active if a[2] > 0 and id(a) not in bad
+                       and a[0].cancel_after is not None and a[0].steps - a[2] >= a[0].cancel_after]
+            if retire:
                 batch.close()
                 batch = None
                 changed = True
-                for a in finished:
+                for a, status in retire:
                     r, sv = a[0], a[1]
-                    if self.keep:
+                    r.status = status
+                    if self.keep and status == "done":
                         r.result = sv.get_state()
-                    else:
-                        sv.sync()
                     sv.close()
                     r.finished = time.perf_counter() - t0
                     used -= self._bytes(r)
@@ -188,7 +220,10 @@ class Server:
             return float(vals[order][np.searchsorted(cw, p)]) if len(vals) else float("nan")
 
         waits = np.array([r.admitted - r.arrival for r in reqs])
-        return {"requests": len(reqs), "wall_s": wall, "point_steps": done_points,
+        return {"requests": len(reqs), "done": sum(r.status == "done" for r in reqs),
+                "cancelled": sum(r.status == "cancelled" for r in reqs),
+                "failed": sum(r.status.startswith("failed") for r in reqs),
+                "wall_s": wall, "point_steps": done_points,
                 "throughput": done_points / wall, "ticks": ticks,
                 "p50_step_latency_ms": pct(0.5) * 1e3, "p99_step_latency_ms": pct(0.99) * 1e3,
                 "p50_queue_s": float(np.percentile(waits, 50)), "p99_queue_s": float(np.percentile(waits, 99))}

@@ -91,3 +91,62 @@ def test_serving_results_same_alone_and_in_the_mix(s2):
         c = serve.initial_case(r)
         alone = solo(s2, c, r.steps, precision=r.precision)
         assert np.array_equal(r.result, alone), r.rid
+
+
+def test_serving_isolates_failed_and_cancelled_requests(s2):
+    """Fault injection on the host side of the serving loop: one request
+    starts from a state with a negative density (the device flags it:
+    S2_ENONFINITE), one is cancelled by its client after 8 steps; both are
+    retired while the batch keeps running, and the other requests' results
+    are bit-identical to their solo runs."""
+    from paper_2304_05494_gb300 import serve
+    reqs = serve.make_requests(4, seed=21, sizes=(24, 32), steps=(16, 24), precisions=("fp64", "mixed"))
+    for i, r in enumerate(reqs):
+        r.arrival = 0.0
+    reqs[1].corrupt = True
+    reqs[2].cancel_after = 8
+    out = serve.Server(max_slots=4, steps_per_tick=4, keep_results=True).run(reqs)
+    assert reqs[1].status == "failed: " + s2.s2_strerror(s2.S2_ENONFINITE)
+    assert reqs[2].status == "cancelled" and reqs[2].result is None
+    assert out["failed"] == 1 and out["cancelled"] == 1 and out["done"] == 2
+    for r in (reqs[0], reqs[3]):
+        assert r.status == "done"
+        alone = solo(s2, serve.initial_case(r), r.steps, precision=r.precision)
+        assert np.array_equal(r.result, alone), r.rid
+
+
+def test_allocation_failure_releases_everything(s2):
+    """An allocator callback that runs dry part-way through s2_create: the
+    call returns S2_ENOMEM and hands every block it did get back to the
+    callback's free."""
+    import ctypes as C
+    torch = pytest.importorskip("torch")
+    live = {}
+    calls = {"alloc": 0}
+
+    @s2._ALLOC
+    def alloc(nbytes, ctx):
+        calls["alloc"] += 1
+        if calls["alloc"] > 6:
+            return None
+        p = torch.cuda.caching_allocator_alloc(max(int(nbytes), 16))
+        live[p] = nbytes
+        return p
+
+    @s2._FREE
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+        del live[ptr]
+
+    g = s2.s2_grid(24, 20, 16, 1.0, 1.0, 1.0)
+    gas = s2.s2_gas(1.4, 0.72, 0.5, 100.0, 0.76, 1.0)
+    b = s2.s2_bcs(0, 0, 0, 1.0, 0)
+    sch = s2.s2_scheme(6, 5, 6, 0.2, 0, 0.8, 0.0, 10)
+    dev = s2.s2_device()
+    dev.alloc = alloc
+    dev.free = free
+    dev.device = -1
+    h = C.c_void_p()
+    rc = s2._lib.s2_create(C.byref(g), None, C.byref(gas), C.byref(b), C.byref(sch), C.byref(dev), C.byref(h))
+    assert rc == s2.S2_ENOMEM
+    assert calls["alloc"] > 6 and not live
