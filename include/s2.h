@@ -45,6 +45,7 @@ extern "C" {
 #define S2_ETIMEOUT -5    /* a bounded device wait gave up */
 #define S2_EBUSY -6       /* solver busy (reserved) */
 #define S2_ETOOBIG -7     /* larger than the fixed scratch of s2_cfl_dt_noalloc */
+#define S2_EBOUNDS -8     /* an index left its array (bounds-checked build libs2_checked.so only) */
 
 #define S2_BC_PERIODIC 0
 #define S2_BC_ISOTHERMAL_WALL 1

@@ -2,6 +2,11 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
 shared library with the CUDA runtime linked statically.  No CMake.
+
+The checked variant libs2_checked.so (-DS2_CHECKED) tests the index
+arithmetic of every kernel against its array before each access and
+reports S2_EBOUNDS instead of touching memory out of range; the binding
+loads it when S2_LIBRARY=checked.
 """
 from __future__ import annotations
 
@@ -15,6 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libs2.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libs2_checked.so")
 SOURCES = ["s2_solver.cu", "s2_flux.cu", "s2_visc.cu", "s2_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
@@ -33,23 +39,21 @@ def _deps() -> list:
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def _build_one(lib: str, defines: list, verbose: bool) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    tag = os.path.splitext(os.path.basename(lib))[0]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(OUT_DIR, "%s_%s.o" % (tag, os.path.splitext(src)[0]))
+        cmd = [nvcc, *ARCH, *FLAGS, *defines, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,12 +63,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = True) -> str:
+    """Build libs2.so and (checked=True) libs2_checked.so, each when out of
+    date; returns the path of libs2.so."""
+    jobs = []
+    if force or not up_to_date(LIB):
+        jobs.append((LIB, []))
+    if checked and (force or not up_to_date(LIB_CHECKED)):
+        jobs.append((LIB_CHECKED, ["-DS2_CHECKED"]))
+    if jobs:
+        with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            list(ex.map(lambda j: _build_one(j[0], j[1], verbose), jobs))
     return LIB
 
 

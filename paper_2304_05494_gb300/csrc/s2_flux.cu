@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
       const int pk = DIR == 2 ? z0 + ta[pp] : z0;
       q[pp] = ((long long)pk * d.ny + pj) * d.nx + pi;
+      if (mine[pp] && !S2_OK_IDX(d, q[pp], d.n)) mine[pp] = false;
 #pragma unroll
       for (int f = 0; f < 5; ++f) prev[pp][f] = (mine[pp] && accumulate) ? V.fl[f * d.n + q[pp]] : R(0);
     }
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
             if (flag && a >= 0) mycount++;
             int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
             slot = islot(d, DIR, s, i, j, k);
-            d.flag[DIR][slot] = flag;
+            if (!S2_OK_IDX(d, slot, d.nslot[DIR])) flag = false;
+            else d.flag[DIR][slot] = flag;
           }
         }
         unsigned bal = __ballot_sync(0xffffffffu, flag);
@@ -293,7 +295,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
           unsigned off = 0;
           if (lane == leader) off = atomicAdd(&d.scal->nlist[DIR], (unsigned)__popc(bal));
           off = __shfl_sync(0xffffffffu, off, leader);
-          if (flag) d.wlist[DIR][off + __popc(bal & ((1u << lane) - 1u))] = (unsigned)slot;
+          const long long at = (long long)off + __popc(bal & ((1u << lane) - 1u));
+          if (flag && S2_OK_IDX(d, at, d.nslot[DIR])) d.wlist[DIR][at] = (unsigned)slot;
         }
       }
       for (int o = 16; o > 0; o >>= 1) mycount += __shfl_xor_sync(0xffffffffu, mycount, o);
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       for (int l = 1; l <= NP; ++l) dp = fma(R(acoef<NP>(l)), Sp[ap + l * SA] - Sp[ap - l * SA], dp);
       D[1 + DIR] += dp;
       const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
+      if (DIR == 1 && !S2_OK_IDX(d, pj, d.ny)) continue;
       R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + pj) : K.idz);
 #pragma unroll
       for (int f = 0; f < 5; ++f) V.fl[f * d.n + q[pp]] = fma(-scale, D[f], prev[pp][f]);
@@ -448,6 +452,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
   const R *vel[3] = {V.u, V.v, V.ww};
   const R bq = K.gamma - R(1);
   for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < cnt; e0 += gridDim.x * blockDim.x) {
+    if (!S2_OK_IDX(d, e0, d.nslot[DIR])) break;
     const long long slot = d.wlist[DIR][e0];
     int i = 0, j = 0, k = 0, s;
     const unsigned us = (unsigned)slot;
@@ -472,6 +477,10 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     }
     const long long stride = DIR == 0 ? 1 : (DIR == 1 ? d.sy : d.sz);
     const long long p0 = pidx(d, i, j, k);  // point s of the interface s+1/2
+    // the WENO stencil and the central pairs reach p0 - 3 stride .. p0 + 4 stride
+    if (!(S2_OK_IDX(d, slot, d.nslot[DIR]) && S2_OK_IDX(d, p0 - 3 * stride, d.np) &&
+          S2_OK_IDX(d, p0 + 4 * stride, d.np)))
+      continue;
 
     // --- central split-form flux at this interface (order 2 npc)
     R FC[5] = {R(0), R(0), R(0), R(0), R(0)}, fp = R(0);

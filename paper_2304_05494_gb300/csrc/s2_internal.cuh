@@ -31,6 +31,7 @@ struct Scal {
 // Error bits written by kernels (mapped to S2_ENONFINITE on the host).
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_TIMEOUT = 2;  // a bounded wait on an asynchronous copy gave up
+constexpr int ERR_BOUNDS = 4;   // an index left its array (checked build)
 
 // Scheme constants in the arithmetic type R of a kernel (double for the
 // FP64 path, float for the flux arithmetic of the mixed path).
@@ -79,6 +80,8 @@ struct Dev {
   long long sy, sz;        // padded strides
   long long off0;          // padded offset of interior point (0,0,0)
   long long n;             // nx*ny*nz (< 2^31; slot counts < 2^32)
+  long long np;            // px*py*pz: elements of a padded field
+  long long nparts;        // elements of the reduction partials
   FastDiv fnx, fny, fnx1, fny1;  // divisions by nx, ny, nx+1, ny+1
   double dx, dz, idx, idz;  // spacings and their inverses
   double ax[5], az[5];     // a_l/dx, a_l/dz (first derivative, viscous order, l = 1..4)
@@ -194,6 +197,23 @@ __device__ __forceinline__ void point_of(const Dev &d, long long q, int &i, int 
   j = (int)(t - kk * (unsigned)d.ny);
   k = (int)kk;
 }
+
+// Bounds checks of the checked build (-DS2_CHECKED): each index is tested
+// against its array before the access it guards; a failure records
+// ERR_BOUNDS and the access is skipped.  The release build compiles the
+// tests away (S2_OK_IDX is then constant true).
+#ifdef S2_CHECKED
+__device__ __forceinline__ bool s2_idx_ok(const Dev &d, long long i, long long size) {
+  if (i >= 0 && i < size) return true;
+  atomicOr(&d.scal->status, ERR_BOUNDS);
+  return false;
+}
+#define S2_OK_IDX(d, i, size) s2_idx_ok((d), (long long)(i), (long long)(size))
+#define S2_GUARD(ok) if (ok)
+#else
+#define S2_OK_IDX(d, i, size) true
+#define S2_GUARD(ok)
+#endif
 
 // j of interior point q.
 __device__ __forceinline__ int row_of(const Dev &d, long long q) {

@@ -141,7 +141,7 @@ __device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_d
     if (threadIdx.x < 32) {
       double s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
       s = warp_max(s);
-      if (threadIdx.x == 0) d.part[blockIdx.x] = s;
+      if (threadIdx.x == 0 && S2_OK_IDX(d, blockIdx.x, d.nparts)) d.part[blockIdx.x] = s;
     }
   }
 }
@@ -176,13 +176,16 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
     double q2 = u * u + v * v + ww * ww;
     double T = (w[4 * d.n + q] * ri - 0.5 * q2) * d.icv;
     double pr = rho * d.R * T;
-    V.rho[p] = rho;
-    V.u[p] = u;
-    V.v[p] = v;
-    V.ww[p] = ww;
-    V.T[p] = T;
-    V.p[p] = pr;
-    V.H[p] = d.cp * T + 0.5 * q2;
+    const bool okp = S2_OK_IDX(d, p, d.np);
+    S2_GUARD(okp) {
+      V.rho[p] = rho;
+      V.u[p] = u;
+      V.v[p] = v;
+      V.ww[p] = ww;
+      V.T[p] = T;
+      V.p[p] = pr;
+      V.H[p] = d.cp * T + 0.5 * q2;
+    }
     double mu = 0.0;
     if (d.viscous) {
       mu = viscosity(d, T);
@@ -219,13 +222,16 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
     float q2 = u * u + v * v + ww * ww;
     const float rhoe = d2f_int(w[4 * d.n + q] - f2d_int(0.5f * rf * q2));
     float T = rhoe * rif * K.icv;
-    V.rho[p] = rf;
-    V.u[p] = u;
-    V.v[p] = v;
-    V.ww[p] = ww;
-    V.T[p] = T;
-    V.p[p] = rf * K.R_gas * T;
-    V.H[p] = K.cp * T + 0.5f * q2;
+    const bool okp = S2_OK_IDX(d, p, d.np);
+    S2_GUARD(okp) {
+      V.rho[p] = rf;
+      V.u[p] = u;
+      V.v[p] = v;
+      V.ww[p] = ww;
+      V.T[p] = T;
+      V.p[p] = rf * K.R_gas * T;
+      V.H[p] = K.cp * T + 0.5f * q2;
+    }
     float mu = 0.0f;
     if (d.viscous) {
       mu = viscosity(d, T);
@@ -250,6 +256,7 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
 __global__ void k_dt_final(Dev d, int nparts) {
   if (!dt_due(d)) return;
   double m = 0.0;
+  if (!S2_OK_IDX(d, nparts - 1, d.nparts)) nparts = 0;
   for (int b = threadIdx.x; b < nparts; b += NT) m = fmax(m, d.part[b]);
   __shared__ double red[NT / 32];
   m = warp_max(m);
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
   int di, dj, dk, si, sj, sk;
   bool wall = ghost_map(d, t, di, dj, dk, si, sj, sk);
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
+  if (!(S2_OK_IDX(d, dp, d.np) && S2_OK_IDX(d, sp, d.np))) return;
   if (!wall) {
     V.rho[dp] = V.rho[sp];
     V.u[dp] = V.u[sp];
@@ -355,11 +363,13 @@ __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
   int di, dj, dk, si, sj, sk;
   bool wall = ghost_map(d, t, di, dj, dk, si, sj, sk);
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
+  if (!(S2_OK_IDX(d, dp, d.np) && S2_OK_IDX(d, sp, d.np))) return;
   V.sens[dp] = V.sens[sp];
   if (!wall) {
     V.div[dp] = V.div[sp];
   } else if (!d.mixed) {  // the mixed path's gradient pass writes these itself
     long long q = ((long long)sk * d.ny + sj) * d.nx + si;
+    if (!S2_OK_IDX(d, q, d.n)) return;
     R ux = V.g[0 * d.n + q], vy = V.g[4 * d.n + q], wz = V.g[8 * d.n + q];
     V.div[dp] = -ux + vy - wz;
   }
@@ -386,11 +396,12 @@ __global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
   }
   double v[1] = {s};
   block_sum<1>(v);
-  if (threadIdx.x == 0) d.part[blockIdx.x] = v[0];
+  if (threadIdx.x == 0 && S2_OK_IDX(d, blockIdx.x, d.nparts)) d.part[blockIdx.x] = v[0];
 }
 
 __global__ void k_force_final(Dev d, int nparts) {
   double s = 0.0;
+  if (!S2_OK_IDX(d, nparts - 1, d.nparts)) nparts = 0;
   for (int b = threadIdx.x; b < nparts; b += NT) s += d.part[b];
   double v[1] = {s};
   block_sum<1>(v);
@@ -411,7 +422,8 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
     if (d.force) {
       int i, j, k;
       point_of(d, q, i, j, k);
-      fu = f * V.u[pidx(d, i, j, k)];
+      const long long pu = pidx(d, i, j, k);
+      if (S2_OK_IDX(d, pu, d.np)) fu = f * V.u[pu];
     }
     const double a = dt * gk, b = dt * rk1;
 #pragma unroll
@@ -445,7 +457,8 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
     if (d.force) {
       int i, j, k;
       point_of(d, q, i, j, k);
-      fu = f * V.u[pidx(d, i, j, k)];
+      const long long pu = pidx(d, i, j, k);
+      if (S2_OK_IDX(d, pu, d.np)) fu = f * V.u[pu];
     }
     const float a = (float)(dt * gk), b = (float)(dt * rk1);
 #pragma unroll
@@ -511,14 +524,16 @@ __global__ void __launch_bounds__(NT) k_stats_partial(Dev d) {
   }
   block_sum<NSTAT>(v);
   if (threadIdx.x == 0)
-    for (int m = 0; m < NSTAT; ++m) d.part[m * NRED + blockIdx.x] = v[m];
+    for (int m = 0; m < NSTAT; ++m)
+      if (S2_OK_IDX(d, m * NRED + blockIdx.x, d.nparts)) d.part[m * NRED + blockIdx.x] = v[m];
 }
 
 __global__ void k_stats_final(Dev d, int nparts) {
   double v[NSTAT];
   for (int m = 0; m < NSTAT; ++m) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < nparts; b += NT) s += d.part[m * NRED + b];
+    for (int b = threadIdx.x; b < nparts; b += NT)
+      if (S2_OK_IDX(d, m * NRED + b, d.nparts)) s += d.part[m * NRED + b];
     v[m] = s;
   }
   block_sum<NSTAT>(v);
@@ -746,6 +761,7 @@ int read_status(s2_solver *s) {
   if (cudaMemcpyAsync(&st, &s->d.scal->status, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
     return S2_ECUDA;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
+  if (st & ERR_BOUNDS) return S2_EBOUNDS;
   if (st & ERR_NONFINITE) return S2_ENONFINITE;
   if (st & ERR_TIMEOUT) return S2_ETIMEOUT;
   return S2_OK;
@@ -808,6 +824,7 @@ const char *s2_strerror(int code) {
     case S2_ETIMEOUT: return "device wait timed out";
     case S2_EBUSY: return "solver busy";
     case S2_ETOOBIG: return "grid larger than the fixed scratch of the allocation-free entry point";
+    case S2_EBOUNDS: return "index out of its array's bounds (checked build)";
   }
   return "unknown error";
 }
@@ -983,6 +1000,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   }
 
   size_t np = (size_t)d.px * d.py * d.pz;
+  d.np = (long long)np;
   size_t nn = (size_t)n;
   const size_t rs = d.mixed ? sizeof(float) : sizeof(double);  // bytes of the arithmetic type
   s->rsize = rs;
@@ -1015,6 +1033,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (nparts < (size_t)NRED * NSTAT) nparts = (size_t)NRED * NSTAT;
   if (nparts < (size_t)z_pass_blocks(d)) nparts = (size_t)z_pass_blocks(d);  // forcing partials of k_visc_z
   d.part = A(nparts);
+  d.nparts = (long long)nparts;
   d.scal = (Scal *)dalloc(s, sizeof(Scal));
   if (!d.scal) ok = false;
   s->flag_bytes[0] = (size_t)grid->nz * grid->ny * (grid->nx + 1);
@@ -1250,7 +1269,10 @@ int s2_stats(s2_solver *s, s2_stats_t *out) {
   out->weno_frac = s->d.weno ? (double)h.wcount / (3.0 * (double)s->d.n) : 0.0;
   out->forcing = h.force;
   out->launches = s->launches;
-  out->status = (h.status & ERR_NONFINITE) ? S2_ENONFINITE : (h.status & ERR_TIMEOUT) ? S2_ETIMEOUT : S2_OK;
+  out->status = (h.status & ERR_BOUNDS)      ? S2_EBOUNDS
+                : (h.status & ERR_NONFINITE) ? S2_ENONFINITE
+                : (h.status & ERR_TIMEOUT)   ? S2_ETIMEOUT
+                                             : S2_OK;
   return out->status;
 }
 

@@ -81,6 +81,7 @@ __device__ __forceinline__ void weno_correction(const Dev &d, const View<R> &V, 
   for (int dir = 0; dir < 3; ++dir) {
     int pos = dir == 0 ? i : (dir == 1 ? j : k);
     long long lo = islot(d, dir, pos - 1, i, j, k), hi = islot(d, dir, pos, i, j, k);
+    if (!(S2_OK_IDX(d, lo, d.nslot[dir]) && S2_OK_IDX(d, hi, d.nslot[dir]))) continue;
     bool fl = d.flag[dir][lo], fh = d.flag[dir][hi];
     if (fl || fh) {
       R scale = dir == 0 ? K.idx : (dir == 1 ? __ldg(V.eta_y + j) : K.idz);
@@ -179,6 +180,8 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
   int i, j, k;
   point_of(d, q, i, j, k);
   long long p = pidx(d, i, j, k);
+  // the stencils reach p -+ NP sz (z is the largest stride)
+  if (!(S2_OK_IDX(d, p - NP * d.sz, d.np) && S2_OK_IDX(d, p + NP * d.sz, d.np))) return;
   C5<R> cx, cy, cz;
   coeffs<NP>(d, V, j, cx, cy, cz);
   const R *vel[3] = {V.u, V.v, V.ww};
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   int i, j, k;
   point_of(d, q, i, j, k);
   long long p = pidx(d, i, j, k);
+  if (!(S2_OK_IDX(d, p - NP * d.sz, d.np) && S2_OK_IDX(d, p + NP * d.sz, d.np))) return;
   C5<R> cx, cy, cz, bx, by, bz;
   coeffs<NP>(d, V, j, cx, cy, cz);
 #pragma unroll
@@ -313,6 +317,9 @@ struct ZTile {
     active = i < d.nx && j < d.ny;
     cvalid = i < d.nx + GH && j < d.ny + GH;
     cbase = cvalid ? pidx(d, i, j, 0) : 0;
+    // loads reach planes z0 - NP .. z1 - 1 + NP of the column and its halo
+    if (cvalid && !(S2_OK_IDX(d, cbase + (z0 - NP) * d.sz, d.np) && S2_OK_IDX(d, cbase + (z1 - 1 + NP) * d.sz, d.np)))
+      cvalid = active = false;
 #pragma unroll
     for (int s = 0; s < ZGeom<NP>::HPT; ++s) {
       int h = tid + s * NT, hx = 0, hy = 0;
@@ -324,6 +331,9 @@ struct ZTile {
         if (ii < d.nx + GH && jj < d.ny + GH) {
           hoff[s] = hy * SX + hx;
           hbase[s] = pidx(d, ii, jj, 0);
+          if (!(S2_OK_IDX(d, hbase[s] + (z0 - NP) * d.sz, d.np) &&
+                S2_OK_IDX(d, hbase[s] + (z1 - 1 + NP) * d.sz, d.np)))
+            hoff[s] = -1;
         }
       }
     }
@@ -401,8 +411,9 @@ __global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
       // wall ghosts of theta: the divergence of the mirrored velocity
       // field at the mirror node is -u_x + v_y - w_z
       if (d.wall_y) {
-        if (t.j < GH) V.div[pidx(d, t.i, -1 - t.j, k)] = -g[0][0] + g[1][1] - g[2][2];
-        if (t.j >= d.ny - GH) V.div[pidx(d, t.i, 2 * d.ny - 1 - t.j, k)] = -g[0][0] + g[1][1] - g[2][2];
+        const long long plo = pidx(d, t.i, -1 - t.j, k), phi = pidx(d, t.i, 2 * d.ny - 1 - t.j, k);
+        if (t.j < GH && S2_OK_IDX(d, plo, d.np)) V.div[plo] = -g[0][0] + g[1][1] - g[2][2];
+        if (t.j >= d.ny - GH && S2_OK_IDX(d, phi, d.np)) V.div[phi] = -g[0][0] + g[1][1] - g[2][2];
       }
       if (d.weno) V.sens[p] = sensor_test(K, g, th);
     }

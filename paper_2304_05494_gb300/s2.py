@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 S2_OK, S2_EINVAL, S2_ENOMEM, S2_ECUDA, S2_ENONFINITE, S2_ETIMEOUT, S2_EBUSY = 0, -1, -2, -3, -4, -5, -6
-S2_ETOOBIG = -7
+S2_ETOOBIG, S2_EBOUNDS = -7, -8
 S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL = 0, 1
 S2_HOST, S2_DEVICE = 0, 1
 S2_FP64, S2_MIXED = 0, 1
@@ -76,9 +76,10 @@ S2_PROF_KINDS = 13
 
 
 def _load():
-    path = _build.LIB
+    # S2_LIBRARY=checked selects the bounds-checked build (debugging, tests)
+    path = _build.LIB_CHECKED if os.environ.get("S2_LIBRARY") == "checked" else _build.LIB
     if not os.path.exists(path):
-        raise ImportError("libs2.so not built (%s); run __graft_entry__.build()" % path)
+        raise ImportError("%s not built; run __graft_entry__.build()" % path)
     lib = C.CDLL(path)
     P = C.c_void_p
     dp = C.POINTER(C.c_double)
