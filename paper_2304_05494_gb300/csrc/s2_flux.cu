@@ -117,6 +117,17 @@ struct TileGrid {
   }
 };
 
+// Any of the per-point sensor tests (1.0 / 0.0) of the WENO stencil
+// a - WR + 1 .. a + WR of interface a + 1/2 (S points at position a),
+// ORed on the integer pipe.
+template <int WR, int SA, class R>
+__device__ __forceinline__ bool window_any(const R *S) {
+  decltype(order_bits(R(0))) any = 0;
+#pragma unroll
+  for (int m = 1 - WR; m <= WR; ++m) any |= order_bits(S[m * SA]);
+  return any != 0;
+}
+
 template <int DIR, class R, int TV>
 struct FluxLayout {
   static constexpr int L = TileR<DIR, TV, R>::L, W = TileR<DIR, TV, R>::W;
@@ -276,11 +287,13 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
             // the stored per-point tests theta > thr are 1.0 or 0.0: the
             // interface is flagged when any point of the stencil has it
             // (max theta over the stencil > thr), ORed on the integer pipe
-            decltype(order_bits(R(0))) any = 0;
-#pragma unroll
-            for (int m = -3; m <= 4; ++m)
-              if (m > -wr && m <= wr) any |= order_bits(Ss[(a + m + GH) * SA + cc * SCS]);
-            flag = any != 0;
+            const R *Sw = Ss + (a + GH) * SA + cc * SCS;
+            switch (wr) {
+              case 1: flag = window_any<1, SA>(Sw); break;
+              case 2: flag = window_any<2, SA>(Sw); break;
+              case 3: flag = window_any<3, SA>(Sw); break;
+              default: flag = window_any<4, SA>(Sw); break;
+            }
             if (flag && a >= 0) mycount++;
             int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
             slot = islot(d, DIR, s, i, j, k);
