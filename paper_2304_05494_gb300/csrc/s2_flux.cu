@@ -8,9 +8,13 @@
 // kernels of Table 2.  The paper's transposition kernel for x is not needed:
 // every direction stages its pencils through shared memory.
 //
-// k_flux<DIR>  one CTA per tile of L points along DIR times W pencils:
-//   1. stage the primitives of the tile plus GH ghost points each side
-//      (coalesced: the x-contiguous index runs fastest);
+// k_flux<DIR>  tiles of L points along DIR times W pencils (one tile per CTA
+// in double precision; a persistent grid walking the tiles in single
+// precision):
+//   1. the tile plus GH ghost points each side arrives by TMA, one box per
+//      staged field (rho, u, v, w, H, p, and the sensor test for WENO),
+//      completing on an mbarrier; single precision prefetches the next
+//      tiles into further buffers while computing this one;
 //   2. per position a the weighted pair mass fluxes of the pairs (a, a+l),
 //      l = 1..NP: m_l(a) = (a_l/4) (rho_a+rho_b)(un_a+un_b);
 //   3. the central flux difference D(a) = F_{a+1/2} - F_{a-1/2} of the

@@ -22,13 +22,14 @@ struct Scal {
   double dt_max_rate;     // last max spectral radius
   unsigned long long wcount;  // flagged interfaces of the last RHS evaluation
   unsigned int nlist[4];  // per-direction lengths of the flagged-interface lists
-  int status;             // 0 or the first error code met
+  int status;             // OR of the ERR_* bits met (0: none)
   int pad;
   long long nstep;        // completed RK3 steps (decides the dt recomputation on the device)
   double red[8];          // results of the last stats reduction
 };
 
-// Error bits written by kernels (mapped to S2_ENONFINITE on the host).
+// Error bits kernels OR into Scal::status (mapped on the host to
+// S2_ENONFINITE, S2_ETIMEOUT and S2_EBOUNDS).
 constexpr int ERR_NONFINITE = 1;
 constexpr int ERR_TIMEOUT = 2;  // a bounded wait on an asynchronous copy gave up
 constexpr int ERR_BOUNDS = 4;   // an index left its array (checked build)
