@@ -450,9 +450,19 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
 __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk1, int stage) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<float> V = view<float>(d);
+  // dt gamma_k, dt rho_{k+1} and the forcing in single precision, once per
+  // CTA: the per-point path then needs the double-precision unit only for
+  // the five additions to the state (float -> double on the integer pipe)
+  __shared__ float coef[3];
   const double dt = d.scal->dt;
+  if (threadIdx.x == 0) {
+    coef[0] = (float)(dt * gk);
+    coef[1] = (float)(dt * rk1);
+    coef[2] = d.force ? (float)d.scal->force : 0.0f;
+  }
+  __syncthreads();
   if (q < d.n) {
-    float f = d.force ? (float)d.scal->force : 0.0f;
+    const float a = coef[0], b = coef[1], f = coef[2];
     float fu = 0.0f;
     if (d.force) {
       int i, j, k;
@@ -460,7 +470,6 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
       const long long pu = pidx(d, i, j, k);
       if (S2_OK_IDX(d, pu, d.np)) fu = f * V.u[pu];
     }
-    const float a = (float)(dt * gk), b = (float)(dt * rk1);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       long long o = v * d.n + q;
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
       if (v == 1) R += f;
       if (v == 4) R += fu;
       float inc = stage > 0 ? fmaf(a, R, V.fln[o]) : a * R;
-      d.w[o] += (double)inc;
+      d.w[o] += f2d_int(inc);
       if (stage < 2) V.fln[o] = b * R;
     }
   }

@@ -253,6 +253,56 @@ def capacity(precision: str, sizes=SIZES, steps: int = 10) -> float:
     return sum(r.points for r in reqs) * steps / el
 
 
+def compare(count: int = 32, seed: int = 4321, steps=(100, 1000), sizes=SIZES, stream=None) -> dict:
+    """Batched serving against plain sequential FP64 solves of the same
+    requests on the same GPU: the requests (all admitted at once) are
+    served batched in mixed precision and batched in FP64, and solved one
+    after another in FP64, each alone; reported are the three throughputs
+    and the error of every mixed result against its sequential FP64 result
+    (max |a - b| / max |b| per conserved field; the batched FP64 results
+    equal the sequential ones exactly)."""
+    from . import s2
+    out = {"requests": count}
+    results = {}
+    for prec in ("mixed", "fp64"):
+        reqs = make_requests(count, seed=seed, sizes=sizes, steps=steps, precisions=(prec,))
+        r = Server(steps_per_tick=10, keep_results=True, stream=stream).run(reqs)
+        out["throughput_batched_" + prec] = r["throughput"]
+        results[prec] = [q.result for q in reqs]
+    reqs = make_requests(count, seed=seed, sizes=sizes, steps=steps, precisions=("fp64",))
+    t0 = time.perf_counter()
+    seq = []
+    for q in reqs:
+        c = initial_case(q)
+        with s2.Solver.from_case(c, precision="fp64") as sv:
+            sv.set_state(c.w0)
+            sv.step(q.steps)
+            seq.append(sv.get_state())
+    wall = time.perf_counter() - t0
+    out["throughput_sequential_fp64"] = sum(q.points * q.steps for q in reqs) / wall
+    out["speedup_batched_mixed_vs_sequential_fp64"] = out["throughput_batched_mixed"] / out["throughput_sequential_fp64"]
+    out["speedup_batched_fp64_vs_sequential_fp64"] = out["throughput_batched_fp64"] / out["throughput_sequential_fp64"]
+    # errors of the mixed results: pointwise per field (max |a-b| / max|b|),
+    # and of the volume-integrated kinetic energy, per case kind; decaying
+    # turbulence is chaotic, so over hundreds of steps its pointwise
+    # difference grows to O(1) while the integrals stay close
+    def ke(w):
+        return float(np.sum(0.5 * (w[1] ** 2 + w[2] ** 2 + w[3] ** 2) / w[0]))
+
+    for kind in ("tgv", "turb"):
+        idx = [i for i, q in enumerate(reqs) if q.kind == kind]
+        if not idx:
+            continue
+        fe = [float(np.max(np.max(np.abs(results["mixed"][i] - seq[i]), axis=(1, 2, 3)) /
+                           np.max(np.abs(seq[i]), axis=(1, 2, 3)))) for i in idx]
+        kd = [abs(ke(results["mixed"][i]) / ke(seq[i]) - 1.0) for i in idx]
+        out["mixed_vs_fp64_" + kind] = {"cases": len(idx), "field_err_median": float(np.median(fe)),
+                                        "field_err_max": float(np.max(fe)), "ke_rel_diff_max": float(np.max(kd)),
+                                        "steps_median": float(np.median([reqs[i].steps for i in idx]))}
+    out["batched_fp64_equals_sequential"] = all(np.array_equal(a, b) for a, b in zip(results["fp64"], seq))
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--requests", type=int, default=256)
@@ -262,7 +312,12 @@ def main(argv=None):
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--steps-per-tick", type=int, default=10)
+    ap.add_argument("--compare", type=int, default=0,
+                    help="instead: serve this many requests batched (mixed, FP64) and solve them sequentially in FP64")
     args = ap.parse_args(argv)
+    if args.compare:
+        print(json.dumps(compare(args.compare, steps=(args.min_steps, args.max_steps))))
+        return
     cap = capacity(args.precision)
     reqs = make_requests(args.requests, steps=(args.min_steps, args.max_steps), precisions=(args.precision,))
     mean_work = np.mean([r.points * r.steps for r in reqs])
