@@ -58,6 +58,11 @@ FP64_PEAK_GOPS = FP64_PEAK_GFLOPS / 2
 #   visc   u, v, w, T, div u, mu (24) + RHS read and write (40)
 #   update w read/write (80), RHS (20), RK register read and write on 2 of 3 stages (26.7), u (4)
 MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68, "visc": 64, "update": 130.7}
+# DRAM bytes per interior point of one launch of the mixed kernels (ncu,
+# same workload, captured with the current kernels; update at stage 0,
+# prims at a stage without the CFL partials): the traffic of the reported
+# kernel.
+MIXED_DRAM_BYTES = {"prims": 64.2, "visc": 66.0, "update": 110.5}
 
 
 def hbm_peak_gbs():
@@ -315,7 +320,8 @@ def our_arm(args):
         mixed = {"value": case.points * args.steps * world / (ms_m * 1e-3), "unit": UNIT,
                  "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state",
                  "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "traffic": None, "kernel": mname, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+                              "traffic": (MIXED_DRAM_BYTES[mname] * case.points if mname in MIXED_DRAM_BYTES
+                                          else None), "kernel": mname, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
                               "per_launch_ms": per_launch, "hbm_frac_per_kernel": kfrac,
                               "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_m.items() if v[1]}},
                  "err_vs_fp64_after_10_steps": err}
