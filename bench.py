@@ -169,7 +169,39 @@ def cpu_baseline(case, budget_s: float = 15.0):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": case.points * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d RK3 step(s) of the full %dx%dx%d channel after 1 untimed step (%.1f s)"
-                      % (steps, case.nx, case.ny, case.nz, el)}
+                      % (steps, case.nx, case.ny, case.nz, el),
+            "single_core": cpu_single_core()}
+
+
+SINGLE_CORE_CODE = """
+import json, os, sys, time
+sys.path.insert(0, %r)
+import bench
+from oracle import oracle as O
+case = bench.workload()
+sub = 16
+w = case.w0[:, :sub].copy()
+pr = O.Problem(case.nx, case.ny, sub, case.lx, case.ly, case.lz * sub / case.nz, y=case.y, mach=case.mach,
+               re=case.re, visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
+               force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+t0 = time.perf_counter()
+O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every)
+el = time.perf_counter() - t0
+print(json.dumps({"value": case.nx * case.ny * sub / el, "seconds": el}))
+"""
+
+
+def cpu_single_core():
+    """The oracle on one host core (a fresh process with OMP_NUM_THREADS=1):
+    one RK3 step of a 16-plane z-slab of the workload."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", SINGLE_CORE_CODE % ROOT], env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
+    v = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": v["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "1 RK3 step of a 16-plane z-slab of the channel (%.1f s)" % v["seconds"]}
 
 
 def reference_arm(args):
