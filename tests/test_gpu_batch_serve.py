@@ -53,11 +53,15 @@ def test_batch_members_match_solo_runs(s2):
         assert np.array_equal(g, solo(s2, c, 6, **kw))
 
 
-def test_tile_variants_give_identical_results(s2):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tile_variants_give_identical_results(s2, precision):
+    """Every flux tile shape (and, in single precision, its two-points-per-
+    thread layout) gives bit-identical results on a grid that is a multiple
+    of none of them."""
     c = W.channel(40, 36, 24, seed=2)
     out = []
     for tiles in ([0, 0, 0], [1, 1, 1], [1, 0, 1]):
-        with s2.Solver.from_case(c, cfl=0.8, threshold=0.05) as sv:
+        with s2.Solver.from_case(c, cfl=0.8, threshold=0.05, precision=precision) as sv:
             sv.set_tiles(tiles)
             sv.set_state(c.w0)
             sv.step(3)
