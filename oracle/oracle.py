@@ -49,6 +49,7 @@ class _Cfg(C.Structure):
         ("bc_y", C.c_int), ("t_wall", C.c_double),
         ("force", C.c_int), ("weno_order", C.c_int), ("threshold", C.c_double),
         ("central_order", C.c_int), ("visc_order", C.c_int),
+        ("cp_coef", C.POINTER(C.c_double)),
     ]
 
 
@@ -79,6 +80,14 @@ def lib():
         _lib.or_weno_parts.restype = C.c_int
         _lib.or_eigvec.argtypes = [C.c_double, C.c_int, dp, C.c_double, dp, dp]
         _lib.or_eigvec.restype = C.c_double
+        _lib.or_eigvec_tp.argtypes = [C.c_double, C.c_double, C.c_int, dp, C.c_double, dp, dp]
+        _lib.or_eigvec_tp.restype = C.c_double
+        _lib.or_thermo.argtypes = [C.POINTER(_Cfg), C.c_double, dp, dp, dp]
+        _lib.or_thermo.restype = C.c_int
+        _lib.or_temperature.argtypes = [C.POINTER(_Cfg), C.c_double, C.c_int, C.c_double]
+        _lib.or_temperature.restype = C.c_double
+        _lib.or_roe_state.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
+        _lib.or_roe_state.restype = C.c_int
         _lib.or_rk3_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
         _lib.or_rk3_scalar.restype = C.c_double
     return _lib
@@ -117,7 +126,10 @@ class Problem:
     threshold: float = 0.2
     central_order: int = 6               # 2, 4, 6, 8
     visc_order: int = 6                  # 2, 4, 6, 8
+    # thermally perfect gas: a_{-2..4} of c_p/R = sum_l a_l T^l; None = calorically perfect
+    cp_coef: Optional[np.ndarray] = None
     _y_buf: Optional[np.ndarray] = field(default=None, repr=False)
+    _cp_buf: Optional[np.ndarray] = field(default=None, repr=False)
 
     def cfg(self) -> _Cfg:
         if self.wall_y and self.ny < 4:
@@ -140,6 +152,12 @@ class Problem:
         c.threshold = self.threshold
         c.central_order = self.central_order
         c.visc_order = self.visc_order
+        if self.cp_coef is not None:
+            self._cp_buf = np.ascontiguousarray(self.cp_coef, dtype=np.float64)
+            assert self._cp_buf.shape == (7,)
+            c.cp_coef = _dp(self._cp_buf)
+        else:
+            c.cp_coef = None
         return c
 
     @property
@@ -246,6 +264,56 @@ def eigvec(gamma: float, direction: int, uvec, H: float):
     R = np.zeros(25)
     c = lib().or_eigvec(gamma, direction, _dp(u), H, _dp(L), _dp(R))
     return L.reshape(5, 5), R.reshape(5, 5), float(c)
+
+
+def eigvec_tp(chi: float, c: float, direction: int, uvec, H: float):
+    """Eigenvector matrices for a general equation of state (chi = (1/rho)
+    dp/de at constant rho, speed of sound c)."""
+    u = np.ascontiguousarray(uvec, dtype=np.float64)
+    L = np.zeros(25)
+    R = np.zeros(25)
+    lib().or_eigvec_tp(chi, c, direction, _dp(u), H, _dp(L), _dp(R))
+    return L.reshape(5, 5), R.reshape(5, 5)
+
+
+def thermo(p: Problem, T: float):
+    """(c_p, dc_p/dT, e) of the problem's gas at temperature T."""
+    cfg = p.cfg()
+    cp, dcp, e = C.c_double(), C.c_double(), C.c_double()
+    lib().or_thermo(C.byref(cfg), T, C.byref(cp), C.byref(dcp), C.byref(e))
+    return cp.value, dcp.value, e.value
+
+
+def temperature(p: Problem, target: float, enthalpy: bool = False, T0: float = 1.0) -> float:
+    """T with e(T) = target (or h(T) = target, Newton from T0)."""
+    cfg = p.cfg()
+    return float(lib().or_temperature(C.byref(cfg), target, 1 if enthalpy else 0, T0))
+
+
+def roe_state(p: Problem, a, b):
+    """Roe state (u, v, w, H, chi, c) of the WENO flux between the states a
+    and b, each (rho, u, v, w, T)."""
+    cfg = p.cfg()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(6)
+    lib().or_roe_state(C.byref(cfg), _dp(a), _dp(b), _dp(out))
+    return out
+
+
+def conserved(p: Problem, rho, u, v, w, T) -> np.ndarray:
+    """State (rho, rho u, rho v, rho w, rho E) of primitive fields, with the
+    problem's internal energy e(T) (element by element)."""
+    rho, u, v, w, T = [np.asarray(f, dtype=np.float64) for f in (rho, u, v, w, T)]
+    shape = np.broadcast(rho, u, v, w, T).shape
+    e = np.vectorize(lambda t: thermo(p, float(t))[2], otypes=[np.float64])(T)
+    out = np.empty((5,) + shape)
+    out[0] = rho
+    out[1] = rho * u
+    out[2] = rho * v
+    out[3] = rho * w
+    out[4] = rho * (e + 0.5 * (u * u + v * v + w * w))
+    return out
 
 
 def rk3_scalar(lam: float, y0: float, dt_: float, n: int) -> float:

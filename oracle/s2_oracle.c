@@ -6,8 +6,9 @@
  * library.
  *
  * What it computes (paper Sec. 2, "Numerical Methods"): the compressible
- * Navier-Stokes equations for a calorically perfect ideal gas on a Cartesian
- * grid (stretched in y), finite differences, with
+ * Navier-Stokes equations for an ideal gas, calorically perfect or
+ * thermally perfect (specific heats from a NASA polynomial in T), on a
+ * Cartesian grid (stretched in y), finite differences, with
  *   - a hybrid convective discretisation: the energy-preserving split
  *     ("skew-symmetric") form of the convective terms written as numerical
  *     fluxes (Pirozzoli, J. Comput. Phys. 2010), switched at interfaces
@@ -74,6 +75,7 @@ typedef struct {
   double threshold;     /* interface is WENO iff max sensor over its stencil > threshold */
   int central_order;    /* 2, 4, 6 or 8: split-form convective flux */
   int visc_order;       /* 2, 4, 6 or 8: viscous terms and the sensor's derivatives */
+  const double *cp_coef; /* NULL: calorically perfect; else a_{-2..4} of c_p/R = sum a_l T^l */
 } or_cfg;
 
 /* Which terms or_rhs evaluates. */
@@ -88,6 +90,8 @@ typedef struct {
   int nx, ny, nz, px, py, pz;
   size_t np, n;
   double R, cv, cp, dx, dz, eps_sensor;
+  int tp;                   /* thermally perfect gas: c_p/R = sum_{l=-2..4} a[l+2] T^l */
+  double a[7];
   int viscous;
   double *eta_y, *eta_yy; /* ny */
   double *rho, *u, *v, *w, *T, *p, *H, *cs, *sens, *div;
@@ -145,6 +149,19 @@ void or_metric(const or_cfg *c, double *eta_y, double *eta_yy) {
 /* ------------------------------------------------------------ workspace --- */
 static int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8; }
 
+/* Non-dimensional gas (reference density, velocity, temperature, length
+ * all 1): R = 1/(gamma M^2), so p = rho R T and, for a calorically perfect
+ * gas, c = sqrt(gamma R T). */
+static void gas_init(ws_t *s, const or_cfg *c) {
+  s->c = c;
+  s->R = 1.0 / (c->gamma * c->mach * c->mach);
+  s->cv = s->R / (c->gamma - 1.0);
+  s->cp = c->gamma * s->cv;
+  s->tp = c->cp_coef != NULL;
+  if (s->tp)
+    for (int l = 0; l < 7; ++l) s->a[l] = c->cp_coef[l];
+}
+
 static int ws_init(ws_t *s, const or_cfg *c) {
   memset(s, 0, sizeof(*s));
   s->c = c;
@@ -158,11 +175,7 @@ static int ws_init(ws_t *s, const or_cfg *c) {
   s->px = c->nx + 2 * GH; s->py = c->ny + 2 * GH; s->pz = c->nz + 2 * GH;
   s->np = (size_t)s->px * s->py * s->pz;
   s->n = (size_t)c->nx * c->ny * c->nz;
-  /* Non-dimensional gas (reference density, velocity, temperature, length
-   * all 1): R = 1/(gamma M^2), so p = rho R T and c = sqrt(gamma R T). */
-  s->R = 1.0 / (c->gamma * c->mach * c->mach);
-  s->cv = s->R / (c->gamma - 1.0);
-  s->cp = c->gamma * s->cv;
+  gas_init(s, c);
   s->dx = c->lx / c->nx;
   s->dz = c->lz / c->nz;
   s->eps_sensor = 1.0; /* (U0/L0)^2 in reference units */
@@ -185,10 +198,80 @@ static void ws_free(ws_t *s) {
   free(s->eta_y); free(s->eta_yy);
 }
 
+/* ------------------------------------------------------- thermodynamics ---
+ * Calorically perfect gas: c_p and c_v constant, e = c_v T.  Thermally
+ * perfect gas (paper Sec. 2: the temperature dependence of the specific
+ * heats through NASA polynomials, McBride et al. 2002): c_p/R is the
+ * polynomial sum_{l=-2..4} a_l T^l of the NASA Glenn 9-coefficient form, in
+ * reference units of T; c_v = c_p - R; the internal energy is the
+ * antiderivative of c_v with zero integration constant,
+ *   e/R = -a_{-2}/T + a_{-1} ln T + (a_0 - 1) T + a_1 T^2/2 + a_2 T^3/3
+ *         + a_3 T^4/4 + a_4 T^5/5,
+ * which is c_v T when only a_0 is non-zero; h = e + R T, and the speed of
+ * sound is c = sqrt(gamma(T) R T), gamma(T) = c_p/c_v. */
+static double cp_of(const ws_t *s, double T) {
+  if (!s->tp) return s->cp;
+  double r = 0.0;
+  for (int l = -2; l <= 4; ++l) r += s->a[l + 2] * pow(T, l);
+  return s->R * r;
+}
+
+/* d c_p / d T */
+static double dcp_of(const ws_t *s, double T) {
+  if (!s->tp) return 0.0;
+  double r = 0.0;
+  for (int l = -2; l <= 4; ++l)
+    if (l != 0) r += l * s->a[l + 2] * pow(T, l - 1);
+  return s->R * r;
+}
+
+static double e_of(const ws_t *s, double T) {
+  if (!s->tp) return s->cv * T;
+  double r = -T;
+  for (int l = -2; l <= 4; ++l) {
+    if (l == -1) r += s->a[1] * log(T);
+    else r += s->a[l + 2] * pow(T, l + 1) / (l + 1);
+  }
+  return s->R * r;
+}
+
+static double gamma_of(const ws_t *s, double T) {
+  if (!s->tp) return s->c->gamma;
+  double cp = cp_of(s, T);
+  return cp / (cp - s->R);
+}
+
+/* The temperature at which e(T) (enthalpy = 0) or h(T) = e(T) + R T
+ * (enthalpy = 1) equals target: Newton's method on that increasing
+ * function (its derivative c_v or c_p is positive) from T0, until a step
+ * changes T by at most 1e-13 relative; NaN if that does not happen within
+ * 100 steps. */
+static double temperature_of(const ws_t *s, double target, int enthalpy, double T0) {
+  if (!s->tp) return enthalpy ? target / s->cp : target / s->cv;
+  double T = T0 > 0.0 ? T0 : 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double f = e_of(s, T) + (enthalpy ? s->R * T : 0.0) - target;
+    double df = cp_of(s, T) - (enthalpy ? 0.0 : s->R);
+    double Tn = T - f / df;
+    if (!(Tn > 0.0)) Tn = 0.5 * T; /* stay in the domain T > 0 */
+    if (fabs(Tn - T) <= 1e-13 * Tn) return Tn;
+    T = Tn;
+  }
+  return NAN;
+}
+
+/* T from e, starting from the linearisation of e(T) about T = 1. */
+static double T_of_e(const ws_t *s, double e) {
+  if (!s->tp) return e / s->cv;
+  double T0 = 1.0 + (e - e_of(s, 1.0)) / (cp_of(s, 1.0) - s->R);
+  return temperature_of(s, e, 0, T0);
+}
+
 /* ------------------------------------------------------------ primitives ---
- * Primitive recovery: rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v,
- * p = rho R T; then the ghost faces; then H = c_p T + |u|^2/2 and
- * c = sqrt(gamma R T) on interior and ghost faces. */
+ * Primitive recovery: rho, u = (rho u)/rho, ..., T from e = E - |u|^2/2
+ * (e/c_v, or the inverse of e(T) for a thermally perfect gas), p = rho R T;
+ * then the ghost faces; then H = h(T) + |u|^2/2 and c = sqrt(gamma(T) R T)
+ * on interior and ghost faces. */
 static void fill_ghost_prims(ws_t *s) {
   const or_cfg *c = s->c;
   int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -248,7 +331,7 @@ static void prims(ws_t *s, const double *w) {
         double rho = w[q];
         double u = w[n + q] / rho, v = w[2 * n + q] / rho, ww = w[3 * n + q] / rho;
         double e = w[4 * n + q] / rho - 0.5 * (u * u + v * v + ww * ww);
-        double T = e / s->cv;
+        double T = T_of_e(s, e);
         s->rho[a] = rho; s->u[a] = u; s->v[a] = v; s->w[a] = ww;
         s->T[a] = T; s->p[a] = rho * s->R * T;
       }
@@ -261,8 +344,16 @@ static void prims(ws_t *s, const double *w) {
         size_t a = ((size_t)kk * s->py + jj) * s->px + ii;
         double T = s->T[a];
         double q2 = s->u[a] * s->u[a] + s->v[a] * s->v[a] + s->w[a] * s->w[a];
-        s->H[a] = s->cp * T + 0.5 * q2;
-        s->cs[a] = T > 0.0 ? sqrt(s->c->gamma * s->R * T) : 0.0;
+        if (!s->tp) {
+          s->H[a] = s->cp * T + 0.5 * q2;
+          s->cs[a] = T > 0.0 ? sqrt(s->c->gamma * s->R * T) : 0.0;
+        } else if (T > 0.0) {
+          s->H[a] = e_of(s, T) + s->R * T + 0.5 * q2;
+          s->cs[a] = sqrt(gamma_of(s, T) * s->R * T);
+        } else { /* edges and corners of the work arrays */
+          s->H[a] = 0.5 * q2;
+          s->cs[a] = 0.0;
+        }
       }
 }
 
@@ -496,6 +587,80 @@ double or_eigvec(double gamma, int dir, const double *uv, double H, double *Lm, 
   return c;
 }
 
+/* The same matrices for a general equation of state p(rho, e): chi =
+ * (1/rho) dp/de at constant rho (gamma - 1 for a calorically perfect gas,
+ * R/c_v(T) for a thermally perfect one) and the speed of sound c are given.
+ * The entropy-wave column carries H - c^2/chi in its energy entry (|u|^2/2
+ * when c^2 = (gamma-1)(H - |u|^2/2)), and the left rows follow from it with
+ * the term K = |u|^2 - (H - c^2/chi) in place of |u|^2/2. */
+double or_eigvec_tp(double chi, double c, int dir, const double *uv, double H, double *Lm, double *Rm) {
+  double b = chi, c2 = c * c;
+  double q2 = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+  double hs = H - c2 / chi, K = q2 - hs;
+  double n[3] = {0.0, 0.0, 0.0};
+  n[dir] = 1.0;
+  int t1 = (dir + 1) % 3, t2 = (dir + 2) % 3;
+  double un = uv[dir];
+  for (int q = 0; q < 25; ++q) { Lm[q] = 0.0; Rm[q] = 0.0; }
+  Rm[0 * 5 + 0] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 0] = uv[a] - c * n[a];
+  Rm[4 * 5 + 0] = H - un * c;
+  Rm[0 * 5 + 1] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 1] = uv[a];
+  Rm[4 * 5 + 1] = hs;
+  Rm[(1 + t1) * 5 + 2] = 1.0;
+  Rm[4 * 5 + 2] = uv[t1];
+  Rm[(1 + t2) * 5 + 3] = 1.0;
+  Rm[4 * 5 + 3] = uv[t2];
+  Rm[0 * 5 + 4] = 1.0;
+  for (int a = 0; a < 3; ++a) Rm[(1 + a) * 5 + 4] = uv[a] + c * n[a];
+  Rm[4 * 5 + 4] = H + un * c;
+  double h2 = 0.5 / c2;
+  Lm[0 * 5 + 0] = h2 * (b * K + un * c);
+  for (int a = 0; a < 3; ++a) Lm[0 * 5 + 1 + a] = h2 * (-b * uv[a] - c * n[a]);
+  Lm[0 * 5 + 4] = h2 * b;
+  Lm[1 * 5 + 0] = 1.0 - b * K / c2;
+  for (int a = 0; a < 3; ++a) Lm[1 * 5 + 1 + a] = b * uv[a] / c2;
+  Lm[1 * 5 + 4] = -b / c2;
+  Lm[2 * 5 + 0] = -uv[t1];
+  Lm[2 * 5 + 1 + t1] = 1.0;
+  Lm[3 * 5 + 0] = -uv[t2];
+  Lm[3 * 5 + 1 + t2] = 1.0;
+  Lm[4 * 5 + 0] = h2 * (b * K - un * c);
+  for (int a = 0; a < 3; ++a) Lm[4 * 5 + 1 + a] = h2 * (-b * uv[a] + c * n[a]);
+  Lm[4 * 5 + 4] = h2 * b;
+  return c;
+}
+
+/* Roe average of the states a and b (rho, u, v, w, T each): velocity and
+ * total enthalpy weighted by sqrt(rho); for a thermally perfect gas also the
+ * temperature T~ with h(T~) = H~ - |u~|^2/2 (Newton from the sqrt(rho)-
+ * weighted mean of T), chi = R/c_v(T~) and c~ = sqrt(gamma(T~) R T~).  A
+ * calorically perfect gas has chi = gamma - 1 and c~^2 = chi (H~ - |u~|^2/2).
+ * out: u, v, w, H, chi, c. */
+static void roe_state(const ws_t *s, const double *sa, const double *sb, double *out) {
+  double ra = sqrt(sa[0]), rb = sqrt(sb[0]);
+  double H[2];
+  const double *st[2] = {sa, sb};
+  for (int m = 0; m < 2; ++m) {
+    const double *z = st[m];
+    double q2 = z[1] * z[1] + z[2] * z[2] + z[3] * z[3];
+    H[m] = (s->tp ? e_of(s, z[4]) + s->R * z[4] : s->cp * z[4]) + 0.5 * q2;
+  }
+  for (int a = 0; a < 3; ++a) out[a] = (ra * sa[1 + a] + rb * sb[1 + a]) / (ra + rb);
+  out[3] = (ra * H[0] + rb * H[1]) / (ra + rb);
+  double q2 = out[0] * out[0] + out[1] * out[1] + out[2] * out[2];
+  if (!s->tp) {
+    out[4] = s->c->gamma - 1.0;
+    out[5] = sqrt(out[4] * (out[3] - 0.5 * q2));
+    return;
+  }
+  double T0 = (ra * sa[4] + rb * sb[4]) / (ra + rb);
+  double Tt = temperature_of(s, out[3] - 0.5 * q2, 1, T0);
+  out[4] = s->R / (cp_of(s, Tt) - s->R);
+  out[5] = sqrt(gamma_of(s, Tt) * s->R * Tt);
+}
+
 /* value of field f at position "pos" along direction dir of the pencil
  * through (i,j,k) */
 static inline size_t at(const ws_t *s, int dir, int pos, int i, int j, int k) {
@@ -521,7 +686,15 @@ static void weno_flux(const ws_t *s, int dir, int pos, int i, int j, int k, doub
   uv[2] = (ra * s->w[a] + rb * s->w[bq]) / (ra + rb);
   H = (ra * s->H[a] + rb * s->H[bq]) / (ra + rb);
   double Lm[25], Rm[25];
-  or_eigvec(gam, dir, uv, H, Lm, Rm);
+  if (!s->tp) {
+    or_eigvec(gam, dir, uv, H, Lm, Rm);
+  } else {
+    double sa[5] = {s->rho[a], s->u[a], s->v[a], s->w[a], s->T[a]};
+    double sb[5] = {s->rho[bq], s->u[bq], s->v[bq], s->w[bq], s->T[bq]};
+    double roe[6];
+    roe_state(s, sa, sb, roe);
+    or_eigvec_tp(roe[4], roe[5], dir, roe, roe[3], Lm, Rm);
+  }
   double V[8][5], G[8][5], lam[8][5];
   for (int m = 0; m < np; ++m) {
     size_t q = at(s, dir, pos - r + 1 + m, i, j, k);
@@ -639,7 +812,7 @@ static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags, int 
  *               - (2/3) theta d_i mu
  *   energy:     u_i * momentum_i + tau_ij d_j u_i + k lap T + grad k . grad T
  * with mu = (T/T_ref)^omega / Re, grad mu = (omega mu / T) grad T,
- * k = mu c_p / Pr, tau_ij = mu (d_j u_i + d_i u_j - (2/3) theta delta_ij),
+ * k = mu c_p(T) / Pr, tau_ij = mu (d_j u_i + d_i u_j - (2/3) theta delta_ij),
  * theta the stored divergence (its gradient by the same stencil). */
 static void viscous(ws_t *s, double *rhs) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -660,9 +833,18 @@ static void viscous(ws_t *s, double *rhs) {
         double T = s->T[pa];
         double mu = pow(T / c->t_ref, c->visc_exp) / c->re;
         double mut = c->visc_exp * mu / T;
-        double kc = mu * s->cp / c->prandtl;
-        double gmu[3], gk[3];
-        for (int b = 0; b < 3; ++b) { gmu[b] = mut * gT[b]; gk[b] = s->cp / c->prandtl * gmu[b]; }
+        double gmu[3], gk[3], kc;
+        if (!s->tp) {
+          kc = mu * s->cp / c->prandtl;
+          for (int b = 0; b < 3; ++b) { gmu[b] = mut * gT[b]; gk[b] = s->cp / c->prandtl * gmu[b]; }
+        } else { /* k = mu c_p(T) / Pr, grad k = (c_p grad mu + mu c_p'(T) grad T) / Pr */
+          double cpT = cp_of(s, T), dcpT = dcp_of(s, T);
+          kc = mu * cpT / c->prandtl;
+          for (int b = 0; b < 3; ++b) {
+            gmu[b] = mut * gT[b];
+            gk[b] = (cpT * gmu[b] + mu * dcpT * gT[b]) / c->prandtl;
+          }
+        }
         double th = s->div[pa];
         double uvec[3] = {s->u[pa], s->v[pa], s->w[pa]};
         double mom[3], en = 0.0;
@@ -774,7 +956,8 @@ int or_sensor(const or_cfg *c, const double *w, double *sens, double *div) {
 /* -------------------------------------------------------------------- dt ---
  * compute_dt of Table 2: dt = cfl / max over the interior of
  *   (|u|+c)/dx + (|v|+c) eta_y + (|w|+c)/dz
- *   + gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2)   (viscous runs). */
+ *   + gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2)   (viscous runs),
+ * gamma = gamma(T) and c = sqrt(gamma(T) R T) for a thermally perfect gas. */
 static double dt_ws(ws_t *s, const double *w, double cfl) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   const or_cfg *c = s->c;
@@ -788,7 +971,7 @@ static double dt_ws(ws_t *s, const double *w, double cfl) {
         double sr = (fabs(s->u[a]) + cs) / s->dx + (fabs(s->v[a]) + cs) * ey + (fabs(s->w[a]) + cs) / s->dz;
         if (s->viscous) {
           double mu = pow(s->T[a] / c->t_ref, c->visc_exp) / c->re;
-          sr += c->gamma * mu / (c->prandtl * s->rho[a]) *
+          sr += gamma_of(s, s->T[a]) * mu / (c->prandtl * s->rho[a]) *
                 (1.0 / (s->dx * s->dx) + ey * ey + 1.0 / (s->dz * s->dz));
         }
         mx = fmax(mx, sr);
@@ -836,6 +1019,37 @@ int or_step(const or_cfg *c, double *w, int nsteps, double cfl, double dt_fixed,
   if (dt_io) *dt_io = dt;
   free(R); free(Rp);
   ws_free(&s);
+  return 0;
+}
+
+/* Thermodynamic functions of the configuration's gas at T: c_p, dc_p/dT,
+ * e.  Returns -1 if the configuration is invalid. */
+int or_thermo(const or_cfg *c, double T, double *cp, double *dcp, double *e) {
+  ws_t s;
+  memset(&s, 0, sizeof(s));
+  gas_init(&s, c);
+  *cp = cp_of(&s, T);
+  *dcp = dcp_of(&s, T);
+  *e = e_of(&s, T);
+  return 0;
+}
+
+/* T from the internal energy e (enthalpy = 0, the primitive recovery's
+ * inversion) or from the enthalpy h (enthalpy = 1, from T0). */
+double or_temperature(const or_cfg *c, double target, int enthalpy, double T0) {
+  ws_t s;
+  memset(&s, 0, sizeof(s));
+  gas_init(&s, c);
+  return enthalpy ? temperature_of(&s, target, 1, T0) : T_of_e(&s, target);
+}
+
+/* Roe state of the WENO flux between the states a and b (rho, u, v, w, T):
+ * out = (u, v, w, H, chi, c). */
+int or_roe_state(const or_cfg *c, const double *a, const double *b, double *out) {
+  ws_t s;
+  memset(&s, 0, sizeof(s));
+  gas_init(&s, c);
+  roe_state(&s, a, b, out);
   return 0;
 }
 
