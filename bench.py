@@ -63,6 +63,11 @@ MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68
 # prims at a stage without the CFL partials): the traffic of the reported
 # kernel.
 MIXED_DRAM_BYTES = {"prims": 64.2, "visc": 66.0, "update": 110.5}
+# Thermally perfect gas of the side measurement: a synthetic polynomial of
+# the NASA 9-coefficient form, c_p/R = sum_{l=-2..4} a_l T^l (reference
+# units of T), whose gamma falls from 1.45 at T = 0.5 through 1.40 at T = 1
+# to 1.35 at T = 2, with the T^-2 and logarithmic T^-1 terms present.
+TP_GAS = [0.05, -0.2, 3.2, 0.5, -0.06, 0.004, 0.0]
 
 
 def hbm_peak_gbs():
@@ -84,6 +89,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-tp", action="store_true", help="skip the thermally perfect gas measurement")
     return ap.parse_args()
 
 
@@ -358,6 +364,38 @@ def our_arm(args):
                               "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_m.items() if v[1]}},
                  "err_vs_fp64_after_10_steps": err}
 
+    # thermally perfect gas (Sec. 2: c_p(T) from a NASA-form polynomial):
+    # the same workload and initial flow (its primitive fields, converted
+    # with this gas's e(T) on the device), FP64 and mixed precision
+    tp = None
+    if not args.no_tp:
+        tp = {"gas": "synthetic NASA 9-coefficient form c_p/R = sum a_l T^l, a_-2..a_4 = %s "
+                     "(gamma 1.45 / 1.40 / 1.35 at T = 0.5 / 1 / 2)" % TP_GAS}
+        for prec in ("fp64", "mixed"):
+            stp = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local, precision=prec,
+                                      cp_coeffs=TP_GAS)
+            stp.set_primitives(case.prim0)
+            stp.step(args.warmup)
+            stp.sync()
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            stp.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            ms_t = e0.elapsed_time(e1)
+            if world > 1:
+                t = torch.tensor([ms_t], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                ms_t = float(t.item())
+            prof_t = stp.profile(args.profile_steps)
+            ok = stp.stats()["status"] == 0
+            stp.close()
+            tp[prec] = {"value": case.points * args.steps * world / (ms_t * 1e-3), "unit": UNIT,
+                        "ms_per_step": ms_t / args.steps, "status_ok": ok,
+                        "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_t.items() if v[1]}}
+
     # end to end through the C ABI with host buffers: H2D of the step's
     # input state, one step, D2H of the result, every step
     pinned_in = torch.from_numpy(case.w0).pin_memory()
@@ -390,7 +428,7 @@ def our_arm(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
                "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "mixed": mixed,
-               "weno_frac": weno_frac, "state_finite": finite}
+               "thermally_perfect": tp, "weno_frac": weno_frac, "state_finite": finite}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(case)
         print(json.dumps(out))

@@ -1,8 +1,9 @@
 /*
  * s2.h -- C ABI of the GB300 STREAmS-2 solver (libs2.so).
  *
- * The library advances the 3-D compressible Navier-Stokes equations of a
- * calorically perfect ideal gas on a Cartesian grid, stretched in y, with
+ * The library advances the 3-D compressible Navier-Stokes equations of an
+ * ideal gas, calorically or thermally perfect, on a Cartesian grid,
+ * stretched in y, with
  * the method of the paper's Sec. 2 ("Numerical Methods"): hybrid
  * convective discretisation (energy-preserving split-form central flux of
  * 6th order; at interfaces flagged by a modified Ducros shock sensor, a
@@ -16,7 +17,9 @@
  *
  * Units: reference density, velocity, temperature and length are 1; the
  * gas constant is R = 1/(gamma mach_ref^2), p = rho R T,
- * E = c_v T + |u|^2/2, c_v = R/(gamma-1), mu = (T/t_ref)^visc_exp / re_ref.
+ * E = e(T) + |u|^2/2, mu = (T/t_ref)^visc_exp / re_ref; e(T) = c_v T with
+ * c_v = R/(gamma-1) for a calorically perfect gas (s2_gas below gives the
+ * thermally perfect e(T)).
  *
  * State layout across the ABI: w[v][k][j][i], v = 0..4 = (rho, rho u,
  * rho v, rho w, rho E), interior points only, i (x) fastest: 5*nx*ny*nz
@@ -76,9 +79,27 @@ typedef struct {
   const double *y;
 } s2_metrics;
 
-/* Gas (Sec. 2: ideal gas; calorically perfect).  re_ref <= 0 = inviscid. */
+/* Gas (Sec. 2: ideal gas, calorically or thermally perfect).  re_ref <= 0
+ * = inviscid.  gamma (with mach_ref) fixes the gas constant R.
+ *
+ * cp_coeffs: NULL for a calorically perfect gas (c_p = gamma R/(gamma-1)).
+ * Otherwise a thermally perfect gas whose specific heat follows the NASA
+ * Glenn 9-coefficient polynomial (Sec. 2: "NASA polynomials", McBride et
+ * al. 2002): host pointer to 7 doubles a_{-2}, a_{-1}, a_0, ..., a_4 with
+ * c_p(T)/R = sum_l a_l T^l, T in reference units (scale dimensional
+ * coefficients by T_ref^l).  Read during the call only.  The internal
+ * energy is the antiderivative of c_v = c_p - R with zero constant,
+ * e(T)/R = -a_{-2}/T + a_{-1} ln T + (a_0 - 1) T + a_1 T^2/2 + a_2 T^3/3
+ * + a_3 T^4/4 + a_4 T^5/5 (the calorically perfect e when only a_0 is
+ * set); states passed in and out use this e.  T follows from e by Newton's
+ * method, the sound speed is sqrt(gamma(T) R T) with gamma(T) = c_p/c_v,
+ * the conductivity mu c_p(T)/Pr.  The coefficients must be finite and
+ * give c_v > 0 at T = 1 and at t_ref (else S2_EINVAL); c_v must stay
+ * positive over the temperatures the flow visits (a Newton iteration that
+ * fails to converge is reported as S2_ENONFINITE). */
 typedef struct {
   double gamma, prandtl, mach_ref, re_ref, visc_exp, t_ref;
+  const double *cp_coeffs;
 } s2_gas;
 
 /* Boundaries: x and z must be S2_BC_PERIODIC; y periodic or isothermal
@@ -158,6 +179,21 @@ int s2_set_state(s2_solver *s, const double *w, int where);
 /* Copy the state out; synchronises the solver's stream first.  Returns
  * S2_ENONFINITE if the device recorded an invalid state. */
 int s2_get_state(s2_solver *s, double *w, int where);
+
+/* Set the state from primitive fields prim[v][k][j][i], v = 0..4 = (rho,
+ * u, v, w, T), interior points only (5*nx*ny*nz doubles), host or device
+ * memory per where.  The conversion runs on the device with the solver's
+ * gas: E = e(T) + |u|^2/2, the thermally perfect e(T) when s2_gas gives
+ * c_p coefficients.  Otherwise as s2_set_state (clock unchanged, RK
+ * register cleared).  Returns S2_ENONFINITE, with the state set as given,
+ * if some rho or T is not positive and finite. */
+int s2_set_primitives(s2_solver *s, const double *prim, int where);
+
+/* Primitive fields (rho, u, v, w, T) of the current state, same layout,
+ * into host or device memory per where; T from e by the solver's gas in
+ * double precision (Newton's method for a thermally perfect gas).
+ * Synchronises.  The state is unchanged. */
+int s2_get_primitives(s2_solver *s, double *prim, int where);
 
 /* Advance n full RK3 steps (3 stages each).  Asynchronous on the solver's
  * stream: the call enqueues the work (a captured CUDA graph per step) and

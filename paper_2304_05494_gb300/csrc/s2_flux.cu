@@ -452,6 +452,9 @@ __device__ __forceinline__ R weno_rec(const R *g, R eps) {
 //   l_0 W = A + B,  l_4 W = A - B,  l_1 W = rho - 2A,
 //   l_2 W = m_1 - u_1 rho,  l_3 W = m_2 - u_2 rho,
 //   A = h2 b (q~^2/2 rho - u_n m_n - u_1 m_1 - u_2 m_2 + E),
+// (a thermally perfect gas: b = chi = R/c_v(T~) at the Roe temperature,
+// q~^2/2 -> q~^2 - hs here and -> hs in the entropy wave's right
+// eigenvector, hs = H~ - c~^2/chi; c~^2 = gamma(T~) R T~),
 //   B = h2 c~ (u_n rho - m_n),
 // and, with the point's flux F = u_n W + p (0, 1, 0, 0, u_n),
 //   l_e F = u_n (l_e W) + p (l_e[1] + l_e[4] u_n),
@@ -538,10 +541,27 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     R ut2 = (ra * __ldg(vel[T2] + ia) + rb * __ldg(vel[T2] + ib)) * inv;
     R Ht = (ra * __ldg(V.H + ia) + rb * __ldg(V.H + ib)) * inv;
     R q2 = un * un + ut1 * ut1 + ut2 * ut2;
-    R c2 = bq * (Ht - R(0.5) * q2);
+    // chi = (1/rho) dp/de, c~^2, the entropy wave's energy entry hs and
+    // the term qa of the left rows (both |u~|^2/2 for a calorically
+    // perfect gas)
+    R chi = bq, c2, hs = R(0.5) * q2, qa = hs;
+    if (!K.tp) {
+      c2 = bq * (Ht - hs);
+    } else {
+      // Roe temperature: h(T~) = H~ - |u~|^2/2 by Newton's method from the
+      // sqrt(rho)-weighted temperature; chi = R/c_v(T~), c~^2 = (1+chi) R T~
+      bool ok = true;
+      const R T0 = (ra * __ldg(V.T + ia) + rb * __ldg(V.T + ib)) * inv;
+      const R Tt = tp_temperature(K, Ht - hs, T0, K.R_gas, ok);
+      if (!ok) atomicOr(&d.scal->status, ERR_NONFINITE);
+      chi = K.R_gas * recip_pos(tp_cp(K, Tt, recip_pos(Tt)) - K.R_gas);
+      c2 = (R(1) + chi) * K.R_gas * Tt;
+      hs = Ht - c2 * recip_pos(chi);
+      qa = q2 - hs;
+    }
     R cs = sqrt(c2);
     R h2 = R(0.5) * recip_pos(c2);
-    R hb = h2 * bq, hc = h2 * cs;
+    R hb = h2 * chi, hc = h2 * cs;
 
     // --- per stencil point: l_e W and l_e F for the five fields
     R Vv[5][NP], G[5][NP];
@@ -552,9 +572,10 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
       R r = __ldg(V.rho + q), unm = __ldg(vel[DIR] + q);
       R u1 = __ldg(vel[T1] + q), u2 = __ldg(vel[T2] + q);
       R pm = __ldg(V.p + q), hm = __ldg(V.H + q);
-      R cm = sqrt(K.gR * __ldg(V.T + q));
+      const R Tm = __ldg(V.T + q);
+      R cm = sqrt(K.tp ? tp_sound2(K, Tm) : K.gR * Tm);
       R mn = r * unm, m1 = r * u1, m2 = r * u2, E = r * hm - pm;
-      R A = hb * (R(0.5) * q2 * r - un * mn - ut1 * m1 - ut2 * m2 + E);
+      R A = hb * (qa * r - un * mn - ut1 * m1 - ut2 * m2 + E);
       R B = hc * (un * r - mn);
       R PA = pm * hb * (unm - un), PB = pm * hc;
       Vv[0][m] = A + B;
@@ -595,7 +616,7 @@ __global__ void __launch_bounds__(128) k_weno(Dev d) {
     Fr[1 + DIR] = un * s014 + cs * dn;
     Fr[1 + T1] = ut1 * s014 + gh[2];
     Fr[1 + T2] = ut2 * s014 + gh[3];
-    Fr[4] = Ht * (gh[0] + gh[4]) + un * cs * dn + R(0.5) * q2 * gh[1] + ut1 * gh[2] + ut2 * gh[3];
+    Fr[4] = Ht * (gh[0] + gh[4]) + un * cs * dn + hs * gh[1] + ut1 * gh[2] + ut2 * gh[3];
     const long long ns = d.nslot[DIR];
 #pragma unroll
     for (int f = 0; f < 5; ++f) V.dF[DIR][f * ns + slot] = Fr[f] - FC[f];

@@ -45,6 +45,13 @@ struct Consts {
   R R_gas, cp, gamma, gR, icv, visc_exp, inv_t_ref, t_wall, cp_over_pr, re, thr;
   R thr2;                  // thr^2 (sensor test without a root)
   R b0xz;                  // b_0/dx^2 + b_0/dz^2 (x and z centre weights of the Laplacian)
+  // thermally perfect gas (tp = 1): c_p(T) = sum_{l=-2..4} cpc[l+2] T^l;
+  // dcc = (-2 c_-2, -c_-1, c_1, 2 c_2, 3 c_3, 4 c_4) for dc_p/dT;
+  // ecf = (-c_-2, c_-1, c_0 - R, c_1/2, c_2/3, c_3/4, c_4/5) for e(T);
+  // e1 = e(1), icv1 = 1/c_v(1) (the first Newton guess); inv_pr = 1/Pr
+  int tp;
+  R cpc[7], dcc[6], ecf[7];
+  R e1, icv1, inv_pr;
 };
 
 // Division of 32-bit unsigned integers by a run-time constant d >= 1 as a
@@ -318,14 +325,87 @@ __device__ __forceinline__ double viscosity(const Dev &d, double T) {
   return y * d.inv_re;
 }
 
+// ---------------------------------------------- thermally perfect gas
+// Sec. 2: the specific heats may depend on T through NASA polynomials
+// (McBride et al. 2002, 9-coefficient form): c_p(T) = sum_{l=-2..4} c_l T^l
+// with c_l = R a_l, c_v = c_p - R, and the internal energy the c_v
+// antiderivative with zero constant,
+//   e(T) = -c_-2/T + c_-1 ln T + T (e_0 + T (e_1 + T (e_2 + T (e_3 + T e_4)))),
+// e_0 = c_0 - R, e_m = c_m/(m+1).  rT = 1/T is passed in.
+__device__ __forceinline__ double tp_log(double x) { return log(x); }
+__device__ __forceinline__ float tp_log(float x) { return logf(x); }
+
+template <class R>
+__device__ __forceinline__ R tp_cp(const Consts<R> &K, R T, R rT) {
+  const R pos = fma(T, fma(T, fma(T, fma(T, K.cpc[6], K.cpc[5]), K.cpc[4]), K.cpc[3]), K.cpc[2]);
+  return fma(rT, fma(rT, K.cpc[0], K.cpc[1]), pos);
+}
+
+template <class R>
+__device__ __forceinline__ R tp_dcp(const Consts<R> &K, R T, R rT) {
+  const R pos = fma(T, fma(T, fma(T, K.dcc[5], K.dcc[4]), K.dcc[3]), K.dcc[2]);
+  return fma(rT * rT, fma(rT, K.dcc[0], K.dcc[1]), pos);
+}
+
+template <class R>
+__device__ __forceinline__ R tp_e(const Consts<R> &K, R T, R rT) {
+  R e = fma(T, fma(T, fma(T, fma(T, fma(T, K.ecf[6], K.ecf[5]), K.ecf[4]), K.ecf[3]), K.ecf[2]), K.ecf[0] * rT);
+  if (K.ecf[1] != R(0)) e = fma(K.ecf[1], tp_log(T), e);
+  return e;
+}
+
+// c^2 = gamma(T) R T = c_p R T / (c_p - R)
+template <class R>
+__device__ __forceinline__ R tp_sound2(const Consts<R> &K, R T) {
+  const R cp = tp_cp(K, T, rcp_pos(T));
+  return cp * K.R_gas * T * rcp_pos(cp - K.R_gas);
+}
+
+// The temperature at which e(T) + sR T equals target (sR = 0: internal
+// energy, sR = R: enthalpy) by Newton's method from T (> 0), whose
+// derivative is c_p - R + sR.  It stops after a step below tol T: the
+// iteration converges quadratically, so the error is then of order tol^2
+// (1e-18 in double, 1e-7 in single precision).  ok is cleared if that
+// does not happen within 24 steps or T leaves T > 0.
+template <class R>
+__device__ __forceinline__ R tp_temperature(const Consts<R> &K, R target, R T, R sR, bool &ok) {
+  const R tol = sizeof(R) == 8 ? R(1e-9) : R(3e-4);
+  const R dR = sR - K.R_gas;
+  for (int it = 0; it < 24; ++it) {
+    const R rT = rcp_pos(T);
+    const R f = fma(sR, T, tp_e(K, T, rT)) - target;
+    const R dT = f * rcp_pos(tp_cp(K, T, rT) + dR);
+    T -= dT;
+    if (!(T > R(0))) break;
+    if (fabs(dT) <= tol * T) return T;
+  }
+  ok = false;
+  return T;
+}
+
+// First guess of T from e: the linearisation of e(T) about T = 1.
+template <class R>
+__device__ __forceinline__ R tp_guess(const Consts<R> &K, R e) {
+  const R T0 = fma(e - K.e1, K.icv1, R(1));
+  return T0 > R(0) ? T0 : R(1);
+}
+
 // CFL spectral radius of one point (compute_dt of Table 2):
 // (|u|+c)/dx + (|v|+c) eta_y + (|w|+c)/dz, plus for viscous runs
-// gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2), c = sqrt(gamma R T).
+// gamma mu / (Pr rho) (1/dx^2 + eta_y^2 + 1/dz^2), c = sqrt(gamma R T),
+// gamma = gamma(T) for a thermally perfect gas.
+// MAYBE_TP = false: the caller knows the gas is calorically perfect.
+template <bool MAYBE_TP = true>
 __device__ __forceinline__ double spectral_radius(const Dev &d, double rho, double u, double v, double ww, double T,
                                                   double mu, double ey) {
-  double cs = sqrt(d.gamma * d.R * T);
+  double gam = d.gamma;
+  if (MAYBE_TP && d.kd.tp) {
+    const double cp = tp_cp(d.kd, T, rcp_pos(T));
+    gam = cp / (cp - d.R);
+  }
+  double cs = sqrt(gam * d.R * T);
   double sr = (fabs(u) + cs) / d.dx + (fabs(v) + cs) * ey + (fabs(ww) + cs) / d.dz;
-  if (d.viscous) sr += d.gamma * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
+  if (d.viscous) sr += gam * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
   return sr;
 }
 
@@ -425,5 +505,6 @@ cudaError_t flux_set_attributes();
 
 // Gas constants (R, c_v, c_p, viscosity law) of a Dev from s2_gas.
 void set_gas(Dev &d, const s2_gas *gas);
+int check_gas(const s2_gas *gas, double t_extra);
 
 }  // namespace s2

@@ -65,7 +65,16 @@ __global__ void __launch_bounds__(NT) k_cfl_parts(Dev d, const double *__restric
     double ri = 1.0 / rho;
     double u = w[d.n + q] * ri, v = w[2 * d.n + q] * ri, ww = w[3 * d.n + q] * ri;
     double q2 = u * u + v * v + ww * ww;
-    double T = (w[4 * d.n + q] * ri - 0.5 * q2) * d.icv;
+    const double e = w[4 * d.n + q] * ri - 0.5 * q2;
+    double T = e * d.icv;
+    if (d.kd.tp) {
+      bool ok = true;
+      T = tp_temperature(d.kd, e, tp_guess(d.kd, e), 0.0, ok);
+      if (!ok) {  // no temperature for this energy: dt = 0 reports it
+        m = INFINITY;
+        continue;
+      }
+    }
     double mu = d.viscous ? viscosity(d, T) : 0.0;
     double ey = eta_y ? eta_y[j] : ey_uniform;
     m = fmax(m, spectral_radius(d, rho, u, v, ww, T, mu, ey));
@@ -106,7 +115,7 @@ extern "C" int s2_cfl_dt_noalloc(const s2_grid *grid, const s2_gas *gas, const d
   if (!grid || !gas || !w || !dt || !(cfl > 0)) return S2_EINVAL;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
     return S2_EINVAL;
-  if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
+  if (check_gas(gas, 0.0) != S2_OK) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   long long per_cta = (long long)NT * PTS_PER_THREAD;
   long long nparts = (n + per_cta - 1) / per_cta;

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
@@ -157,9 +159,13 @@ __device__ __forceinline__ int block_want_dt(const Dev &d, int stage0) {
 }
 
 // ------------------------------------------------------------- primitives
-// rho, u = (rho u)/rho, ..., T = (E - |u|^2/2)/c_v, p = rho R T,
-// H = c_p T + |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the
-// CFL spectral radius max into part[block] (c = sqrt(gamma R T)).
+// rho, u = (rho u)/rho, ..., T from e = E - |u|^2/2 (e/c_v, or the
+// inverse of e(T) of a thermally perfect gas), p = rho R T, H = e + R T +
+// |u|^2/2, mu = (T/T_ref)^omega/Re.  With want_dt, also the CFL spectral
+// radius max into part[block] (c = sqrt(gamma R T)).
+// TP: thermally perfect gas (a separate instantiation keeps the
+// calorically perfect kernel free of the Newton iteration's code).
+template <bool TP>
 __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
   long long q = (long long)blockIdx.x * NT + threadIdx.x;
   const View<double> V = view<double>(d);
@@ -174,9 +180,21 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
     double ri = rcp_pos(rho);
     double u = w[d.n + q] * ri, v = w[2 * d.n + q] * ri, ww = w[3 * d.n + q] * ri;
     double q2 = u * u + v * v + ww * ww;
-    double T = (w[4 * d.n + q] * ri - 0.5 * q2) * d.icv;
-    double pr = rho * d.R * T;
+    const double e = w[4 * d.n + q] * ri - 0.5 * q2;
+    double T = e * d.icv;
+    double h = d.cp * T;  // enthalpy
     const bool okp = S2_OK_IDX(d, p, d.np);
+    if (TP) {
+      // T from e by Newton's method, from the point's previous temperature
+      double T0 = 0.0;
+      S2_GUARD(okp) T0 = V.T[p];
+      if (!positive_finite(T0)) T0 = tp_guess(d.kd, e);
+      bool ok = true;
+      T = tp_temperature(d.kd, e, T0, 0.0, ok);
+      if (!ok) atomicOr(&d.scal->status, ERR_NONFINITE);
+      h = fma(d.R, T, e);
+    }
+    double pr = rho * d.R * T;
     S2_GUARD(okp) {
       V.rho[p] = rho;
       V.u[p] = u;
@@ -184,7 +202,7 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
       V.ww[p] = ww;
       V.T[p] = T;
       V.p[p] = pr;
-      V.H[p] = d.cp * T + 0.5 * q2;
+      V.H[p] = h + 0.5 * q2;
     }
     double mu = 0.0;
     if (d.viscous) {
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
     }
     if (!positive_finite(rho) || !positive_finite(T) || !finite_bits(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
-    if (want_dt) sr = spectral_radius(d, rho, u, v, ww, T, mu, d.eta_y[j]);
+    if (want_dt) sr = spectral_radius<TP>(d, rho, u, v, ww, T, mu, d.eta_y[j]);
   }
   dt_block_max(d, sr, want_dt);
 }
@@ -222,7 +240,18 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
     float q2 = u * u + v * v + ww * ww;
     const float rhoe = d2f_int(w[4 * d.n + q] - f2d_int(0.5f * rf * q2));
     float T = rhoe * rif * K.icv;
+    float h = K.cp * T;  // enthalpy
+    bool ok = true;
     const bool okp = S2_OK_IDX(d, p, d.np);
+    if (K.tp) {
+      // T from e by Newton's method, from the point's previous temperature
+      const float e = rhoe * rif;
+      float T0 = 0.0f;
+      S2_GUARD(okp) T0 = V.T[p];
+      if (!(T0 > 0.0f && T0 < 3.0e38f)) T0 = tp_guess(K, e);
+      T = tp_temperature(K, e, T0, 0.0f, ok);
+      h = fmaf(K.R_gas, T, e);
+    }
     S2_GUARD(okp) {
       V.rho[p] = rf;
       V.u[p] = u;
@@ -230,21 +259,27 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
       V.ww[p] = ww;
       V.T[p] = T;
       V.p[p] = rf * K.R_gas * T;
-      V.H[p] = K.cp * T + 0.5f * q2;
+      V.H[p] = h + 0.5f * q2;
     }
     float mu = 0.0f;
     if (d.viscous) {
       mu = viscosity(d, T);
       V.mu[q] = mu;
     }
-    if (!(rf > 0.0f) || !(T > 0.0f) || !isfinite(rf) || !isfinite(T) || !isfinite(q2))
+    if (!ok || !(rf > 0.0f) || !(T > 0.0f) || !isfinite(rf) || !isfinite(T) || !isfinite(q2))
       atomicOr(&d.scal->status, ERR_NONFINITE);
     if (want_dt) {
-      float cs = sqrtf(K.gR * T);
+      float gam = K.gamma, c2 = K.gR * T;
+      if (K.tp) {
+        const float cp = tp_cp(K, T, 1.0f / T);
+        gam = cp / (cp - K.R_gas);
+        c2 = gam * K.R_gas * T;
+      }
+      float cs = sqrtf(c2);
       float ey = d.eta_yf[j];
       float srf = (fabsf(u) + cs) * K.idx + (fabsf(v) + cs) * ey + (fabsf(ww) + cs) * K.idz;
       if (d.viscous)
-        srf += K.gamma * mu / ((float)d.prandtl * rf) * (K.idx * K.idx + ey * ey + K.idz * K.idz);
+        srf += gam * mu / ((float)d.prandtl * rf) * (K.idx * K.idx + ey * ey + K.idz * K.idz);
       sr = srf;
     }
   }
@@ -315,8 +350,8 @@ __device__ __forceinline__ bool ghost_map(const Dev &d, long long t, int &di, in
 
 // Face ghosts of the primitive fields.  x and z periodic; y periodic or
 // isothermal no-slip wall mirrored about the face between the outermost
-// node and its ghost: u -> -u, T -> 2 T_w - T, p -> p, rho = p/(R T), H from
-// T and |u|.
+// node and its ghost: u -> -u, T -> 2 T_w - T, p -> p, rho = p/(R T), H =
+// h(T) + |u|^2/2.
 template <class R>
 __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
   long long total = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
@@ -346,7 +381,8 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
     V.T[dp] = T;
     V.p[dp] = pr;
     V.rho[dp] = pr / (K.R_gas * T);
-    V.H[dp] = K.cp * T + R(0.5) * (u * u + v * v + ww * ww);
+    const R h = K.tp ? fma(K.R_gas, T, tp_e(K, T, rcp_pos(T))) : K.cp * T;
+    V.H[dp] = h + R(0.5) * (u * u + v * v + ww * ww);
     if (!(T > R(0))) atomicOr(&d.scal->status, ERR_NONFINITE);
   }
 }
@@ -485,6 +521,44 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
     d.scal->t += dt;
     d.scal->nstep += 1;
   }
+}
+
+// Primitive fields prim[v][k][j][i] = (rho, u, v, w, T) -> conserved
+// state w with the solver's gas, E = e(T) + |u|^2/2 (e = c_v T, or the
+// thermally perfect e(T)).  prim and w may be the same array: each thread
+// reads its point's five values before writing them.
+__global__ void __launch_bounds__(NT) k_from_prims(Dev d, const double *prim, double *w) {
+  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  if (q >= d.n) return;
+  const double rho = prim[q], u = prim[d.n + q], v = prim[2 * d.n + q], ww = prim[3 * d.n + q];
+  const double T = prim[4 * d.n + q];
+  if (!positive_finite(rho) || !positive_finite(T)) atomicOr(&d.scal->status, ERR_NONFINITE);
+  const double e = d.kd.tp ? tp_e(d.kd, T, rcp_pos(T)) : d.cv * T;
+  w[q] = rho;
+  w[d.n + q] = rho * u;
+  w[2 * d.n + q] = rho * v;
+  w[3 * d.n + q] = rho * ww;
+  w[4 * d.n + q] = rho * (e + 0.5 * (u * u + v * v + ww * ww));
+}
+
+// Conserved state -> primitive fields (rho, u, v, w, T), T in double
+// precision in both modes (the thermally perfect inversion from the
+// linearisation of e(T) about T = 1).
+__global__ void __launch_bounds__(NT) k_to_prims(Dev d, const double *w, double *prim) {
+  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+  if (q >= d.n) return;
+  const double rho = w[q], ri = 1.0 / rho;
+  const double u = w[d.n + q] * ri, v = w[2 * d.n + q] * ri, ww = w[3 * d.n + q] * ri;
+  const double e = w[4 * d.n + q] * ri - 0.5 * (u * u + v * v + ww * ww);
+  double T = e * d.icv;
+  bool ok = true;
+  if (d.kd.tp) T = tp_temperature(d.kd, e, tp_guess(d.kd, e), 0.0, ok);
+  if (!ok || !positive_finite(rho) || !positive_finite(T)) atomicOr(&d.scal->status, ERR_NONFINITE);
+  prim[q] = rho;
+  prim[d.n + q] = u;
+  prim[2 * d.n + q] = v;
+  prim[3 * d.n + q] = ww;
+  prim[4 * d.n + q] = T;
 }
 
 // R = fl + forcing into out (diagnostics, double).
@@ -647,7 +721,8 @@ cudaError_t enqueue_rhs(s2_solver *s, int stage0, Trace *tr) {
   unsigned ngb = (unsigned)((nghost + NT - 1) / NT);
   e = run(tr, st, S2_PROF_PRIMS, 1, [&] {
     if (d.mixed) k_prims_mixed<<<nb, NT, 0, st>>>(d, stage0);
-    else k_prims<<<nb, NT, 0, st>>>(d, stage0);
+    else if (d.kd.tp) k_prims<true><<<nb, NT, 0, st>>>(d, stage0);
+    else k_prims<false><<<nb, NT, 0, st>>>(d, stage0);
     return cudaGetLastError();
   });
   if (e != cudaSuccess) return e;
@@ -819,6 +894,56 @@ void s2::set_gas(Dev &d, const s2_gas *gas) {
   d.inv_t_ref = 1.0 / gas->t_ref;
   d.cp_over_pr = d.cp / gas->prandtl;
   d.viscous = gas->re_ref > 0.0;
+  // thermally perfect gas: coefficients of c_p, dc_p/dT and e(T) in both
+  // precisions (kernels of both paths read them from the constants)
+  d.kd.R_gas = d.R;
+  d.kf.R_gas = (float)d.R;
+  d.kd.inv_pr = 1.0 / gas->prandtl;
+  d.kf.inv_pr = (float)d.kd.inv_pr;
+  d.kd.tp = d.kf.tp = gas->cp_coeffs ? 1 : 0;
+  if (gas->cp_coeffs) {
+    double c[7];
+    for (int l = 0; l < 7; ++l) c[l] = d.R * gas->cp_coeffs[l];
+    const double dcc[6] = {-2.0 * c[0], -c[1], c[3], 2.0 * c[4], 3.0 * c[5], 4.0 * c[6]};
+    const double ecf[7] = {-c[0], c[1], c[2] - d.R, c[3] / 2.0, c[4] / 3.0, c[5] / 4.0, c[6] / 5.0};
+    for (int l = 0; l < 7; ++l) {
+      d.kd.cpc[l] = c[l];
+      d.kf.cpc[l] = (float)c[l];
+      d.kd.ecf[l] = ecf[l];
+      d.kf.ecf[l] = (float)ecf[l];
+    }
+    for (int l = 0; l < 6; ++l) {
+      d.kd.dcc[l] = dcc[l];
+      d.kf.dcc[l] = (float)dcc[l];
+    }
+    double e1 = 0.0, cv1 = -d.R;
+    for (int l = 0; l < 7; ++l) {
+      if (l != 1) e1 += ecf[l];
+      cv1 += c[l];
+    }
+    d.kd.e1 = e1;
+    d.kf.e1 = (float)e1;
+    d.kd.icv1 = 1.0 / cv1;
+    d.kf.icv1 = (float)d.kd.icv1;
+  }
+}
+
+// S2_OK if the gas is usable: gamma > 1, positive reference values and,
+// for a thermally perfect gas, finite coefficients with c_v > 0 at T = 1,
+// T = t_ref and T = t_extra (the wall temperature; ignored if <= 0).
+int s2::check_gas(const s2_gas *gas, double t_extra) {
+  if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
+  if (!gas->cp_coeffs) return S2_OK;
+  for (int l = 0; l < 7; ++l)
+    if (!std::isfinite(gas->cp_coeffs[l])) return S2_EINVAL;
+  const double Ts[3] = {1.0, gas->t_ref, t_extra};
+  for (double T : Ts) {
+    if (!(T > 0)) continue;
+    double cpr = 0.0;  // c_p / R
+    for (int l = -2; l <= 4; ++l) cpr += gas->cp_coeffs[l + 2] * std::pow(T, l);
+    if (!(cpr > 1.0)) return S2_EINVAL;
+  }
+  return S2_OK;
 }
 
 extern "C" {
@@ -854,7 +979,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     return S2_EINVAL;
   if (scheme->precision != S2_FP64 && scheme->precision != S2_MIXED) return S2_EINVAL;
   if (!(scheme->cfl > 0) && !(scheme->dt_fixed > 0)) return S2_EINVAL;
-  if (!(gas->gamma > 1.0) || !(gas->mach_ref > 0) || !(gas->prandtl > 0) || !(gas->t_ref > 0)) return S2_EINVAL;
+  if (check_gas(gas, bcs->y == S2_BC_ISOTHERMAL_WALL ? bcs->t_wall : 0.0) != S2_OK) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
   // point and interface-slot indices are split in 32-bit unsigned arithmetic
   if ((long long)(grid->nx + 1) * (grid->ny + 1) * (long long)(grid->nz + 1) > 0x7fffffffLL) return S2_EINVAL;
@@ -1154,6 +1279,43 @@ int s2_set_state(s2_solver *s, const double *w, int where) {
   if (e == cudaSuccess) e = cudaMemsetAsync(&s->d.scal->status, 0, sizeof(int), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_err(e);
+}
+
+int s2_set_primitives(s2_solver *s, const double *prim, int where) {
+  if (!s || !prim || (where != S2_HOST && where != S2_DEVICE)) return S2_EINVAL;
+  DeviceGuard guard(s->device);
+  size_t bytes = NV * (size_t)s->d.n * sizeof(double);
+  unsigned nb = (unsigned)((s->d.n + NT - 1) / NT);
+  cudaError_t e = cudaMemsetAsync(&s->d.scal->status, 0, sizeof(int), s->stream);
+  if (where == S2_HOST) {
+    // stage the primitives in the state array and convert in place
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d.w, prim, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) k_from_prims<<<nb, NT, 0, s->stream>>>(s->d, s->d.w, s->d.w);
+  } else if (e == cudaSuccess) {
+    k_from_prims<<<nb, NT, 0, s->stream>>>(s->d, prim, s->d.w);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.fln, 0, NV * (size_t)s->d.n * s->rsize, s->stream);
+  if (e != cudaSuccess) return S2_ECUDA;
+  return read_status(s);
+}
+
+int s2_get_primitives(s2_solver *s, double *prim, int where) {
+  if (!s || !prim || (where != S2_HOST && where != S2_DEVICE)) return S2_EINVAL;
+  DeviceGuard guard(s->device);
+  size_t bytes = NV * (size_t)s->d.n * sizeof(double);
+  unsigned nb = (unsigned)((s->d.n + NT - 1) / NT);
+  // FP64: fln is zero between steps; it stages the result and is cleared
+  // again afterwards (as in s2_rhs)
+  double *dst = where == S2_DEVICE ? prim : s->rhs_stage;
+  k_to_prims<<<nb, NT, 0, s->stream>>>(s->d, s->d.w, dst);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && where == S2_HOST) {
+    e = cudaMemcpyAsync(prim, s->rhs_stage, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess && !s->d.mixed) e = cudaMemsetAsync(s->d.fln, 0, bytes, s->stream);
+  }
+  if (e != cudaSuccess) return S2_ECUDA;
+  return read_status(s);
 }
 
 int s2_get_state(s2_solver *s, double *w, int where) {

@@ -140,7 +140,8 @@ __device__ __forceinline__ void visc_terms(const Consts<R> &K, const R (&g)[3][3
   }
   // energy: u . div tau + tau : grad u + div(k grad T), k = mu cp / Pr;
   // tau : grad u / mu = sum_a dg_a g_aa + S_01^2 + S_02^2 + S_12^2, and
-  // grad k . grad T = (cp/Pr) (d mu/dT) |grad T|^2
+  // grad k . grad T = (cp/Pr) (d mu/dT) |grad T|^2 (plus the c_p'(T) term
+  // of a thermally perfect gas)
   R e = uv[0] * mom[0];
   e = fma(uv[1], mom[1], e);
   e = fma(uv[2], mom[2], e);
@@ -154,7 +155,14 @@ __device__ __forceinline__ void visc_terms(const Consts<R> &K, const R (&g)[3][3
   R gT2 = gT[0] * gT[0];
   gT2 = fma(gT[1], gT[1], gT2);
   gT2 = fma(gT[2], gT[2], gT2);
-  en = fma(K.cp_over_pr, fma(mut, gT2, mu * lapT), e);
+  R cpr = K.cp_over_pr;
+  if (K.tp) {
+    // k = mu c_p(T)/Pr: grad k . grad T gains mu (c_p'(T)/Pr) |grad T|^2
+    const R rT = rcp_pos(T);
+    cpr = tp_cp(K, T, rT) * K.inv_pr;
+    e = fma(mu * tp_dcp(K, T, rT) * K.inv_pr, gT2, e);
+  }
+  en = fma(cpr, fma(mut, gT2, mu * lapT), e);
 }
 
 template <class R>

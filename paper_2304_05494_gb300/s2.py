@@ -42,7 +42,8 @@ class s2_metrics(C.Structure):
 
 class s2_gas(C.Structure):
     _fields_ = [("gamma", C.c_double), ("prandtl", C.c_double), ("mach_ref", C.c_double),
-                ("re_ref", C.c_double), ("visc_exp", C.c_double), ("t_ref", C.c_double)]
+                ("re_ref", C.c_double), ("visc_exp", C.c_double), ("t_ref", C.c_double),
+                ("cp_coeffs", C.POINTER(C.c_double))]
 
 
 class s2_bcs(C.Structure):
@@ -88,6 +89,8 @@ def _load():
     lib.s2_create.restype = C.c_int
     lib.s2_set_state.argtypes = [P, P, C.c_int]
     lib.s2_get_state.argtypes = [P, P, C.c_int]
+    lib.s2_set_primitives.argtypes = [P, P, C.c_int]
+    lib.s2_get_primitives.argtypes = [P, P, C.c_int]
     lib.s2_step.argtypes = [P, C.c_int]
     lib.s2_sync.argtypes = [P]
     lib.s2_set_clock.argtypes = [P, C.c_double, C.c_longlong, C.c_double]
@@ -168,6 +171,16 @@ def s2_set_state(h, w) -> None:
 def s2_get_state(h, out) -> None:
     p, where, _ = _ptr(out)
     _check(_lib.s2_get_state(h, p, where), "s2_get_state")
+
+
+def s2_set_primitives(h, prim) -> None:
+    p, where, _ = _ptr(prim)
+    _check(_lib.s2_set_primitives(h, p, where), "s2_set_primitives")
+
+
+def s2_get_primitives(h, out) -> None:
+    p, where, _ = _ptr(out)
+    _check(_lib.s2_get_primitives(h, p, where), "s2_get_primitives")
 
 
 def s2_step(h, n: int) -> None:
@@ -288,7 +301,7 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, *, y=None, gamma=1.4, prandtl=0.72, mach=0.1, re=1600.0,
                  visc_exp=0.76, t_ref=1.0, wall_y=False, t_wall=1.0, force=False, weno_order=0,
                  threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1, precision="fp64",
-                 central_order=6, visc_order=6):
+                 central_order=6, visc_order=6, cp_coeffs=None):
         self.shape = (5, nz, ny, nx)
         self.n = nx * ny * nz
         grid = s2_grid(nx, ny, nz, lx, ly, lz)
@@ -298,6 +311,12 @@ class Solver:
             self._y = np.ascontiguousarray(y, dtype=np.float64)
             met.y = self._y.ctypes.data_as(C.POINTER(C.c_double))
         gas = s2_gas(gamma, prandtl, mach, re, visc_exp, t_ref)
+        if cp_coeffs is not None:
+            # thermally perfect gas: a_{-2..4} of c_p/R = sum_l a_l T^l (read during s2_create)
+            cpc = np.ascontiguousarray(cp_coeffs, dtype=np.float64)
+            if cpc.shape != (7,):
+                raise ValueError("cp_coeffs needs the 7 coefficients a_-2 .. a_4")
+            gas.cp_coeffs = cpc.ctypes.data_as(C.POINTER(C.c_double))
         bcs = s2_bcs(S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL if wall_y else S2_BC_PERIODIC, S2_BC_PERIODIC,
                      t_wall, 1 if force else 0)
         prec = {"fp64": S2_FP64, "mixed": S2_MIXED}[precision]
@@ -324,6 +343,16 @@ class Solver:
         if out is None:
             out = np.empty(self.shape)
         s2_get_state(self.h, out)
+        return out
+
+    def set_primitives(self, prim):
+        """State from primitive fields (rho, u, v, w, T), shape (5, nz, ny, nx)."""
+        s2_set_primitives(self.h, prim)
+
+    def get_primitives(self, out=None):
+        if out is None:
+            out = np.empty(self.shape)
+        s2_get_primitives(self.h, out)
         return out
 
     def step(self, n: int = 1):

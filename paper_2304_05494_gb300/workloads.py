@@ -47,6 +47,9 @@ class Case:
     dt_every: int = 10
     steps: int = 10
     extra: dict = field(default_factory=dict)
+    # the primitive fields (rho, u, v, w, T) w0 was built from, where kept:
+    # the same initial flow for another gas model
+    prim0: Optional[np.ndarray] = None
 
     @property
     def points(self) -> int:
@@ -151,7 +154,8 @@ def channel(nx: int = 256, ny: int = 128, nz: int = 128, mach_b: float = 1.5, re
     return Case("channel_%dx%dx%d" % (nx, ny, nz), nx, ny, nz, lx, ly, lz, w0, y=yn, gamma=1.4,
                 mach=mach_b, re=re_b, visc_exp=0.76, prandtl=0.72, wall_y=True, t_wall=1.0,
                 force=True, weno_order=weno_order, threshold=0.2, cfl=0.8, steps=200,
-                extra={"beta": beta, "re_tau": re_tau})
+                extra={"beta": beta, "re_tau": re_tau},
+                prim0=np.ascontiguousarray(np.stack([rho, u, v, w, T]), dtype=np.float64))
 
 
 def smooth_periodic(nx: int, ny: int, nz: int, seed: int, mach: float = 0.5, amp_u: float = 0.5,

@@ -63,6 +63,11 @@ def test_strerror_and_invalid_arguments(lib):
     assert create(gas__gamma=1.0) == s2.S2_EINVAL
     # point and interface indices are split in 32-bit arithmetic
     assert create(g__nx=2000, g__ny=1100, g__nz=1000) == s2.S2_EINVAL
+    # thermally perfect gas: c_v = c_p - R must be positive (c_p/R = 0.9 at
+    # T = 1 is not), coefficients finite
+    for bad in ([0.0, 0.0, 0.9, 0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 3.5, float("nan"), 0.0, 0.0, 0.0]):
+        a = (C.c_double * 7)(*bad)
+        assert create(gas__cp_coeffs=C.cast(a, C.POINTER(C.c_double))) == s2.S2_EINVAL
     # null arguments
     h = C.c_void_p()
     assert s2._lib.s2_create(None, None, None, None, None, None, C.byref(h)) == s2.S2_EINVAL
