@@ -94,8 +94,9 @@ typedef struct {
  * set); states passed in and out use this e.  T follows from e by Newton's
  * method, the sound speed is sqrt(gamma(T) R T) with gamma(T) = c_p/c_v,
  * the conductivity mu c_p(T)/Pr.  The coefficients must be finite and
- * give c_v > 0 at T = 1 and at t_ref (else S2_EINVAL); c_v must stay
- * positive over the temperatures the flow visits (a Newton iteration that
+ * give c_v > 0 at T = 1, at t_ref and at the wall temperature (else
+ * S2_EINVAL); c_v must stay
+ * positive over the temperatures the flow visits (an inversion that
  * fails to converge is reported as S2_ENONFINITE). */
 typedef struct {
   double gamma, prandtl, mach_ref, re_ref, visc_exp, t_ref;

@@ -196,3 +196,33 @@ def test_primitive_fields_round_trip(s2, gas):
         assert np.all(field_err(w, ref) < 1e-15), field_err(w, ref)
     for back in (back_host, back_dev):
         assert np.all(field_err(back, prim) < 1e-14), field_err(back, prim)
+
+
+def test_batch_with_thermally_perfect_members_matches_solo_runs(s2):
+    """Thermally perfect members (FP64 and mixed) stepped in one batch with
+    a calorically perfect one give their solo results bit for bit."""
+    c, pr, w0 = hot_channel(24, 20, 12, seed=8)
+    _, prc, _ = hot_channel(24, 20, 12, seed=8, a=None)
+    specs = [(pr, dict(precision="fp64")), (pr, dict(precision="mixed")), (prc, dict(precision="mixed"))]
+    states = [w0, w0, c.w0]
+
+    def run(batch):
+        svs = []
+        for (p, kw), w in zip(specs, states):
+            sv = solver(s2, p, cfl=0.8, dt_every=2, **kw)
+            sv.set_state(w)
+            svs.append(sv)
+        if batch:
+            with s2.Batch(svs) as b:
+                b.step(5)
+                b.sync()
+        else:
+            for sv in svs:
+                sv.step(5)
+        out = [sv.get_state() for sv in svs]
+        for sv in svs:
+            sv.close()
+        return out
+
+    for a, b in zip(run(True), run(False)):
+        assert np.array_equal(a, b)
