@@ -364,13 +364,16 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
   if (!(S2_OK_IDX(d, dp, d.np) && S2_OK_IDX(d, sp, d.np))) return;
   if (!wall) {
-    V.rho[dp] = V.rho[sp];
-    V.u[dp] = V.u[sp];
-    V.v[dp] = V.v[sp];
-    V.ww[dp] = V.ww[sp];
-    V.T[dp] = V.T[sp];
-    V.p[dp] = V.p[sp];
-    V.H[dp] = V.H[sp];
+    // all loads first (the stores could alias them as far as the compiler
+    // knows; interleaving would serialise the round trips)
+    const R r = V.rho[sp], u = V.u[sp], v = V.v[sp], ww = V.ww[sp], T = V.T[sp], pr = V.p[sp], H = V.H[sp];
+    V.rho[dp] = r;
+    V.u[dp] = u;
+    V.v[dp] = v;
+    V.ww[dp] = ww;
+    V.T[dp] = T;
+    V.p[dp] = pr;
+    V.H[dp] = H;
   } else {
     R u = -V.u[sp], v = -V.v[sp], ww = -V.ww[sp];
     R T = R(2) * K.t_wall - V.T[sp];
@@ -400,10 +403,15 @@ __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
   bool wall = ghost_map(d, t, di, dj, dk, si, sj, sk);
   long long dp = pidx(d, di, dj, dk), sp = pidx(d, si, sj, sk);
   if (!(S2_OK_IDX(d, dp, d.np) && S2_OK_IDX(d, sp, d.np))) return;
-  V.sens[dp] = V.sens[sp];
+  const R sv = V.sens[sp];
   if (!wall) {
-    V.div[dp] = V.div[sp];
-  } else if (!d.mixed) {  // the mixed path's gradient pass writes these itself
+    const R dv = V.div[sp];
+    V.sens[dp] = sv;
+    V.div[dp] = dv;
+    return;
+  }
+  V.sens[dp] = sv;
+  if (!d.mixed) {  // the mixed path's gradient pass writes these itself
     long long q = ((long long)sk * d.ny + sj) * d.nx + si;
     if (!S2_OK_IDX(d, q, d.n)) return;
     R ux = V.g[0 * d.n + q], vy = V.g[4 * d.n + q], wz = V.g[8 * d.n + q];
@@ -462,16 +470,25 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
       if (S2_OK_IDX(d, pu, d.np)) fu = f * V.u[pu];
     }
     const double a = dt * gk, b = dt * rk1;
+    // every load before the first store: the arrays could alias as far as
+    // the compiler knows, so interleaving would serialise the round trips
+    double R[NV], wo[NV], ro[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      long long o = v * d.n + q;
-      double R = V.fl[o];
-      if (v == 1) R += f;
-      if (v == 4) R += fu;
-      double wn = fma(a, R, d.w[o]);
-      if (stage > 0) wn += V.fln[o];
+      const long long o = v * d.n + q;
+      R[v] = V.fl[o];
+      wo[v] = d.w[o];
+      ro[v] = stage > 0 ? V.fln[o] : 0.0;
+    }
+    R[1] += f;
+    R[4] += fu;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long o = v * d.n + q;
+      double wn = fma(a, R[v], wo[v]);
+      if (stage > 0) wn += ro[v];
       d.w[o] = wn;
-      if (stage < 2) V.fln[o] = b * R;
+      if (stage < 2) V.fln[o] = b * R[v];
     }
   }
   if (stage == 2 && q == 0) {
@@ -506,15 +523,24 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
       const long long pu = pidx(d, i, j, k);
       if (S2_OK_IDX(d, pu, d.np)) fu = f * V.u[pu];
     }
+    // every load before the first store (see k_update)
+    float R[NV], ro[NV];
+    double wo[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      long long o = v * d.n + q;
-      float R = V.fl[o];
-      if (v == 1) R += f;
-      if (v == 4) R += fu;
-      float inc = stage > 0 ? fmaf(a, R, V.fln[o]) : a * R;
-      d.w[o] += f2d_int(inc);
-      if (stage < 2) V.fln[o] = b * R;
+      const long long o = v * d.n + q;
+      R[v] = V.fl[o];
+      wo[v] = d.w[o];
+      ro[v] = stage > 0 ? V.fln[o] : 0.0f;
+    }
+    R[1] += f;
+    R[4] += fu;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const long long o = v * d.n + q;
+      const float inc = stage > 0 ? fmaf(a, R[v], ro[v]) : a * R[v];
+      d.w[o] = wo[v] + f2d_int(inc);
+      if (stage < 2) V.fln[o] = b * R[v];
     }
   }
   if (stage == 2 && q == 0) {
