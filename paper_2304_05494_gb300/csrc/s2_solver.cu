@@ -1131,6 +1131,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     k.t_wall = d.t_wall;
     k.cp_over_pr = d.cp_over_pr;
     k.re = d.re;
+    k.inv_re = d.inv_re;
     k.thr = d.thr;
     k.thr2 = d.thr * d.thr;
     k.b0xz = d.bx[0] + d.bz[0];
@@ -1154,6 +1155,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     f.t_wall = (float)k.t_wall;
     f.cp_over_pr = (float)k.cp_over_pr;
     f.re = (float)k.re;
+    f.inv_re = (float)k.inv_re;
     f.thr = (float)k.thr;
     f.thr2 = f.thr * f.thr;
     f.b0xz = (float)k.b0xz;
