@@ -205,12 +205,14 @@ int s2_step(s2_solver *s, int n);
 /* Wait for the solver's stream; returns the device status. */
 int s2_sync(s2_solver *s);
 
-/* Flux tile shape per direction: tiles[d] = 0 (default: 64x4 points for x,
- * 32x8 for y and z) or 1 (narrower along the direction: 32x8 for x, 16x16
- * for y and z, for small boxes).  Chosen per grid by the autotuner
- * (paper_2304_05494_gb300/autotune.py, the tile knobs of the paper's
- * launch-bounds study, Table 3).  Takes effect at the next s2_step; batches
- * created earlier keep the previous choice.  Results do not depend on it. */
+/* Flux tile shape per direction: tiles[d] = 0 (64x4 points for x, 32x8
+ * for y and z) or 1 (narrower along the direction: 32x8 for x, 16x16 for y
+ * and z, for small boxes); single precision doubles each tile along one
+ * axis.  Default: (0, 0, 0) for S2_FP64, (0, 1, 1) for S2_MIXED.  Chosen
+ * per grid by the autotuner (paper_2304_05494_gb300/autotune.py, the tile
+ * knobs of the paper's launch-bounds study, Table 3).  Takes effect at the
+ * next s2_step; batches created earlier keep the previous choice.  Results
+ * do not depend on it. */
 int s2_set_tiles(s2_solver *s, const int *tiles);
 
 /* Restore the clock (for a restart from a saved state). */

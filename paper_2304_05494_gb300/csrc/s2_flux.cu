@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       const int pi = DIR == 0 ? x0 + ta[pp] : x0 + tc;
       const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
       const int pk = DIR == 2 ? z0 + ta[pp] : z0;
-      q[pp] = ((long long)pk * d.ny + pj) * d.nx + pi;
+      // interior index in 32-bit arithmetic (n < 2^31; unused when not mine)
+      q[pp] = (long long)(((unsigned)pk * (unsigned)d.ny + (unsigned)pj) * (unsigned)d.nx + (unsigned)pi);
       if (mine[pp] && !S2_OK_IDX(d, q[pp], d.n)) mine[pp] = false;
 #pragma unroll
       for (int f = 0; f < 5; ++f) prev[pp][f] = (mine[pp] && accumulate) ? V.fl[f * d.n + q[pp]] : R(0);
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       for (int base = 0; base < NI; base += NTHREADS) {
         int idx = base + tid;
         bool flag = false;
-        long long slot = 0;
+        unsigned slot = 0;
         if (idx < NI) {
           int a, cc;
           if (DIR == 0) { a = idx % (L + 1) - 1; cc = idx / (L + 1); }
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
             }
             if (flag && a >= 0) mycount++;
             int i = DIR == 0 ? 0 : x0 + cc, j = DIR == 0 ? y0 + cc : (DIR == 1 ? 0 : y0), k = DIR == 2 ? 0 : z0;
-            slot = islot(d, DIR, s, i, j, k);
+            slot = islot32(d, DIR, s, i, j, k);
             if (!S2_OK_IDX(d, slot, d.nslot[DIR])) flag = false;
             else d.flag[DIR][slot] = flag;
           }

@@ -417,6 +417,15 @@ __host__ __device__ inline long long islot(const Dev &d, int dir, int s, int i, 
   return ((long long)(s + 1) * d.ny + j) * d.nx + i;
 }
 
+// The same in 32-bit unsigned arithmetic, exact for every slot of a grid
+// (s2_create keeps (nx+1)(ny+1)(nz+1) below 2^31).
+__device__ __forceinline__ unsigned islot32(const Dev &d, int dir, int s, int i, int j, int k) {
+  const unsigned nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+  if (dir == 0) return ((unsigned)k * ny + (unsigned)j) * (nx + 1u) + (unsigned)(s + 1);
+  if (dir == 1) return ((unsigned)k * (ny + 1u) + (unsigned)(s + 1)) * nx + (unsigned)i;
+  return ((unsigned)(s + 1) * ny + (unsigned)j) * nx + (unsigned)i;
+}
+
 // Single-precision power law mu = (T/T_ref)^omega / Re of the mixed path,
 // as 2^(omega log2 x) from the hardware base-2 logarithm and exponential:
 // for x = T/T_ref in the flow's range (0.1 .. 10) the logarithm's absolute

@@ -1109,6 +1109,11 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.weno = scheme->weno_order;
   d.force = bcs->force_mass_flow ? 1 : 0;
   d.mixed = scheme->precision == S2_MIXED ? 1 : 0;
+  // default flux tiles: the wide ones everywhere in double precision; in
+  // single precision the narrow y and z tiles (measured ~5 % faster on a
+  // 256 x 128 x 128 channel)
+  d.tile[0] = 0;
+  d.tile[1] = d.tile[2] = d.mixed;
   // scheme constants in both arithmetic types
   {
     Consts<double> &k = d.kd;

@@ -80,7 +80,7 @@ __device__ __forceinline__ void weno_correction(const Dev &d, const View<R> &V, 
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
     int pos = dir == 0 ? i : (dir == 1 ? j : k);
-    long long lo = islot(d, dir, pos - 1, i, j, k), hi = islot(d, dir, pos, i, j, k);
+    const long long lo = islot32(d, dir, pos - 1, i, j, k), hi = islot32(d, dir, pos, i, j, k);
     if (!(S2_OK_IDX(d, lo, d.nslot[dir]) && S2_OK_IDX(d, hi, d.nslot[dir]))) continue;
     bool fl = d.flag[dir][lo], fh = d.flag[dir][hi];
     if (fl || fh) {
