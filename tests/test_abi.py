@@ -23,7 +23,7 @@ def lib():
     return C.CDLL(build.LIB)
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_problem_statement_calls():
     names = header_functions()
     for f in ("s2_create", "s2_set_state", "s2_step", "s2_get_state", "s2_stats", "s2_destroy", "s2_strerror"):
         assert f in names
