@@ -17,6 +17,10 @@ L2 flush is needed between steps.
 N > 1 runs under torchrun as independent replicas (the solver does not
 shard across GPUs); value = all ranks' point-steps / the slowest rank's time.
 The reference arm times the plain CPU oracle on the host cores.
+
+Beside the FP64 line: the same workload in mixed precision (`mixed`), with
+a thermally perfect gas (`thermally_perfect`), and a short continuous-
+batching serving run for the p50/p99 batched step latency (`serving`).
 """
 from __future__ import annotations
 
@@ -59,10 +63,9 @@ FP64_PEAK_GOPS = FP64_PEAK_GFLOPS / 2
 #   update w read/write (80), RHS (20), RK register read and write on 2 of 3 stages (26.7), u (4)
 MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68, "visc": 64, "update": 130.7}
 # DRAM bytes per interior point of one launch of the mixed kernels (ncu,
-# same workload, captured with the current kernels; update at stage 0,
-# prims at a stage without the CFL partials): the traffic of the reported
-# kernel.
-MIXED_DRAM_BYTES = {"prims": 64.2, "visc": 66.0, "update": 110.3}
+# same workload, captured with the current kernels; stage 0 of a step that
+# recomputes dt): the traffic of the reported kernel.
+MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.3, "update": 110.6}
 # Thermally perfect gas of the side measurement: a synthetic polynomial of
 # the NASA 9-coefficient form, c_p/R = sum_{l=-2..4} a_l T^l (reference
 # units of T), whose gamma falls from 1.45 at T = 0.5 through 1.40 at T = 1
@@ -90,6 +93,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-tp", action="store_true", help="skip the thermally perfect gas measurement")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the short serving run (p50/p99 batched step latency); 0 skips it")
     return ap.parse_args()
 
 
@@ -396,6 +401,25 @@ def our_arm(args):
                         "ms_per_step": ms_t / args.steps, "status_ok": ok,
                         "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_t.items() if v[1]}}
 
+    # batched step latency: a short continuous-batching serving run (mixed
+    # precision, Poisson arrivals at 80 % of the measured capacity of a full
+    # batch, boxes of 32^3 .. 128^3, 50 .. 200 steps each)
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        from paper_2304_05494_gb300 import serve
+        cap = serve.capacity("mixed")
+        reqs = serve.make_requests(args.serve_requests, steps=(50, 200), precisions=("mixed",))
+        rate = 0.8 * cap / float(np.mean([r.points * r.steps for r in reqs]))
+        serve.poisson_arrivals(reqs, rate)
+        so = serve.Server(max_slots=64, steps_per_tick=10).run(reqs)
+        serving = {"requests": so["requests"], "done": so["done"], "precision": "mixed", "load": 0.8,
+                   "capacity": cap, "throughput": so["throughput"], "unit": UNIT,
+                   "p50_step_latency_ms": so["p50_step_latency_ms"],
+                   "p99_step_latency_ms": so["p99_step_latency_ms"],
+                   "p50_queue_s": so["p50_queue_s"], "p99_queue_s": so["p99_queue_s"],
+                   "workload": "Taylor-Green or seeded decaying turbulence boxes {32,48,64,96,128}^3, "
+                               "M in [0.1, 0.8], Re in [400, 3200], 50-200 RK3 steps"}
+
     # end to end through the C ABI with host buffers: H2D of the step's
     # input state, one step, D2H of the result, every step
     pinned_in = torch.from_numpy(case.w0).pin_memory()
@@ -428,7 +452,7 @@ def our_arm(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
                "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "mixed": mixed,
-               "thermally_perfect": tp, "weno_frac": weno_frac, "state_finite": finite}
+               "thermally_perfect": tp, "serving": serving, "weno_frac": weno_frac, "state_finite": finite}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(case)
         print(json.dumps(out))
