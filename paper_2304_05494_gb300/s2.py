@@ -336,23 +336,30 @@ class Solver:
         args.update(kw)
         return cls(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, **args)
 
+    def _fits(self, a):
+        """The library reads or writes 5 nx ny nz doubles: refuse other sizes."""
+        shape = tuple(a.shape)
+        if shape != self.shape and shape != (5 * self.n,):
+            raise ValueError("state buffer of shape %s, need %s" % (shape, self.shape))
+        return a
+
     def set_state(self, w):
-        s2_set_state(self.h, w)
+        s2_set_state(self.h, self._fits(w))
 
     def get_state(self, out=None):
         if out is None:
             out = np.empty(self.shape)
-        s2_get_state(self.h, out)
+        s2_get_state(self.h, self._fits(out))
         return out
 
     def set_primitives(self, prim):
         """State from primitive fields (rho, u, v, w, T), shape (5, nz, ny, nx)."""
-        s2_set_primitives(self.h, prim)
+        s2_set_primitives(self.h, self._fits(prim))
 
     def get_primitives(self, out=None):
         if out is None:
             out = np.empty(self.shape)
-        s2_get_primitives(self.h, out)
+        s2_get_primitives(self.h, self._fits(out))
         return out
 
     def step(self, n: int = 1):
@@ -373,7 +380,7 @@ class Solver:
     def rhs(self, out=None):
         if out is None:
             out = np.empty(self.shape)
-        s2_rhs(self.h, out)
+        s2_rhs(self.h, self._fits(out))
         return out
 
     def flags(self):
