@@ -678,6 +678,11 @@ struct s2_solver {
   size_t rsize;         // bytes of the arithmetic type (8 FP64, 4 mixed)
   double *rhs_stage;    // staging of s2_rhs output
   FluxMaps fmaps[3][2];  // tensor maps of the staged fields, per direction and tile variant
+  // second stream for the WENO corrections of a direction, which run while
+  // the flux kernels of the next directions do (fork after each flux
+  // kernel, join before the viscous pass)
+  cudaStream_t side;
+  cudaEvent_t ev_flux[3], ev_join;
 };
 
 namespace {
@@ -699,6 +704,10 @@ void *dalloc(s2_solver *s, size_t bytes) {
 
 void release(s2_solver *s) {
   if (s->graph_ready) cudaGraphExecDestroy(s->graph);
+  for (int a = 0; a < 3; ++a)
+    if (s->ev_flux[a]) cudaEventDestroy(s->ev_flux[a]);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->side) cudaStreamDestroy(s->side);
   for (void *p : s->blocks) {
     if (s->dev.free) s->dev.free(p, s->dev.ctx);
     else cudaFree(p);
@@ -781,11 +790,29 @@ cudaError_t enqueue_rhs(s2_solver *s, int stage0, Trace *tr) {
         cudaSuccess)
       return e;
   }
+  // Outside the per-kernel profile, each direction's WENO corrections run
+  // on the side stream as soon as its flux kernel has listed the flagged
+  // interfaces, beside the flux kernels of the next directions (they share
+  // no output: dF of the direction against the RHS and the other lists).
+  // Double precision only: there both are bound by the double-precision
+  // unit and the WENO kernels fill its idle slots (1 % per step); the
+  // single-precision flux kernels occupy every SM with a persistent grid
+  // and measured slower with the extra branch.
+  const bool overlap = d.weno && !d.mixed && !(tr && tr->timed);
   for (int dir = 0; dir < 3; ++dir) {
     e = run(tr, st, S2_PROF_FLUX_X + dir, 1, [&] { return launch_flux(d, s->fmaps[dir], dir, dir > 0, st); });
     if (e != cudaSuccess) return e;
+    if (overlap) {
+      if ((e = cudaEventRecord(s->ev_flux[dir], st)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s->side, s->ev_flux[dir], 0)) != cudaSuccess) return e;
+      if ((e = launch_weno(d, dir, s->side)) != cudaSuccess) return e;
+      if (tr) tr->count[S2_PROF_WENO] += 1;
+    }
   }
-  if (d.weno) {
+  if (overlap) {
+    if ((e = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, s->ev_join, 0)) != cudaSuccess) return e;
+  } else if (d.weno) {
     e = run(tr, st, S2_PROF_WENO, 3, [&] {
       cudaError_t r = cudaSuccess;
       for (int dir = 0; dir < 3 && r == cudaSuccess; ++dir) r = launch_weno(d, dir, st);
@@ -1050,6 +1077,17 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
       return S2_ECUDA;
     }
     s->own_stream = true;
+  }
+  {
+    bool ok = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) == cudaSuccess;
+    for (int a = 0; a < 3 && ok; ++a) ok = cudaEventCreateWithFlags(&s->ev_flux[a], cudaEventDisableTiming) == cudaSuccess;
+    if (ok) ok = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      release(s);
+      delete s;
+      return S2_ECUDA;
+    }
   }
   if (flux_set_attributes() != cudaSuccess) {
     cudaGetLastError();
