@@ -109,6 +109,38 @@ __device__ __forceinline__ R sensor_test(const Consts<R> &K, const R (&g)[3][3],
   return on ? R(1) : R(0);
 }
 
+// Double precision: the margin m = theta^2 - thr^2 (theta^2 + |omega|^2 + 1)
+// is first formed in single precision from the gradients converted on the
+// integer pipe.  With u = 2^-24 and A_k = |a_k| + |b_k| for the two
+// gradients of omega_k, its rounding error is below ~12.1 u (theta^2 +
+// thr^2 (theta^2 + sum A_k^2 + 1)) (conversion, differences, squares,
+// sums, products); when |m| exceeds 2^-19 = 32 u times that scale the sign
+// of m is the exact one, and so the double-precision test's (which is
+// exact outside ~1e-15 of the scale).  Otherwise -- within ~1e-6 of the
+// threshold, or for values outside the single-precision range (the margin
+// is then not finite) -- the double-precision test decides.  The
+// decisions are identical; the double-precision unit skips ~12
+// operations per point.
+template <>
+__device__ __forceinline__ double sensor_test<double>(const Consts<double> &K, const double (&g)[3][3], double th) {
+  if (K.thr < 0.0) return 1.0;
+  const float a1 = d2f_int(g[2][1]), b1 = d2f_int(g[1][2]);
+  const float a2 = d2f_int(g[0][2]), b2 = d2f_int(g[2][0]);
+  const float a3 = d2f_int(g[1][0]), b3 = d2f_int(g[0][1]);
+  const float thf = d2f_int(th), t2 = d2f_int(K.thr2);
+  const float o1 = a1 - b1, o2 = a2 - b2, o3 = a3 - b3;
+  const float om2 = o1 * o1 + o2 * o2 + o3 * o3;
+  const float th2 = thf * thf;
+  const float m = th2 - t2 * (th2 + om2 + 1.0f);
+  const float s1 = fabsf(a1) + fabsf(b1), s2 = fabsf(a2) + fabsf(b2), s3 = fabsf(a3) + fabsf(b3);
+  const float scale = th2 + t2 * (th2 + (s1 * s1 + s2 * s2 + s3 * s3) + 1.0f);
+  if (fabsf(m) > 0x1p-19f * scale) return (thf < 0.0f && m > 0.0f) ? 1.0 : 0.0;
+  const double od1 = g[2][1] - g[1][2], od2 = g[0][2] - g[2][0], od3 = g[1][0] - g[0][1];
+  const double dom2 = od1 * od1 + od2 * od2 + od3 * od3;
+  const double dth2 = th * th;
+  return (th < 0.0 && dth2 > K.thr2 * (dth2 + dom2 + 1.0)) ? 1.0 : 0.0;
+}
+
 // Viscous momentum and energy terms of one point from its derivatives:
 // velocity gradient g[a][b] = d u_a / d x_b, Laplacians lap[a] and lapT,
 // grad T, grad theta; T, mu, theta and u at the point.
