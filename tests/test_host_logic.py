@@ -1,5 +1,6 @@
 """Host-side logic that needs no GPU: serving workload generation, arrival
-process, autotuner choice and cache."""
+process, autotuner choice and cache, and the error bound behind the
+single-precision pre-test of the double-precision sensor decision."""
 import numpy as np
 
 from paper_2304_05494_gb300 import autotune, serve
@@ -89,3 +90,58 @@ int main() {
     assert r.returncode == 0, r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0 and out.stdout.startswith("ok"), out.stdout + out.stderr
+
+
+def _sensor_pretest(g, th, thr2):
+    """Single-precision pre-test of the double-precision sensor decision,
+    step by step as the gradient kernel forms it (float32 arithmetic,
+    round to nearest, no fused operations): returns (decided, on)."""
+    f = np.float32
+    a1, b1 = f(g[2][1]), f(g[1][2])
+    a2, b2 = f(g[0][2]), f(g[2][0])
+    a3, b3 = f(g[1][0]), f(g[0][1])
+    thf, t2 = f(th), f(thr2)
+    o1, o2, o3 = a1 - b1, a2 - b2, a3 - b3
+    om2 = o1 * o1 + o2 * o2 + o3 * o3
+    th2 = thf * thf
+    m = th2 - t2 * (th2 + om2 + f(1))
+    s1, s2, s3 = abs(a1) + abs(b1), abs(a2) + abs(b2), abs(a3) + abs(b3)
+    scale = th2 + t2 * (th2 + (s1 * s1 + s2 * s2 + s3 * s3) + f(1))
+    if abs(m) > f(2.0 ** -19) * scale:
+        return True, bool(thf < 0 and m > 0)
+    return False, None
+
+
+def test_sensor_single_precision_pretest_matches_exact_decision():
+    """Wherever the single-precision pre-test of the sensor decides, its
+    decision is the exact one (margin th^2 - thr^2 (th^2 + |omega|^2 + 1)
+    in rational arithmetic), on random gradients of many magnitudes, with
+    strong cancellation in the vorticity, and on states placed within
+    1e-3 .. 1e-9 of the threshold; close states fall back to double."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(7)
+    decided = fallback = 0
+    for it in range(6000):
+        thr = [0.05, 0.2, 0.5, 0.0][it % 4]
+        scale = 10.0 ** rng.uniform(-4, 4)
+        g = rng.normal(size=(3, 3)) * scale
+        if it % 3 == 1:  # cancellation: o_k small against its two gradients
+            for a, b in ((2, 1), (0, 2), (1, 0)):
+                g[b][a] = g[a][b] * (1 + rng.normal() * 1e-6)
+        om2 = (g[2][1] - g[1][2]) ** 2 + (g[0][2] - g[2][0]) ** 2 + (g[1][0] - g[0][1]) ** 2
+        if it % 2 == 0 and thr > 0:  # theta near the threshold
+            th = -np.sqrt(thr * thr * (om2 + 1.0) / (1.0 - thr * thr)) * (1 + rng.choice([-1, 1]) * 10.0 ** rng.uniform(-9, -3))
+        else:
+            th = rng.normal() * scale
+        thr2 = thr * thr
+        o = [Fr(g[2][1]) - Fr(g[1][2]), Fr(g[0][2]) - Fr(g[2][0]), Fr(g[1][0]) - Fr(g[0][1])]
+        T = Fr(th)
+        exact_m = T * T - Fr(thr2) * (T * T + sum(x * x for x in o) + 1)
+        exact_on = th < 0 and exact_m > 0
+        ok, on = _sensor_pretest(g, th, thr2)
+        if ok:
+            decided += 1
+            assert on == exact_on, (g, th, thr)
+        else:
+            fallback += 1
+    assert decided > 4000 and fallback > 0
