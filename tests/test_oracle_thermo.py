@@ -265,3 +265,39 @@ def test_thermally_perfect_design_order_manufactured(stretched):
         errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
     rates = np.log2(errs[0] / errs[1])
     assert np.all(rates > 5.4), rates
+
+
+def test_thermally_perfect_design_order_with_walls():
+    """Isothermal no-slip walls with the thermally perfect gas: fields whose
+    mirror continuation is analytic (velocity and T - T_w odd about each
+    wall, pressure even) converge at 6th order, wall rows included -- this
+    pins the wall ghosts' rho = p/(R T) and H = h(T) + |u|^2/2 with h(T)
+    from the polynomial."""
+    x, y, z = sp.symbols("x y z")
+    mach, tw = 0.8, 1.0
+    R = 1 / (GAMMA * sp.nsimplify(mach) ** 2)
+    cy, sy = sp.cos(sp.pi * y / 2), sp.sin(sp.pi * y)
+    u = (sp.Rational(3, 2) + sp.sin(x + z) / 5) * cy
+    v = sp.Rational(3, 10) * sy * sp.cos(x)
+    w = sp.Rational(2, 5) * cy * sp.sin(z)
+    T = tw + sp.Rational(3, 10) * cy * (1 + sp.cos(x) / 10)
+    p = R * (1 + sp.cos(sp.pi * y) * sp.cos(z) / 10)
+    rho = p / (R * T)
+    f, fe, rhs = _tp_rhs_exact((rho, u, v, w, T), mach, 50.0, 0.72, 0.76, A_TP)
+    errs = []
+    for ny in (16, 32):
+        nx = nz = ny // 2
+        xs = np.arange(nx) * 2 * np.pi / nx
+        zs = np.arange(nz) * 2 * np.pi / nz
+        ys = -1.0 + (np.arange(ny) + 0.5) * 2.0 / ny
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        vals = [g(X, Y, Z) * np.ones_like(X) for g in f]
+        wv = np.stack([vals[0], vals[0] * vals[1], vals[0] * vals[2], vals[0] * vals[3],
+                       fe(X, Y, Z) * np.ones_like(X)])
+        pr = O.Problem(nx, ny, nz, 2 * np.pi, 2.0, 2 * np.pi, wall_y=True, t_wall=tw, mach=mach, re=50.0,
+                       weno_order=0, cp_coef=A_TP)
+        r = O.rhs(pr, wv)
+        ex = np.stack([g(X, Y, Z) * np.ones_like(X) for g in rhs])
+        errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(rates > 5.0), rates
