@@ -45,8 +45,8 @@ UNIT = "point-steps/s"
 # The FP64 unit issues one add, multiply or fused multiply-add per slot,
 # so OPS against the slot rate is the pipe utilisation and FLOPS against
 # 2 flop/slot the flop-rate fraction.
-ALG_FLOPS = {"prims": 61.0, "grad": 81.0, "flux_x": 91.6, "flux_y": 92.1, "flux_z": 92.1, "visc": 252.7, "update": 20.0}
-FP64_OPS = {"prims": 47.0, "grad": 64.0, "flux_x": 60.5, "flux_y": 60.5, "flux_z": 60.5, "visc": 170.4, "update": 15.0}
+ALG_FLOPS = {"prims": 61.0, "grad": 81.0, "flux_x": 90.6, "flux_y": 92.1, "flux_z": 91.1, "visc": 252.7, "update": 20.0}
+FP64_OPS = {"prims": 47.0, "grad": 64.0, "flux_x": 59.5, "flux_y": 60.5, "flux_z": 59.5, "visc": 170.4, "update": 15.0}
 # DRAM bytes per interior point of one launch from the same ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured.
 DRAM_BYTES = {"prims": 92.1, "grad": 102.3, "flux_x": 89.7, "flux_y": 134.7, "flux_z": 134.7, "visc": 207.4, "update": 155.0}

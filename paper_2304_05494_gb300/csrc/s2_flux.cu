@@ -337,7 +337,9 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
         mm[l - 1] = TP[(l - 1) * ST + at - l * SA];
         M += mp[l - 1] - mm[l - 1];
       }
-      D[0] = R(2) * M;
+      // D_rho = 2 M: in x and z the factor 2 rides on the constant scale
+      // (2/dx, 2/dz, exact), saving a double-precision operation
+      D[0] = DIR == 1 ? R(2) * M : M;
 #pragma unroll
       for (int f = 1; f < 5; ++f) {
         const R *Sf = S + f * SFA;         // F_U .. F_H follow F_RHO
@@ -357,8 +359,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
       const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
       if (DIR == 1 && !S2_OK_IDX(d, pj, d.ny)) continue;
       R scale = DIR == 0 ? K.idx : (DIR == 1 ? __ldg(V.eta_y + pj) : K.idz);
+      const R scale0 = DIR == 0 ? K.idx2 : (DIR == 1 ? scale : K.idz2);
+      V.fl[q[pp]] = fma(-scale0, D[0], prev[pp][0]);
 #pragma unroll
-      for (int f = 0; f < 5; ++f) V.fl[f * d.n + q[pp]] = fma(-scale, D[f], prev[pp][f]);
+      for (int f = 1; f < 5; ++f) V.fl[f * d.n + q[pp]] = fma(-scale, D[f], prev[pp][f]);
     }
     __syncthreads();  // staging buffer and TP free for the next tile
   }

@@ -42,6 +42,7 @@ struct Consts {
   R bx[5], bz[5];          // b_l/dx^2, b_l/dz^2 (second derivative, l = 0..4)
   R acen[5];               // a_l of the central (convective) order, l = 1..4
   R idx, idz;              // 1/dx, 1/dz
+  R idx2, idz2;            // 2/dx, 2/dz
   R R_gas, cp, gamma, gR, icv, visc_exp, inv_t_ref, t_wall, cp_over_pr, re, inv_re, thr;
   R thr2;                  // thr^2 (sensor test without a root)
   R b0xz;                  // b_0/dx^2 + b_0/dz^2 (x and z centre weights of the Laplacian)

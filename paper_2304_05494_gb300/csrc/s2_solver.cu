@@ -1164,6 +1164,8 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     }
     k.idx = d.idx;
     k.idz = d.idz;
+    k.idx2 = 2.0 * d.idx;
+    k.idz2 = 2.0 * d.idz;
     k.R_gas = d.R;
     k.cp = d.cp;
     k.gamma = d.gamma;
@@ -1188,6 +1190,8 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
     }
     f.idx = (float)k.idx;
     f.idz = (float)k.idz;
+    f.idx2 = 2.0f * f.idx;
+    f.idz2 = 2.0f * f.idz;
     f.R_gas = (float)k.R_gas;
     f.cp = (float)k.cp;
     f.gamma = (float)k.gamma;
