@@ -173,17 +173,19 @@ def test_thermally_perfect_noalloc_dt(s2):
     assert abs(out.item() - ref) < 1e-13 * ref
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("gas", ["thermally_perfect", "calorically_perfect"])
-def test_primitive_fields_round_trip(s2, gas):
+def test_primitive_fields_round_trip(s2, gas, precision):
     """s2_set_primitives builds the oracle's conserved state from (rho, u,
     v, w, T) with E = e(T) + |u|^2/2, and s2_get_primitives recovers the
-    fields, from host and from device buffers."""
+    fields, from host and from device buffers (the conversions are double
+    precision in both modes)."""
     c = W.channel(24, 20, 12, seed=2)
     pr = problem(c, A_TP if gas == "thermally_perfect" else None)
     prim = c.prim0.copy()
     prim[4] = 1.0 + 0.6 * (1.0 - np.broadcast_to(c.y[None, :, None], prim[4].shape) ** 2)
     ref = O.conserved(pr, *prim)
-    with solver(s2, pr, cfl=0.8) as sv:
+    with solver(s2, pr, cfl=0.8, precision=precision) as sv:
         sv.set_primitives(prim)
         w_host = sv.get_state()
         back_host = sv.get_primitives()
