@@ -510,10 +510,26 @@ def test_dt_closed_form_uniform():
 
 
 # --------------------------------------------------------- exact solutions ---
+def _golden(name):
+    """name -> (value, tolerance) from a fixture under tests/golden/."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v, tol = line.split()
+            out[k] = (float(v), float(tol))
+    return out
+
+
 def test_riemann_solver_textbook_values():
-    """Star state of Sod's problem as tabulated by Toro (Table 4.3)."""
+    """Star state of Sod's problem as tabulated by Toro (Table 4.3;
+    tests/golden/sod_star_state.txt)."""
+    g = _golden("sod_star_state.txt")
     ps, us = ER.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
-    assert abs(ps - 0.30313) < 5e-5 and abs(us - 0.92745) < 5e-5
+    assert abs(ps - g["p_star"][0]) < g["p_star"][1]
+    assert abs(us - g["u_star"][0]) < g["u_star"][1]
 
 
 def test_sod_exact_solution():
