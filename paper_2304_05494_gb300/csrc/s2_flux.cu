@@ -82,6 +82,7 @@ struct Tile<2, 1> {  // z: 16 along z, 16 columns
 };
 
 constexpr int NTHREADS = 256;
+constexpr int WENO_NT = 64;  // threads per CTA of the WENO kernels
 enum { F_RHO = 0, F_U, F_V, F_W, F_H, F_P, F_S, NF };
 
 // The tile a kernel of arithmetic type R works on.  Double precision uses
@@ -468,7 +469,7 @@ __device__ __forceinline__ R weno_rec(const R *g, R eps) {
 // dissipation is the largest |eigenvalue| (u_n - c, u_n, u_n + c) over the
 // stencil points.  The result goes back with the right eigenvectors.
 template <int DIR, int WR, class R>
-__global__ void __launch_bounds__(128) k_weno(Dev d) {
+__global__ void __launch_bounds__(WENO_NT) k_weno(Dev d) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int NP = 2 * WR;  // stencil points s-WR+1 .. s+WR
   const View<R> V = view<R>(d);
@@ -673,11 +674,13 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  long long need = (d.nslot[DIR] + 127) / 128;
-  long long cap = 8LL * sms;
+  // small CTAs: the flagged interfaces (a device-side count, often a few
+  // per cent of the slots) then spread evenly over the multiprocessors
+  long long need = (d.nslot[DIR] + WENO_NT - 1) / WENO_NT;
+  long long cap = 16LL * sms;
   unsigned nb = (unsigned)(need < cap ? need : cap);
   if (nb == 0) nb = 1;
-  k_weno<DIR, WR, R><<<nb, 128, 0, st>>>(d);
+  k_weno<DIR, WR, R><<<nb, WENO_NT, 0, st>>>(d);
   return cudaGetLastError();
 }
 
