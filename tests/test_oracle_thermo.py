@@ -301,3 +301,22 @@ def test_thermally_perfect_design_order_with_walls():
         errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
     rates = np.log2(errs[0] / errs[1])
     assert np.all(rates > 5.0), rates
+
+
+def test_thermally_perfect_dt_closed_form_uniform():
+    """CFL dt of a uniform state: c = sqrt(gamma(T) R T) and the viscous
+    term gamma(T) mu / (Pr rho), gamma(T) = c_p/(c_p - R) of the polynomial."""
+    mach, T, rho = 0.5, 1.7, 1.3
+    R = 1.0 / (GAMMA * mach ** 2)
+    p = _prob(8, 8, 8, mach=mach, re=200.0, prandtl=0.7, cp_coef=A_TP)
+    one = np.ones((8, 8, 8))
+    w = O.conserved(p, rho * one, 0.4 * one, -0.3 * one, 0.2 * one, T * one)
+    cp = R * _cp_over_r(A_TP, T)
+    gam = cp / (cp - R)
+    c = np.sqrt(gam * R * T)
+    h = 2 * np.pi / 8
+    conv = (0.4 + c + 0.3 + c + 0.2 + c) / h
+    visc = gam * (T ** 0.76 / 200.0) / (0.7 * rho) * 3 / h ** 2
+    assert abs(O.dt(p, w, 0.8) - 0.8 / (conv + visc)) < 1e-13 * (0.8 / (conv + visc))
+    # and gamma(T) is not the reference gamma here
+    assert abs(gam - GAMMA) > 1e-3
