@@ -80,3 +80,19 @@ def test_python_binding_names_match_header():
     from paper_2304_05494_gb300 import s2
     for f in header_functions():
         assert hasattr(s2, f), f
+
+
+def test_binding_refuses_wrong_state_sizes():
+    """The Solver wrapper checks a buffer's shape before the library reads
+    or writes 5 nx ny nz doubles through it (no device needed: the check
+    runs before any call)."""
+    import numpy as np
+    import pytest
+    from paper_2304_05494_gb300 import s2
+    sv = object.__new__(s2.Solver)
+    sv.shape, sv.n, sv.h = (5, 4, 3, 2), 24, None
+    assert sv._fits(np.zeros((5, 4, 3, 2))) is not None
+    assert sv._fits(np.zeros(120)) is not None
+    for bad in (np.zeros((5, 4, 3, 3)), np.zeros(119), np.zeros((4, 4, 3, 2))):
+        with pytest.raises(ValueError):
+            sv._fits(bad)
