@@ -56,40 +56,47 @@ class _Cfg(C.Structure):
 _lib = None
 
 
+def load(path: str) -> C.CDLL:
+    """Load an oracle library built from ``s2_oracle.c`` and declare its entry
+    points (the tests also load deliberately broken copies this way)."""
+    lb = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    bp = C.POINTER(C.c_ubyte)
+    lb.or_rhs.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int, dp]
+    lb.or_rhs.restype = C.c_int
+    lb.or_rhs_given_flags.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int]
+    lb.or_rhs_given_flags.restype = C.c_int
+    lb.or_sensor.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
+    lb.or_sensor.restype = C.c_int
+    lb.or_dt.argtypes = [C.POINTER(_Cfg), dp, C.c_double]
+    lb.or_dt.restype = C.c_double
+    lb.or_step.argtypes = [C.POINTER(_Cfg), dp, C.c_int, C.c_double, C.c_double, C.c_int,
+                           C.POINTER(C.c_longlong), dp]
+    lb.or_step.restype = C.c_int
+    lb.or_metric.argtypes = [C.POINTER(_Cfg), dp, dp]
+    lb.or_weno_rec.argtypes = [C.c_int, dp]
+    lb.or_weno_rec.restype = C.c_double
+    lb.or_weno_parts.argtypes = [C.c_int, dp, dp, dp]
+    lb.or_weno_parts.restype = C.c_int
+    lb.or_eigvec.argtypes = [C.c_double, C.c_int, dp, C.c_double, dp, dp]
+    lb.or_eigvec.restype = C.c_double
+    lb.or_eigvec_tp.argtypes = [C.c_double, C.c_double, C.c_int, dp, C.c_double, dp, dp]
+    lb.or_eigvec_tp.restype = C.c_double
+    lb.or_thermo.argtypes = [C.POINTER(_Cfg), C.c_double, dp, dp, dp]
+    lb.or_thermo.restype = C.c_int
+    lb.or_temperature.argtypes = [C.POINTER(_Cfg), C.c_double, C.c_int, C.c_double]
+    lb.or_temperature.restype = C.c_double
+    lb.or_roe_state.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
+    lb.or_roe_state.restype = C.c_int
+    lb.or_rk3_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
+    lb.or_rk3_scalar.restype = C.c_double
+    return lb
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        dp = C.POINTER(C.c_double)
-        bp = C.POINTER(C.c_ubyte)
-        _lib.or_rhs.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int, dp]
-        _lib.or_rhs.restype = C.c_int
-        _lib.or_rhs_given_flags.argtypes = [C.POINTER(_Cfg), dp, dp, bp, bp, bp, C.c_int]
-        _lib.or_rhs_given_flags.restype = C.c_int
-        _lib.or_sensor.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
-        _lib.or_sensor.restype = C.c_int
-        _lib.or_dt.argtypes = [C.POINTER(_Cfg), dp, C.c_double]
-        _lib.or_dt.restype = C.c_double
-        _lib.or_step.argtypes = [C.POINTER(_Cfg), dp, C.c_int, C.c_double, C.c_double, C.c_int,
-                                 C.POINTER(C.c_longlong), dp]
-        _lib.or_step.restype = C.c_int
-        _lib.or_metric.argtypes = [C.POINTER(_Cfg), dp, dp]
-        _lib.or_weno_rec.argtypes = [C.c_int, dp]
-        _lib.or_weno_rec.restype = C.c_double
-        _lib.or_weno_parts.argtypes = [C.c_int, dp, dp, dp]
-        _lib.or_weno_parts.restype = C.c_int
-        _lib.or_eigvec.argtypes = [C.c_double, C.c_int, dp, C.c_double, dp, dp]
-        _lib.or_eigvec.restype = C.c_double
-        _lib.or_eigvec_tp.argtypes = [C.c_double, C.c_double, C.c_int, dp, C.c_double, dp, dp]
-        _lib.or_eigvec_tp.restype = C.c_double
-        _lib.or_thermo.argtypes = [C.POINTER(_Cfg), C.c_double, dp, dp, dp]
-        _lib.or_thermo.restype = C.c_int
-        _lib.or_temperature.argtypes = [C.POINTER(_Cfg), C.c_double, C.c_int, C.c_double]
-        _lib.or_temperature.restype = C.c_double
-        _lib.or_roe_state.argtypes = [C.POINTER(_Cfg), dp, dp, dp]
-        _lib.or_roe_state.restype = C.c_int
-        _lib.or_rk3_scalar.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int]
-        _lib.or_rk3_scalar.restype = C.c_double
+        _lib = load(build())
     return _lib
 
 

@@ -679,22 +679,15 @@ static void weno_flux(const ws_t *s, int dir, int pos, int i, int j, int k, doub
   int np = 2 * r; /* stencil points pos-r+1 .. pos+r */
   size_t a = at(s, dir, pos, i, j, k), bq = at(s, dir, pos + 1, i, j, k);
   /* Roe average of the states at pos and pos+1 */
-  double ra = sqrt(s->rho[a]), rb = sqrt(s->rho[bq]);
-  double uv[3], H;
-  uv[0] = (ra * s->u[a] + rb * s->u[bq]) / (ra + rb);
-  uv[1] = (ra * s->v[a] + rb * s->v[bq]) / (ra + rb);
-  uv[2] = (ra * s->w[a] + rb * s->w[bq]) / (ra + rb);
-  H = (ra * s->H[a] + rb * s->H[bq]) / (ra + rb);
+  double sa[5] = {s->rho[a], s->u[a], s->v[a], s->w[a], s->T[a]};
+  double sb[5] = {s->rho[bq], s->u[bq], s->v[bq], s->w[bq], s->T[bq]};
+  double roe[6];
+  roe_state(s, sa, sb, roe);
   double Lm[25], Rm[25];
-  if (!s->tp) {
-    or_eigvec(gam, dir, uv, H, Lm, Rm);
-  } else {
-    double sa[5] = {s->rho[a], s->u[a], s->v[a], s->w[a], s->T[a]};
-    double sb[5] = {s->rho[bq], s->u[bq], s->v[bq], s->w[bq], s->T[bq]};
-    double roe[6];
-    roe_state(s, sa, sb, roe);
+  if (!s->tp)
+    or_eigvec(gam, dir, roe, roe[3], Lm, Rm);
+  else
     or_eigvec_tp(roe[4], roe[5], dir, roe, roe[3], Lm, Rm);
-  }
   double V[8][5], G[8][5], lam[8][5];
   for (int m = 0; m < np; ++m) {
     size_t q = at(s, dir, pos - r + 1 + m, i, j, k);

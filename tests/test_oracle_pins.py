@@ -616,3 +616,196 @@ def test_forcing_is_body_force_with_its_power():
     assert np.allclose(d[1], f, rtol=1e-12, atol=0)
     assert np.max(np.abs(d[[0, 2, 3]])) == 0.0
     assert np.allclose(d[4], f * c.w0[1] / c.w0[0], rtol=1e-12, atol=1e-15)
+
+
+# --------------------------------------------- characteristic WENO flux ---
+def _linear_upwind_coeffs(order):
+    """Coefficients c_m, m = -(r-1) .. r-1, of the linear (optimal-weight)
+    reconstruction at x_{i+1/2} from the left, derived symbolically here."""
+    fs, qs, _, d = _jiang_shu_reference(order)
+    lin = sp.expand(sum(d[k] * qs[k] for k in range(len(qs))))
+    return np.array([float(lin.coeff(f)) for f in fs])
+
+
+def _upwind_symbol_rhs(order, speed, eps, k, h, x):
+    """-(speed/h) times the flux difference of the linear upwind
+    reconstruction of eps sin(k x), taken from the side the wave comes from:
+    F_{i+1/2} = speed sum_m c_m f_{i+m} (speed > 0) or speed sum_m c_m
+    f_{i+1-m} (speed < 0)."""
+    c = _linear_upwind_coeffs(order)
+    r = (order + 1) // 2
+    m = np.arange(-(r - 1), r)
+    shift = m if speed > 0 else 1 - m
+    S = np.sum(c * np.exp(1j * k * shift * h))
+    return -(speed * eps / h) * np.imag(np.exp(1j * k * x) * S * (1.0 - np.exp(-1j * k * h)))
+
+
+def _central_symbol_rhs(order, speed, eps, k, h, x):
+    """The same with the non-dissipative central reconstruction of the same
+    stencil width (the mean of the left and right linear reconstructions)."""
+    return 0.5 * (_upwind_symbol_rhs(order, speed, eps, k, h, x) + _upwind_symbol_rhs(order, -speed, eps, k, h, x)
+                  * -1.0)
+
+
+@pytest.mark.parametrize("order", [1, 3, 5, 7])
+@pytest.mark.parametrize("U", [0.6, -0.45])
+def test_weno_entropy_wave_linear_upwind_symbol(order, U):
+    """Small-amplitude entropy wave (velocity U and pressure uniform), WENO at
+    every interface, inviscid.  With amplitude 1e-8 the nonlinear weights equal
+    the linear ones to ~1e-9, and the characteristic Lax-Friedrichs flux of
+    the mass equation is exactly U times the linear upwind reconstruction of
+    rho from the side the flow comes from -- but only if the entropy field is
+    split with its own dissipation max|u_n| = |U| (one alpha per
+    characteristic field).  With one alpha = max(|u_n| + c) for every field the
+    entropy wave would get the extra dissipation (c/2)(upwind - downwind),
+    some 1e-3 of R_rho here.  R_rho must equal the closed-form symbol of the
+    upwind scheme to 1e-6."""
+    n, k, eps, mach = 32, 5, 1e-8, 0.5
+    h = 2 * np.pi / n
+    x = np.arange(n) * h
+    X = x[None, None, :] * np.ones((1, 1, n))
+    rho = 1.0 + eps * np.sin(k * X)
+    one = np.ones_like(X)
+    w = W.conserved(rho, U * one, 0 * one, 0 * one, 1.0 / rho, 1.4, mach)  # p = rho R T uniform
+    p = O.Problem(n, 1, 1, 2 * np.pi, 1.0, 1.0, mach=mach, re=-1.0, weno_order=order, threshold=-1.0)
+    r = O.rhs(p, w, terms=O.CONV)
+    exact = _upwind_symbol_rhs(order, U, eps, k, h, x)
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(r[0, 0, 0] - exact)) < 1e-6 * scale
+    # the momentum row follows the mass flux (u uniform); its flux carries
+    # the pressure, ~300 times R_rho here, hence the rounding allowance
+    assert np.max(np.abs(r[1, 0, 0] - U * exact)) < 1e-5 * abs(U) * scale
+    # the test resolves the dissipation: the central symbol of the same width is far off
+    if order > 1:
+        central = _central_symbol_rhs(order, U, eps, k, h, x)
+        assert np.max(np.abs(central - exact)) > 1e-4 * scale
+
+
+@pytest.mark.parametrize("order", [3, 5, 7])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_weno_acoustic_wave_linear_upwind_symbol(order, sign):
+    """Small-amplitude acoustic wave carried by the u + sign*c field alone
+    (rho' = eps s, u' = sign c eps s, p' = c^2 eps s, s = sin kx) on a flow
+    at U = 0.3, c = 2, WENO everywhere: every conserved field's RHS is the
+    linear upwind symbol at the speed U + sign*c, taken from that speed's
+    upwind side, up to O(eps) relative.  Pins the eigenvectors (no leak into
+    the other fields), the side each field is upwinded from and the
+    acoustic fields' dissipation."""
+    n, k, eps, mach, U, g = 32, 5, 1e-8, 0.5, 0.3, 1.4
+    c0 = 1.0 / mach  # T = 1: c^2 = gamma R T = 1/M^2
+    h = 2 * np.pi / n
+    x = np.arange(n) * h
+    X = x[None, None, :] * np.ones((1, 1, n))
+    s = np.sin(k * X)
+    Rg = 1.0 / (g * mach * mach)
+    rho = 1.0 + eps * s
+    u = U + sign * c0 * eps * s
+    pr = Rg + c0 * c0 * eps * s
+    one = np.ones_like(X)
+    w = W.conserved(rho, u, 0 * one, 0 * one, pr / (rho * Rg), g, mach)
+    p = O.Problem(n, 1, 1, 2 * np.pi, 1.0, 1.0, mach=mach, re=-1.0, weno_order=order, threshold=-1.0)
+    r = O.rhs(p, w, terms=O.CONV)
+    lam = U + sign * c0
+    exact = _upwind_symbol_rhs(order, lam, eps, k, h, x)
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(r[0, 0, 0] - exact)) < 1e-6 * scale
+    # momentum: d(rho u)' = u0 rho' + rho0 u' = (U + sign c) eps s
+    assert np.max(np.abs(r[1, 0, 0] - (U + sign * c0) * exact)) < 1e-6 * abs(U + sign * c0) * scale
+    assert np.max(np.abs(r[2:4])) < 1e-6 * scale
+
+
+def test_roe_average_property_calorically_perfect():
+    """Roe's property of the sqrt(rho)-weighted state of the WENO flux: with
+    A~ = R diag(u_n - c, u_n, u_n, u_n, u_n + c) L at that state,
+    A~ (w_b - w_a) = F(w_b) - F(w_a) exactly, for any two states of a
+    calorically perfect gas (Roe 1981).  An arithmetic mean of H or u, or a
+    sound speed not from (gamma-1)(H - |u|^2/2), breaks it."""
+    g, mach = 1.4, 0.5
+    Rg = 1.0 / (g * mach * mach)
+    cv = Rg / (g - 1.0)
+    p = O.Problem(4, 4, 4, 1.0, 1.0, 1.0, mach=mach, gamma=g)
+    rng = np.random.default_rng(17)
+    for d in range(3):
+        for _ in range(20):
+            sa = np.array([rng.uniform(0.2, 3.0), *rng.normal(size=3), rng.uniform(0.3, 3.0)])
+            sb = np.array([rng.uniform(0.2, 3.0), *rng.normal(size=3), rng.uniform(0.3, 3.0)])
+            roe = O.roe_state(p, sa, sb)
+            L, R, c = O.eigvec(g, d, roe[:3], roe[3])
+            assert abs(roe[5] - c) <= 1e-14 * c
+            lam = np.diag([roe[d] - c, roe[d], roe[d], roe[d], roe[d] + c])
+            A = R @ lam @ L
+
+            def cons(st):
+                rho, vel, T = st[0], st[1:4], st[4]
+                return np.array([rho, *(rho * vel), rho * (cv * T + 0.5 * np.dot(vel, vel))])
+
+            wa, wb = cons(sa), cons(sb)
+            dF = _euler_flux(wb, d, g) - _euler_flux(wa, d, g)
+            scale = np.max(np.abs(_euler_flux(wb, d, g))) + np.max(np.abs(_euler_flux(wa, d, g)))
+            assert np.max(np.abs(A @ (wb - wa) - dF)) < 1e-12 * scale
+
+
+def test_weno7_indicator_evaluation_form():
+    """The WENO7 smoothness indicators are one quadratic form of the stencil
+    values (240 x the Jiang-Shu integral).  The oracle evaluates it as a
+    weighted sum of squares of undivided differences; the alternative is the
+    expanded form sum_ij C_ij f_i f_j.  Against the exact rational value of
+    the integral definition (fractions.Fraction), on stencils with a common
+    offset much larger than their variation -- characteristic fluxes near a
+    mean state -- the sum of squares stays within a few 1e-7 relative while
+    the expanded form loses every digit to cancellation; on unit-scale data
+    both are at rounding level.  This, not agreement with another
+    implementation, is why the oracle uses that form."""
+    from fractions import Fraction
+
+    fs, _, bs, _ = _jiang_shu_reference(7)
+    polys = [sp.Poly(sp.expand(240 * b), *fs) for b in bs]
+    terms = [[(tuple(mon), Fraction(int(sp.fraction(cf)[0]), int(sp.fraction(cf)[1])))
+              for mon, cf in P.terms()] for P in polys]
+
+    def exact(f):
+        fr = [Fraction(float(v)) for v in f]
+        out = []
+        for tt in terms:
+            acc = Fraction(0)
+            for mon, cf in tt:
+                t = cf
+                for i, e in enumerate(mon):
+                    if e:
+                        t *= fr[i] ** e
+                acc += t
+            out.append(acc)
+        return out
+
+    def expanded(f):
+        out = []
+        for tt in terms:
+            acc = 0.0
+            for mon, cf in tt:
+                t = float(cf)
+                for i, e in enumerate(mon):
+                    for _ in range(e):
+                        t *= float(f[i])
+                acc += t
+            out.append(acc)
+        return out
+
+    rng = np.random.default_rng(29)
+    err_sos = {"offset": 0.0, "unit": 0.0}
+    err_exp = {"offset": 0.0, "unit": 0.0}
+    for trial in range(120):
+        kind = "offset" if trial % 2 == 0 else "unit"
+        if kind == "offset":
+            f = rng.uniform(-1e3, 1e3) + rng.normal(size=7) * 10.0 ** rng.uniform(-5, -1)
+        else:
+            f = rng.normal(size=7)
+        ex = exact(f)
+        _, b = O.weno_parts(7, f)
+        be = expanded(f)
+        for kk in range(4):
+            ref = float(ex[kk])
+            err_sos[kind] = max(err_sos[kind], abs(b[kk] - ref) / ref)
+            err_exp[kind] = max(err_exp[kind], abs(be[kk] - ref) / ref)
+    assert err_sos["unit"] < 1e-13 and err_exp["unit"] < 1e-12
+    assert err_sos["offset"] < 1e-6
+    assert err_exp["offset"] > 1e3 * err_sos["offset"]
