@@ -11,8 +11,11 @@
 //
 // The array lives in every GPU that loads the library, until the process
 // exits.  Host code only sees a stand-in for it, so its device address is
-// looked up (cudaGetSymbolAddress) once per device, on that device's first
-// call, and cached.
+// looked up (cudaGetSymbolAddress) once per device and context, on the
+// first call with that device current, and cached with the identifier of
+// the context it belongs to; a call that finds another context current
+// (the device was reset since) looks it up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -31,9 +34,16 @@ constexpr int PTS_PER_THREAD = 16;
 constexpr int MAX_PARTS = 65536;
 static __device__ __align__(256) double g_dt_parts[MAX_PARTS];
 
+// Largest grid: one partial per CTA of NT * PTS_PER_THREAD points.
+constexpr long long MAX_POINTS = (long long)MAX_PARTS * NT * PTS_PER_THREAD;
+
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
-double *g_parts_addr[MAX_DEVICES] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id;  // process-unique context identifier (cuCtxGetId)
+  double *ptr;
+};
+ScratchAddr g_parts_addr[MAX_DEVICES] = {};
 
 __device__ __forceinline__ double wmax(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -67,13 +77,14 @@ __global__ void __launch_bounds__(NT) k_cfl_parts(Dev d, const double *__restric
     double q2 = u * u + v * v + ww * ww;
     const double e = w[4 * d.n + q] * ri - 0.5 * q2;
     double T = e * d.icv;
-    if (d.kd.tp) {
-      bool ok = true;
-      T = tp_temperature(d.kd, e, tp_guess(d.kd, e), 0.0, ok);
-      if (!ok) {  // no temperature for this energy: dt = 0 reports it
-        m = INFINITY;
-        continue;
-      }
+    bool ok = true;
+    if (d.kd.tp && positive_finite(rho) && finite_bits(e)) T = tp_temperature(d.kd, e, tp_guess(d.kd, e), 0.0, ok);
+    // the solver's validity test (rho and T positive and finite, |u|^2
+    // finite): an invalid point has no spectral radius, and dt = 0
+    // reports it
+    if (!ok || !positive_finite(rho) || !positive_finite(T) || !finite_bits(q2)) {
+      m = INFINITY;
+      continue;
     }
     double mu = d.viscous ? viscosity(d, T) : 0.0;
     double ey = eta_y ? eta_y[j] : ey_uniform;
@@ -90,21 +101,51 @@ __global__ void __launch_bounds__(NT) k_cfl_final(const double *parts, int npart
   if (threadIdx.x == 0) dt[0] = cfl / m;
 }
 
-// Device address of the scratch array on the current device (looked up
-// once per device).
+// The driver's cuCtxGetCurrent and cuCtxGetId, reached through the
+// runtime (no link against the driver library).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+void *driver_fn(const char *name) {
+  void *p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return p;
+}
+
+// Identifier of the calling thread's current context; 0 if none is
+// current yet (the runtime creates it at its first device call).
+cudaError_t current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get = (CtxGetCurrentFn)driver_fn("cuCtxGetCurrent");
+  static CtxGetIdFn get_id = (CtxGetIdFn)driver_fn("cuCtxGetId");
+  *id = 0;
+  if (!get || !get_id) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
+
+// Device address of the scratch array on the current device, looked up
+// once per device and context.
 cudaError_t scratch_address(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  unsigned long long id = 0;
+  if ((e = current_context_id(&id)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_parts_addr[dev]) {
+  if (!id || !g_parts_addr[dev].ptr || g_parts_addr[dev].ctx_id != id) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_dt_parts);
+    e = cudaGetSymbolAddress(&p, g_dt_parts);  // creates the context if none was current
     if (e != cudaSuccess) return e;
-    g_parts_addr[dev] = (double *)p;
+    if (!id && ((e = current_context_id(&id)) != cudaSuccess || !id)) return cudaErrorDeviceUninitialized;
+    g_parts_addr[dev].ctx_id = id;
+    g_parts_addr[dev].ptr = (double *)p;
   }
-  *out = g_parts_addr[dev];
+  *out = g_parts_addr[dev].ptr;
   return cudaSuccess;
 }
 
@@ -116,10 +157,16 @@ extern "C" int s2_cfl_dt_noalloc(const s2_grid *grid, const s2_gas *gas, const d
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0) || !(grid->lz > 0))
     return S2_EINVAL;
   if (check_gas(gas, 0.0) != S2_OK) return S2_EINVAL;
-  long long n = (long long)grid->nx * grid->ny * grid->nz;
-  long long per_cta = (long long)NT * PTS_PER_THREAD;
-  long long nparts = (n + per_cta - 1) / per_cta;
-  if (nparts > MAX_PARTS) return S2_ETOOBIG;
+  // size checked factor by factor: every partial product stays below
+  // MAX_POINTS before the next multiplication, so nothing overflows
+  long long n = grid->nx;
+  if (n > MAX_POINTS) return S2_ETOOBIG;
+  n *= grid->ny;
+  if (n > MAX_POINTS) return S2_ETOOBIG;
+  n *= grid->nz;
+  if (n > MAX_POINTS) return S2_ETOOBIG;
+  const long long per_cta = (long long)NT * PTS_PER_THREAD;
+  const long long nparts = (n + per_cta - 1) / per_cta;
   Dev d;
   memset(&d, 0, sizeof(d));
   d.nx = grid->nx;

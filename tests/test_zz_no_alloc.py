@@ -35,10 +35,10 @@ def solver_dt(s2, case):
         return sv.stats()["dt"]
 
 
-def noalloc_dt(s2, case, eta_y):
+def noalloc_dt(s2, case, eta_y, w0=None):
     grid = s2.s2_grid(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz)
     gas = s2.s2_gas(case.gamma, case.prandtl, case.mach, case.re, case.visc_exp, case.t_ref)
-    w = torch.from_numpy(case.w0).cuda()
+    w = torch.from_numpy(case.w0 if w0 is None else w0).cuda()
     ey = torch.from_numpy(eta_y).cuda() if eta_y is not None else None
     dt = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream()
@@ -64,6 +64,24 @@ def test_noalloc_dt_matches_solver_twice_in_a_row(s2):
     assert noalloc_dt(s2, tgv, None) == a
 
 
+@pytest.mark.parametrize("bad", ["negative_density", "negative_energy", "nan_momentum"])
+def test_noalloc_dt_is_zero_for_an_invalid_state(s2, bad):
+    """A single point that s2_step would report as invalid makes dt = 0
+    instead of a plausible value taken from the other points."""
+    tgv = W.taylor_green(24)
+    w = tgv.w0.copy()
+    if bad == "negative_density":
+        w[0, 3, 5, 7] = -w[0, 3, 5, 7]
+    elif bad == "negative_energy":
+        w[4, 3, 5, 7] = -1.0
+    else:
+        w[2, 3, 5, 7] = np.nan
+    assert noalloc_dt(s2, tgv, None) > 0.0
+    assert noalloc_dt(s2, tgv, None, w) == 0.0
+    # and the next call on a valid state is unaffected by the shared scratch
+    assert noalloc_dt(s2, tgv, None) > 0.0
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch(s2):
     grid = s2.s2_grid(2048, 1024, 1024, 1.0, 1.0, 1.0)
     gas = s2.s2_gas(1.4, 0.72, 0.5, 100.0, 0.76, 1.0)
@@ -72,3 +90,8 @@ def test_noalloc_rejects_grids_beyond_its_scratch(s2):
     rc = s2.s2_cfl_dt_noalloc(grid, gas, w, None, 0.8, dt, None)
     assert rc == s2.S2_ETOOBIG
     assert "scratch" in s2.s2_strerror(rc)
+    # extents whose product would overflow a 64-bit integer are rejected too
+    big = 2 ** 31 - 1
+    for ext in ((big, big, big), (1, big, big), (big, 1, 1)):
+        rc = s2.s2_cfl_dt_noalloc(s2.s2_grid(*ext, 1.0, 1.0, 1.0), gas, w, None, 0.8, dt, None)
+        assert rc == s2.S2_ETOOBIG, ext
