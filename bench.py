@@ -1,16 +1,19 @@
 #!/usr/bin/env python
-"""Benchmark: grid-point RK3 steps per second of the FP64 solver.
+"""Benchmark: grid-point RK3 steps per second of the solver.
 
-Workload: the compressible turbulent channel, bulk Mach 1.5, Re_tau ~ 220,
-256 x 128 x 128 points (6 pi h x 2h x 2 pi h, tanh-stretched y, isothermal
-walls, constant mass flow), hybrid central-6 / WENO5 where the sensor
-exceeds 0.2, 6th-order viscous terms, dt from CFL 0.8 every 10 steps.
-Synthetic seeded initial state (laminar Poiseuille profile plus 10 %
-smooth random velocity perturbations).
+Headline workload: the large compressible turbulent channel, bulk Mach 1.5,
+Re_tau ~ 550, 1024 x 256 x 512 points (134M; 6 pi h x 2h x 2 pi h,
+tanh-stretched y, first wall cell at dy+ = 0.7, isothermal walls, constant
+mass flow), hybrid central-6 / WENO5 where the sensor exceeds 0.2,
+6th-order viscous terms, dt from CFL 0.8 every 10 steps, in double
+precision (`value`) and in mixed precision (`mixed`: single-precision
+flux, WENO and viscous arithmetic, double-precision state and RK
+accumulation).  Synthetic seeded initial state (laminar Poiseuille profile
+plus 10 % smooth random velocity perturbations).
 
 One step = one full RK3 step (3 RHS stages) of the whole grid.  The state
-(168 MB) and the working set (~1.2 GB) are larger than the 129 MB L2, so no
-L2 flush is needed between steps.
+(5.4 GB) and the working set (tens of GB) are far larger than the 129 MB
+L2, so no L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -18,9 +21,11 @@ N > 1 runs under torchrun as independent replicas (the solver does not
 shard across GPUs); value = all ranks' point-steps / the slowest rank's time.
 The reference arm times the plain CPU oracle on the host cores.
 
-Beside the FP64 line: the same workload in mixed precision (`mixed`), with
-a thermally perfect gas (`thermally_perfect`), and a short continuous-
-batching serving run for the p50/p99 batched step latency (`serving`).
+Beside the headline: the 256 x 128 x 128 channel (Re_tau ~ 220) in both
+precisions (`channel256`), the same with a thermally perfect gas
+(`thermally_perfect`), and a continuous-batching serving run of the serving
+workload for the p50/p99 batched step latency (`serving`).  The last keys
+of the line repeat the mixed-precision figures.
 """
 from __future__ import annotations
 
@@ -39,20 +44,28 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point RK3 steps/s"
 UNIT = "point-steps/s"
 
-# FP64 work per interior point of one launch of each kernel as formulated
-# (ncu, channel 256x128x128 hybrid: dadd + dmul + 2 dfma thread
-# instructions / points for FLOPS; every FP64-pipe instruction for OPS).
-# The FP64 unit issues one add, multiply or fused multiply-add per slot,
-# so OPS against the slot rate is the pipe utilisation and FLOPS against
-# 2 flop/slot the flop-rate fraction.
-ALG_FLOPS = {"prims": 61.0, "grad": 81.0, "flux_x": 90.6, "flux_y": 92.1, "flux_z": 91.1, "visc": 252.7, "update": 20.0}
-FP64_OPS = {"prims": 47.0, "grad": 64.0, "flux_x": 59.5, "flux_y": 60.5, "flux_z": 59.5, "visc": 170.4, "update": 15.0}
-# DRAM bytes per interior point of one launch from the same ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum); None where not captured.
-DRAM_BYTES = {"prims": 92.1, "grad": 102.3, "flux_x": 89.7, "flux_y": 134.7, "flux_z": 134.7, "visc": 207.4, "update": 155.0}
-# FP64 peak: 152 SMs x 2 DFMA/clk (4 flop) x 2070 MHz maximum SM clock.
+# Algorithmic double-precision operations per interior point of one launch
+# of each kernel class: the CPU oracle's operation tally (oracle/tally.py;
+# adds, multiplies, divides, square roots and pow/log/exp, one flop each)
+# of the part of the method that the kernel computes, for the benchmark
+# scheme (central 6, WENO5, viscous 6, calorically perfect gas).
+# tests/test_oracle_tally.py checks them against a fresh tally.
+#   prims   primitive recovery (14) and H, c (11)
+#   grad    nine velocity gradients, divergence and shock sensor
+#   visc    viscous and heat-flux terms, given the velocity gradients
+#   update  RK3 update, 5 per field
+ALG_FLOPS = {"prims": 25.0, "grad": 105.0, "visc": 383.0, "update": 25.0}
+ALG_FLOPS_VISC_GRAD = 90.0            # the nine velocity gradients the viscous terms use
+ALG_FLOPS_CENTRAL_INTERFACE = 226.0   # one split-form interface flux (5 fields)
+ALG_FLOPS_WENO_INTERFACE = 1760.0     # one characteristic WENO5 interface flux
+ALG_FLOPS_FLUX_DIFFERENCE = 47.0 / 3  # flux difference per point and direction
+# Double-precision issue peak of the FP64 unit: 152 SMs x 2 DFMA per clock
+# (4 flop) at the 2070 MHz maximum SM clock.
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
-FP64_PEAK_GOPS = FP64_PEAK_GFLOPS / 2
+# DRAM bytes per interior point of one launch of the FP64 viscous kernel
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum, 256 x 128 x 128
+# channel; profiles/channel256x128x128_fp64_kernels_dram.md).
+FP64_DRAM_BYTES = {"visc": 207.4}
 # Mixed path: algorithmic HBM bytes per interior point of one launch
 # (single-precision primitives and RHS, double-precision state; each field
 # read or written once, halos not counted):
@@ -62,9 +75,11 @@ FP64_PEAK_GOPS = FP64_PEAK_GFLOPS / 2
 #   visc   u, v, w, T, div u, mu (24) + RHS read and write (40)
 #   update w read/write (80), RHS (20), RK register read and write on 2 of 3 stages (26.7), u (4)
 MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68, "visc": 64, "update": 130.7}
+# The method's algorithmic traffic per point and RK3 step: per stage read
+# and write the state and the RK register, 4 x 40 B.
+METHOD_BYTES_PER_POINT_STEP = 480.0
 # DRAM bytes per interior point of one launch of the mixed kernels (ncu,
-# same workload, captured with the current kernels; stage 0 of a step that
-# recomputes dt): the traffic of the reported kernel.
+# 256 x 128 x 128 channel, current kernels; profiles/channel256x128x128_mixed_kernels_dram.md).
 MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.3, "update": 110.6}
 # Thermally perfect gas of the side measurement: a synthetic polynomial of
 # the NASA 9-coefficient form, c_p/R = sum_{l=-2..4} a_l T^l (reference
@@ -89,26 +104,33 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--profile-steps", type=int, default=3)
-    ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-tp", action="store_true", help="skip the thermally perfect gas measurement")
-    ap.add_argument("--serve-requests", type=int, default=32,
-                    help="requests of the short serving run (p50/p99 batched step latency); 0 skips it")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--err-steps", type=int, default=10,
+                    help="steps of the mixed-vs-FP64 error measurement on the headline workload")
+    ap.add_argument("--no-side", action="store_true", help="skip the 256x128x128 channel and thermally perfect legs")
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the serving run (p50/p99 batched step latency); 0 skips it")
+    ap.add_argument("--small", action="store_true", help="headline on the 256x128x128 channel (quick checks)")
     return ap.parse_args()
 
 
-def workload():
+def workload(small: bool = False):
     from paper_2304_05494_gb300 import workloads as W
-    return W.channel()
+    return W.channel() if small else W.channel_big()
 
 
 def config_of(case):
-    return {"workload": "compressible channel %dx%dx%d (6pi x 2 x 2pi, tanh y, M_b=1.5, Re_tau~220), "
-                        "FP64 hybrid central-6/WENO5 (sensor>0.2), viscous-6, RK3, CFL 0.8 dt every 10"
-                        % (case.nx, case.ny, case.nz),
-            "points": case.points, "grid": [case.nx, case.ny, case.nz], "seed": 1235,
-            "l2": "inputs larger than L2 (state 168 MB, working set ~1.2 GB > 129 MB L2); no flush"}
+    retau = 550 if case.nx == 1024 else 220
+    return {"workload": "compressible channel %dx%dx%d (6pi x 2 x 2pi, tanh y, M_b=1.5, Re_tau~%d), "
+                        "hybrid central-6/WENO5 (sensor>0.2), viscous-6, RK3, CFL 0.8 dt every 10; "
+                        "value FP64, mixed = f32 flux/f64 state" % (case.nx, case.ny, case.nz, retau),
+            "points": case.points, "grid": [case.nx, case.ny, case.nz], "seed": case_seed(case),
+            "l2": "inputs larger than L2 (state %.1f GB > 129 MB L2); no flush" % (case.w0.nbytes / 1e9)}
+
+
+def case_seed(case):
+    return 1234 + (3 if case.nx == 1024 else 1)
 
 
 class Clocks:
@@ -162,76 +184,87 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _problem(O, case, nz=None):
+    sub = case.nz if nz is None else nz
+    return O.Problem(case.nx, case.ny, sub, case.lx, case.ly, case.lz * sub / case.nz, y=case.y, mach=case.mach,
+                     re=case.re, visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y,
+                     t_wall=case.t_wall, force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+
+
+def slab_planes(case) -> int:
+    """z-slab of the workload that one oracle RK3 step covers in a second or
+    two on a many-core host (8 planes of 1024 x 256, or 16 of 256 x 128)."""
+    return max(4, min(case.nz, (2 << 20) // (case.nx * case.ny)))
+
+
 def cpu_baseline(case, budget_s: float = 15.0):
-    """The CPU oracle, as it stands, on a bounded sample of the workload."""
-    import numpy as np  # noqa: F401
+    """The CPU oracle, as it stands, on a bounded sample of the workload: RK3
+    steps of a z-slab (same grid spacing, same flow) on all host cores."""
+    import numpy as np
     from oracle import oracle as O
     O.build()
-    pr = O.Problem(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, y=case.y, mach=case.mach, re=case.re,
-                   visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
-                   force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+    sub = slab_planes(case)
+    w = np.ascontiguousarray(case.w0[:, :sub])
+    pr = _problem(O, case, sub)
     t0 = time.perf_counter()
-    O.step(pr, case.w0, 1, cfl=case.cfl, dt_every=case.dt_every)
+    w1, st, dt = O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every)
     one = time.perf_counter() - t0
-    steps = max(1, min(10, int(budget_s / max(one, 1e-3)) - 1))
+    steps = max(1, min(10, int(budget_s / max(one, 1e-3))))
     t0 = time.perf_counter()
-    O.step(pr, case.w0, steps, cfl=case.cfl, dt_every=case.dt_every)
+    O.step(pr, w1, steps, cfl=case.cfl, dt_every=case.dt_every, step0=st, dt0=dt)
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": case.points * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d RK3 step(s) of the full %dx%dx%d channel after 1 untimed step (%.1f s)"
-                      % (steps, case.nx, case.ny, case.nz, el),
-            "single_core": cpu_single_core()}
+    pts = case.nx * case.ny * sub
+    return {"value": pts * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK3 step(s) of a %d-plane z-slab (%dx%dx%d, same spacing) of the workload after 1 "
+                      "untimed step (%.1f s)" % (steps, sub, case.nx, case.ny, sub, el),
+            "single_core": cpu_single_core(case)}
 
 
 SINGLE_CORE_CODE = """
 import json, os, sys, time
 sys.path.insert(0, %r)
 import bench
+import numpy as np
 from oracle import oracle as O
-case = bench.workload()
-sub = 16
-w = case.w0[:, :sub].copy()
-pr = O.Problem(case.nx, case.ny, sub, case.lx, case.ly, case.lz * sub / case.nz, y=case.y, mach=case.mach,
-               re=case.re, visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
-               force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+case = bench.workload(%r)
+sub = 2
+w = np.ascontiguousarray(case.w0[:, :sub])
+pr = bench._problem(O, case, sub)
 t0 = time.perf_counter()
 O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every)
 el = time.perf_counter() - t0
-print(json.dumps({"value": case.nx * case.ny * sub / el, "seconds": el}))
+print(json.dumps({"value": case.nx * case.ny * sub / el, "seconds": el, "planes": sub}))
 """
 
 
-def cpu_single_core():
+def cpu_single_core(case):
     """The oracle on one host core (a fresh process with OMP_NUM_THREADS=1):
-    one RK3 step of a 16-plane z-slab of the workload."""
+    one RK3 step of a 2-plane z-slab of the workload."""
     env = dict(os.environ, OMP_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", SINGLE_CORE_CODE % ROOT], env=env, capture_output=True, text=True,
-                       timeout=600)
+    small = case.nx != 1024
+    r = subprocess.run([sys.executable, "-c", SINGLE_CORE_CODE % (ROOT, small)], env=env, capture_output=True,
+                       text=True, timeout=900)
     if r.returncode != 0:
         return {"error": r.stderr.strip().splitlines()[-1] if r.stderr.strip() else "failed"}
     v = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": v["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "1 RK3 step of a 16-plane z-slab of the channel (%.1f s)" % v["seconds"]}
+            "sample": "1 RK3 step of a %d-plane z-slab of the workload (%.1f s)" % (v["planes"], v["seconds"])}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import oracle as O
     import numpy as np
-    case = workload()
+    from oracle import oracle as O
+    case = workload(args.small)
     O.build()
-    # bounded sample: a z-slab of nz/8 planes of the channel (same spacing),
-    # so that one RK3 step of the oracle takes a second or so here
-    nz = case.nz
-    sub = max(4, nz // 8)
+    # bounded sample: a z-slab of the workload (same spacing, same flow) so
+    # that one RK3 step of the oracle takes a second or so here
+    sub = slab_planes(case)
     w = np.ascontiguousarray(case.w0[:, :sub])
-    lz = case.lz * sub / nz
-    pr = O.Problem(case.nx, case.ny, sub, case.lx, case.ly, lz, y=case.y, mach=case.mach, re=case.re,
-                   visc_exp=case.visc_exp, prandtl=case.prandtl, wall_y=case.wall_y, t_wall=case.t_wall,
-                   force=case.force, weno_order=case.weno_order, threshold=case.threshold)
+    pr = _problem(O, case, sub)
     st, dt = 0, 0.0
     for _ in range(args.warmup):
         w, st, dt = O.step(pr, w, 1, cfl=case.cfl, dt_every=case.dt_every, step0=st, dt0=dt)
@@ -242,7 +275,7 @@ def reference_arm(args):
     pts = case.nx * case.ny * sub
     value = pts * args.steps / el
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = "%d-plane z-slab (%dx%dx%d, same spacing) of the channel, one RK3 step per bench step" % (
+    sample = "%d-plane z-slab (%dx%dx%d, same spacing) of the workload, one RK3 step per bench step" % (
         sub, case.nx, case.ny, sub)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
@@ -251,6 +284,98 @@ def reference_arm(args):
            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value, "unit": UNIT},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+class Timer:
+    """Device time of a region on one stream (CUDA events), max over ranks."""
+
+    def __init__(self, torch, dist, world, stream):
+        self.torch, self.dist, self.world, self.stream = torch, dist, world, stream
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def run(self, fn):
+        torch = self.torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        self.barrier()
+        torch.cuda.synchronize()
+        e0.record(self.stream)
+        fn()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        self.barrier()
+        return self.max(e0.elapsed_time(e1))
+
+    def max(self, v):
+        if self.world > 1:
+            t = self.torch.tensor([v], device="cuda", dtype=self.torch.float64)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+            v = float(t.item())
+        return v
+
+
+def per_launch(prof, name):
+    ms, n = prof.get(name, (0.0, 0))
+    return ms / n if n else None
+
+
+def fp64_roofline(case, prof, steps, weno_frac, step_ms, fma_gflops):
+    """FP64 path: bound by the double-precision unit.  achieved = the
+    oracle-tallied flops of the dominant kernel class per launch / its mean
+    launch time (CUDA events on the solver's stream); the whole step's
+    tallied flops / step time beside it."""
+    n = case.points
+    flux_pp = {d: ALG_FLOPS_CENTRAL_INTERFACE * (nd + 1) / nd + ALG_FLOPS_FLUX_DIFFERENCE
+               for d, nd in (("flux_x", case.nx), ("flux_y", case.ny), ("flux_z", case.nz))}
+    alg = dict(ALG_FLOPS, **flux_pp)
+    # WENO corrections: flagged interfaces (weno_frac x 3N per stage) x the
+    # WENO flux minus the central flux it replaces
+    weno_pl = weno_frac * 3 * n * (ALG_FLOPS_WENO_INTERFACE - ALG_FLOPS_CENTRAL_INTERFACE) / 3
+    kernels = {k: v for k, v in prof.items() if v[1] and (k in alg or k == "weno")}
+    name = max(kernels, key=lambda k: kernels[k][0])
+    pl = per_launch(prof, name)
+    flops = (weno_pl if name == "weno" else alg[name] * n)
+    achieved = flops / (pl * 1e-3) / 1e9
+    per_kernel = {}
+    for k in kernels:
+        f = weno_pl if k == "weno" else alg[k] * n
+        per_kernel[k] = round(f / (per_launch(prof, k) * 1e-3) / 1e9 / FP64_PEAK_GFLOPS, 3)
+    step_flops = 3 * (sum(alg[k] for k in ("prims", "grad", "visc", "update", "flux_x", "flux_y", "flux_z"))
+                      + weno_frac * 3 * (ALG_FLOPS_WENO_INTERFACE - ALG_FLOPS_CENTRAL_INTERFACE)) * n
+    traffic = FP64_DRAM_BYTES.get(name)
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic * n if traffic else None, "kernel": name,
+            "per_launch_ms": pl,
+            "peak_source": "152 SM x 2 DFMA/clk x 2070 MHz (FP64 unit issue rate); FMA loop measured live: "
+                           "%.0f GFLOP/s" % fma_gflops,
+            "frac_of_fma_measured": achieved / fma_gflops,
+            "flops_source": "oracle operation tally (oracle/tally.py)",
+            "step_frac": step_flops / (step_ms * 1e-3) / 1e9 / FP64_PEAK_GFLOPS,
+            "frac_per_kernel": per_kernel}
+
+
+def mixed_roofline(case, prof, step_ms):
+    """Mixed path: HBM.  The method's 480 B per point-step against the
+    step time, and per kernel the algorithmic bytes of its launch."""
+    n = case.points
+    peak, src = hbm_peak_gbs()
+    kernels = {k: v for k, v in prof.items() if v[1] and k in MIXED_BYTES}
+    name = max(kernels, key=lambda k: kernels[k][0])
+    pl = per_launch(prof, name)
+    ach = MIXED_BYTES[name] * n / (pl * 1e-3) / 1e9
+    kfrac = {k: round(MIXED_BYTES[k] * n / (per_launch(prof, k) * 1e-3) / 1e9 / peak, 3) for k in kernels}
+    step_gbs = METHOD_BYTES_PER_POINT_STEP * n / (step_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": MIXED_DRAM_BYTES[name] * n if name in MIXED_DRAM_BYTES else None, "kernel": name,
+            "per_launch_ms": pl, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+            "step_frac": step_gbs / peak, "step_bytes_per_point": METHOD_BYTES_PER_POINT_STEP,
+            "frac_per_kernel": kfrac}
+
+
+def ms_per_step(prof, steps):
+    return {k: round(v[0] / steps, 4) for k, v in prof.items() if v[1]}
 
 
 def our_arm(args):
@@ -266,149 +391,112 @@ def our_arm(args):
     torch.cuda.set_device(local)
     from paper_2304_05494_gb300 import s2
 
-    case = workload()
+    case = workload(args.small)
     stream = torch.cuda.Stream()
+    T = Timer(torch, dist, world, stream)
+    fma = s2.s2_fma_rate("fp64", local)
+
+    # ---- headline: FP64 --------------------------------------------------
     sv = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local)
     sv.set_state(case.w0)
-    # warm-up (graph capture happens here)
-    sv.step(args.warmup)
+    sv.step(args.warmup)  # graph capture happens here
     sv.sync()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.4)
-    barrier()
-    torch.cuda.synchronize()
     launches0 = sv.stats()["launches"]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sv.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
+    t_max = T.run(lambda: sv.step(args.steps))
     clk = clocks.stop()
-    st = sv.stats()
-    launches = st["launches"] - launches0
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    launches = sv.stats()["launches"] - launches0
     value = case.points * args.steps * world / (t_max * 1e-3)
-
-    # per-kernel device times (CUDA events on the solver's stream)
     prof = sv.profile(args.profile_steps)
-    st2 = sv.stats()
-    weno_frac = st2["weno_frac"]
-    dom = max(((k, v) for k, v in prof.items() if k in ALG_FLOPS), key=lambda kv: kv[1][0])
-    name, (kms, kl) = dom
-    per_launch_ms = kms / max(kl, 1)
-    flops = ALG_FLOPS[name] * case.points
-    achieved = flops / (per_launch_ms * 1e-3) / 1e9
-    ops = FP64_OPS[name] * case.points / (per_launch_ms * 1e-3) / 1e9
-    traffic = DRAM_BYTES.get(name)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": traffic * case.points if traffic is not None else None, "kernel": name,
-                "peak_source": "FP64 pipe: 152 SM x 4 flop/clk x 2070 MHz (measured FMA loop: 1204 GFLOP/s)",
-                "fp64_pipe_frac": ops / FP64_PEAK_GOPS,
-                "per_launch_ms": per_launch_ms,
-                "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1]}}
+    weno_frac = sv.stats()["weno_frac"]
+    roofline = fp64_roofline(case, prof, args.profile_steps, weno_frac, t_max / args.steps, fma)
+    roofline["kernels_ms_per_step"] = ms_per_step(prof, args.profile_steps)
 
-    # mixed precision: same workload, single-precision flux arithmetic
-    mixed = None
-    if not args.no_mixed:
-        sm = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local, precision="mixed")
-        sm.set_state(case.w0)
-        sm.step(args.warmup)
-        sm.sync()
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        sm.step(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms_m = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms_m], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_m = float(t.item())
-        prof_m = sm.profile(args.profile_steps)
-        domm = max(((k, v) for k, v in prof_m.items() if k in MIXED_BYTES), key=lambda kv: kv[1][0])
-        mname, (mms, ml) = domm
-        per_launch = mms / max(ml, 1)
-        peak, src = hbm_peak_gbs()
-        ach = MIXED_BYTES[mname] * case.points / (per_launch * 1e-3) / 1e9
-        # every mixed kernel against the same HBM peak (algorithmic bytes)
-        kfrac = {k: MIXED_BYTES[k] * case.points / (v[0] / v[1] * 1e-3) / 1e9 / peak
-                 for k, v in prof_m.items() if k in MIXED_BYTES and v[1]}
-        # error of the mixed path against the FP64 path after 10 steps from w0
-        sm.set_state(case.w0)
-        sm.set_clock(0.0, 0, 0.0)
-        sm.step(10)
+    # end to end through the C ABI with host buffers: H2D of the step's
+    # input state, one step, D2H of the result, every step
+    pinned_in = torch.from_numpy(case.w0).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    win, wout = pinned_in.numpy(), pinned_out.numpy()
+    sv.set_state(win)
+    sv.step(1)
+    sv.get_state(wout)
+    T.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sv.set_state(win)
+        sv.step(1)
+        sv.get_state(wout)
+    t_e2e = T.max(time.perf_counter() - t0)
+    e2e = {"value": case.points * args.e2e_steps * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": case.w0.nbytes, "d2h_bytes_per_step": case.w0.nbytes}
+    finite = bool(np.isfinite(wout[:, ::64]).all())
+    del pinned_in, pinned_out, win, wout
+
+    # ---- mixed precision, same workload ----------------------------------
+    sm = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local, precision="mixed")
+    sm.set_state(case.w0)
+    sm.step(args.warmup)
+    sm.sync()
+    ms_m = T.run(lambda: sm.step(args.steps))
+    prof_m = sm.profile(args.profile_steps)
+    mroof = mixed_roofline(case, prof_m, ms_m / args.steps)
+    mroof["kernels_ms_per_step"] = ms_per_step(prof_m, args.profile_steps)
+    # error of the mixed path against the FP64 path after err_steps steps
+    # from the same state, per conserved field (field-normalised), and the
+    # relative difference of the total energy
+    err = energy_drift = None
+    if args.err_steps > 0:
+        for s in (sm, sv):
+            s.set_state(case.w0)
+            s.set_clock(0.0, 0, 0.0)
+            s.step(args.err_steps)
+        e_m, e_d = sm.stats()["energy"], sv.stats()["energy"]
         wm = sm.get_state()
-        sm.close()
-        with s2.Solver.from_case(case, stream=stream.cuda_stream, device=local) as sd:
-            sd.set_state(case.w0)
-            sd.step(10)
-            wd = sd.get_state()
-        scale = np.max(np.abs(wd), axis=(1, 2, 3))
-        err = (np.max(np.abs(wm - wd), axis=(1, 2, 3)) / scale).tolist()
-        mixed = {"value": case.points * args.steps * world / (ms_m * 1e-3), "unit": UNIT,
-                 "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state",
-                 "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "traffic": (MIXED_DRAM_BYTES[mname] * case.points if mname in MIXED_DRAM_BYTES
-                                          else None), "kernel": mname, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
-                              "per_launch_ms": per_launch, "hbm_frac_per_kernel": kfrac,
-                              "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_m.items() if v[1]}},
-                 "err_vs_fp64_after_10_steps": err}
+        wd = sv.get_state()
+        err = [float(np.max(np.abs(wm[f] - wd[f])) / np.max(np.abs(wd[f]))) for f in range(5)]
+        energy_drift = (e_m - e_d) / abs(e_d)
+        del wm, wd
+    sm.close()
+    sv.close()
+    mixed = {"value": case.points * args.steps * world / (ms_m * 1e-3), "unit": UNIT,
+             "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state", "roofline": mroof,
+             "err_vs_fp64": err, "energy_rel_diff_vs_fp64": energy_drift, "err_steps": args.err_steps}
 
-    # thermally perfect gas (Sec. 2: c_p(T) from a NASA-form polynomial):
-    # the same workload and initial flow (its primitive fields, converted
-    # with this gas's e(T) on the device), FP64 and mixed precision
-    tp = None
-    if not args.no_tp:
-        tp = {"gas": "synthetic NASA 9-coefficient form c_p/R = sum a_l T^l, a_-2..a_4 = %s "
-                     "(gamma 1.45 / 1.40 / 1.35 at T = 0.5 / 1 / 2)" % TP_GAS}
+    # ---- side legs on the 256 x 128 x 128 channel ------------------------
+    side = tp = None
+    if not args.no_side and not args.small:
+        side = {"workload": "compressible channel 256x128x128, Re_tau~220, same scheme"}
+        c2 = workload(True)
         for prec in ("fp64", "mixed"):
-            stp = s2.Solver.from_case(case, stream=stream.cuda_stream, device=local, precision=prec,
-                                      cp_coeffs=TP_GAS)
-            stp.set_primitives(case.prim0)
-            stp.step(args.warmup)
-            stp.sync()
-            barrier()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            stp.step(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            barrier()
-            ms_t = e0.elapsed_time(e1)
-            if world > 1:
-                t = torch.tensor([ms_t], device="cuda", dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                ms_t = float(t.item())
-            prof_t = stp.profile(args.profile_steps)
-            ok = stp.stats()["status"] == 0
-            stp.close()
-            tp[prec] = {"value": case.points * args.steps * world / (ms_t * 1e-3), "unit": UNIT,
-                        "ms_per_step": ms_t / args.steps, "status_ok": ok,
-                        "kernels_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof_t.items() if v[1]}}
+            s = s2.Solver.from_case(c2, stream=stream.cuda_stream, device=local, precision=prec)
+            s.set_state(c2.w0)
+            s.step(args.warmup)
+            s.sync()
+            ms = T.run(lambda: s.step(args.steps))
+            s.close()
+            side[prec] = {"value": c2.points * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps}
+        # thermally perfect gas (Sec. 2: c_p(T) from a NASA-form polynomial):
+        # the same flow, converted with this gas's e(T) on the device
+        tp = {"gas": "synthetic NASA 9-coefficient form, a_-2..a_4 = %s" % TP_GAS, "workload": "channel 256x128x128"}
+        for prec in ("fp64", "mixed"):
+            s = s2.Solver.from_case(c2, stream=stream.cuda_stream, device=local, precision=prec, cp_coeffs=TP_GAS)
+            s.set_primitives(c2.prim0)
+            s.step(args.warmup)
+            s.sync()
+            ms = T.run(lambda: s.step(args.steps))
+            ok = s.stats()["status"] == 0
+            s.close()
+            tp[prec] = {"value": c2.points * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                        "status_ok": ok}
 
-    # batched step latency: a short continuous-batching serving run (mixed
-    # precision, Poisson arrivals at 80 % of the measured capacity of a full
-    # batch, boxes of 32^3 .. 128^3, 50 .. 200 steps each)
+    # ---- serving: continuous batching at 80 % of capacity ----------------
     serving = None
     if args.serve_requests > 0 and world == 1:
         from paper_2304_05494_gb300 import serve
         cap = serve.capacity("mixed")
-        reqs = serve.make_requests(args.serve_requests, steps=(50, 200), precisions=("mixed",))
+        reqs = serve.make_requests(args.serve_requests, steps=(100, 1000), precisions=("mixed",))
         rate = 0.8 * cap / float(np.mean([r.points * r.steps for r in reqs]))
         serve.poisson_arrivals(reqs, rate)
         so = serve.Server(max_slots=64, steps_per_tick=10).run(reqs)
@@ -418,43 +506,24 @@ def our_arm(args):
                    "p99_step_latency_ms": so["p99_step_latency_ms"],
                    "p50_queue_s": so["p50_queue_s"], "p99_queue_s": so["p99_queue_s"],
                    "workload": "Taylor-Green or seeded decaying turbulence boxes {32,48,64,96,128}^3, "
-                               "M in [0.1, 0.8], Re in [400, 3200], 50-200 RK3 steps"}
-
-    # end to end through the C ABI with host buffers: H2D of the step's
-    # input state, one step, D2H of the result, every step
-    pinned_in = torch.from_numpy(case.w0).pin_memory()
-    pinned_out = torch.empty_like(pinned_in).pin_memory()
-    win = pinned_in.numpy()
-    wout = pinned_out.numpy()
-    sv.set_state(win)
-    sv.step(1)
-    sv.get_state(wout)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        sv.set_state(win)
-        sv.step(1)
-        sv.get_state(wout)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    nbytes = case.w0.nbytes
-    e2e = {"value": case.points * args.e2e_steps * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes}
-    finite = bool(np.isfinite(wout).all())
-    sv.close()
+                               "M in [0.1, 0.8], Re in [400, 3200], 100-1000 RK3 steps, Poisson arrivals"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
-               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "mixed": mixed,
-               "thermally_perfect": tp, "serving": serving, "weno_frac": weno_frac, "state_finite": finite}
+               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "weno_frac": weno_frac, "state_finite": finite, "channel256": side, "thermally_perfect": tp,
+               "serving": serving, "mixed": mixed}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(case)
+        # the mixed-precision headline figures again, last on the line
+        out["mixed_value"] = mixed["value"]
+        out["mixed_ms_per_step"] = mixed["ms_per_step"]
+        out["mixed_step_hbm_frac"] = mroof["step_frac"]
+        out["mixed_roofline_frac"] = mroof["frac"]
+        out["mixed_err_vs_fp64"] = err
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

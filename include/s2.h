@@ -259,6 +259,16 @@ int s2_profile(s2_solver *s, int n, double *ms, long long *launches);
 /* Name of a kernel class ("prims", "flux_y", ...); NULL if out of range. */
 const char *s2_profile_name(int kind);
 
+/* Measurement aid (the paper has no counterpart): the issue-limited
+ * fused multiply-add rate of the GPU, in GFLOP/s (2 flops per FMA), in
+ * double (precision = S2_FP64) or single precision (S2_MIXED), from a
+ * register-only loop of independent FMA chains on every SM for a few
+ * hundred milliseconds.  The double-precision path of this library is
+ * bound by that unit; this is the denominator of its roofline, taken at
+ * the clock the GPU runs at.  device: CUDA ordinal or -1 for the current
+ * one.  Allocates no memory; synchronises. */
+int s2_fma_rate(int precision, int device, double *gflops);
+
 /* Release everything; NULL is accepted. */
 void s2_destroy(s2_solver *s);
 
@@ -293,17 +303,23 @@ void s2_batch_destroy(s2_batch *b);
  * w: device pointer, the state in the ABI layout (5*nx*ny*nz doubles).
  * eta_y: device pointer to ny values of deta/dy, or NULL for uniform nodes
  * (ny/ly).  dt: device pointer; one double is written.  stream: a
- * cudaStream_t or NULL.  The call is asynchronous on that stream.
+ * cudaStream_t or NULL.  The call is asynchronous on that stream.  A point
+ * that s2_step would report as invalid (density or temperature not
+ * positive and finite, or a non-finite velocity) makes *dt = 0.
  *
  * Its only scratch is a fixed array of 65536 doubles (512 KiB) compiled
  * into the library, present on every GPU that loads it until the process
  * exits; nothing is allocated (no cudaMalloc, cudaFree or allocating
  * library call).  Grids above 65536 * 4096 = 268,435,456 points return
- * S2_ETOOBIG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current and caches it;
- * make that first call before any stream capture.  All calls on a device
- * share the array and every call rewrites the entries it reads, so nothing
- * needs clearing; calls that overlap on the GPU (different streams without
+ * S2_ETOOBIG (each extent is checked before it is multiplied).  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it with the
+ * identifier of the current context; make that first call before any
+ * stream capture.  A later call that finds another context current (after
+ * cudaDeviceReset, say) looks the address up again, so it too should not
+ * be the first call inside a capture.  All calls on a device share the
+ * array and every call rewrites the entries it reads, so nothing needs
+ * clearing; calls that overlap on the GPU (different streams without
  * ordering) race on it and must be serialised by the caller. */
 int s2_cfl_dt_noalloc(const s2_grid *grid, const s2_gas *gas, const double *w, const double *eta_y, double cfl,
                       double *dt, void *stream);

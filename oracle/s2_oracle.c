@@ -39,6 +39,27 @@
 #define NV 5
 #define GH 4 /* ghost width of the padded work arrays (WENO7 needs 4) */
 
+/* Operation tally: the counting build (oracle/tally.py) defines OR_SECTION
+ * to attribute the floating-point operations that follow a marker to one
+ * part of the method; the plain build compiles the markers away. */
+#ifndef OR_SECTION
+#define OR_SECTION(sec) ((void)0)
+#endif
+enum {
+  SEC_PRIMS,     /* primitive recovery, H and c */
+  SEC_SENSOR,    /* velocity gradients, divergence, shock sensor */
+  SEC_CENTRAL,   /* split-form central interface fluxes and the flux differences */
+  SEC_WENO,      /* characteristic WENO interface fluxes */
+  SEC_VISC_GRAD, /* the viscous terms' nine velocity gradients */
+  SEC_VISC,      /* the rest of the viscous and heat-flux terms */
+  SEC_FORCE,     /* channel forcing */
+  SEC_UPDATE,    /* RK3 update */
+  SEC_DT,        /* CFL time step */
+  SEC_PRIMS_HC,  /* H and c on interior and ghost points */
+  SEC_GHOST,     /* ghost values of the primitives, divergence and sensor */
+  SEC_OTHER
+};
+
 /* Central first derivative of order 2L (L = 1..4, the paper's orders
  * 2/4/6/8, Sec. 2): f' = sum_{l=1..L} a_l (f_{i+l} - f_{i-l}). */
 static const double A1_ORD[5][5] = {
@@ -274,6 +295,7 @@ static double T_of_e(const ws_t *s, double e) {
  * on interior and ghost faces. */
 static void fill_ghost_prims(ws_t *s) {
   const or_cfg *c = s->c;
+  OR_SECTION(SEC_GHOST);
   int nx = s->nx, ny = s->ny, nz = s->nz;
   double *fl[] = {s->rho, s->u, s->v, s->w, s->T, s->p};
   /* x faces (periodic) */
@@ -323,6 +345,7 @@ static void fill_ghost_prims(ws_t *s) {
 static void prims(ws_t *s, const double *w) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   size_t n = s->n;
+  OR_SECTION(SEC_PRIMS);
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -337,6 +360,7 @@ static void prims(ws_t *s, const double *w) {
       }
   fill_ghost_prims(s);
   /* H and c everywhere the primitives are defined (edges/corners stay 0) */
+  OR_SECTION(SEC_PRIMS_HC);
 #pragma omp parallel for schedule(static)
   for (int kk = 0; kk < s->pz; ++kk)
     for (int jj = 0; jj < s->py; ++jj)
@@ -409,6 +433,7 @@ static double d2(const ws_t *s, const double *f, int i, int j, int k, int dir) {
  * odd with an even y derivative). */
 static void sensor(ws_t *s) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
+  OR_SECTION(SEC_SENSOR);
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -424,6 +449,7 @@ static void sensor(ws_t *s) {
         s->sens[a] = sv > 0.0 ? sv : 0.0;
         s->div[a] = th;
       }
+  OR_SECTION(SEC_GHOST);
   double *fl[] = {s->sens, s->div};
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -785,9 +811,15 @@ static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags, int 
           }
           if (flags) flags[slot] = (unsigned char)fl;
         }
-        if (fl) weno_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
-        else central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+        if (fl) {
+          OR_SECTION(SEC_WENO);
+          weno_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+        } else {
+          OR_SECTION(SEC_CENTRAL);
+          central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+        }
       }
+      OR_SECTION(SEC_CENTRAL);
       for (int pos = 0; pos < n; ++pos) {
         int ii = dir == 0 ? pos : i, jj = dir == 1 ? pos : j, kk = dir == 2 ? pos : k;
         double sc = dir == 0 ? 1.0 / s->dx : (dir == 1 ? s->eta_y[jj] : 1.0 / s->dz);
@@ -817,8 +849,10 @@ static void viscous(ws_t *s, double *rhs) {
       for (int i = 0; i < nx; ++i) {
         const double *vel[3] = {s->u, s->v, s->w};
         double g[3][3], lap[3], gT[3], gth[3];
+        OR_SECTION(SEC_VISC_GRAD);
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) g[a][b] = d1(s, vel[a], i, j, k, b); /* d u_a / d x_b */
+        OR_SECTION(SEC_VISC);
         for (int a = 0; a < 3; ++a) lap[a] = d2(s, vel[a], i, j, k, 0) + d2(s, vel[a], i, j, k, 1) + d2(s, vel[a], i, j, k, 2);
         for (int b = 0; b < 3; ++b) { gT[b] = d1(s, s->T, i, j, k, b); gth[b] = d1(s, s->div, i, j, k, b); }
         double lapT = d2(s, s->T, i, j, k, 0) + d2(s, s->T, i, j, k, 1) + d2(s, s->T, i, j, k, 2);
@@ -869,6 +903,7 @@ static void viscous(ws_t *s, double *rhs) {
 static double forcing(ws_t *s, double *rhs) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   size_t n = s->n;
+  OR_SECTION(SEC_FORCE);
   double num = 0.0, den = 0.0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j) {
@@ -955,6 +990,7 @@ static double dt_ws(ws_t *s, const double *w, double cfl) {
   int nx = s->nx, ny = s->ny, nz = s->nz;
   const or_cfg *c = s->c;
   prims(s, w);
+  OR_SECTION(SEC_DT);
   double mx = 0.0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -1004,6 +1040,7 @@ int or_step(const or_cfg *c, double *w, int nsteps, double cfl, double dt_fixed,
     }
     for (int st = 0; st < 3; ++st) {
       rhs_ws(&s, w, R, NULL, NULL, NULL, OR_CONV | OR_VISC | OR_FORCE, NULL, 0);
+      OR_SECTION(SEC_UPDATE);
       for (size_t q = 0; q < tot; ++q) w[q] += dt * (RK_GAMMA[st] * R[q] + RK_RHO[st] * Rp[q]);
       double *t = Rp; Rp = R; R = t;
     }

@@ -21,7 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libs2.so")
 LIB_CHECKED = os.path.join(OUT_DIR, "libs2_checked.so")
-SOURCES = ["s2_solver.cu", "s2_flux.cu", "s2_visc.cu", "s2_noalloc.cu"]
+SOURCES = ["s2_solver.cu", "s2_flux.cu", "s2_visc.cu", "s2_noalloc.cu", "s2_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

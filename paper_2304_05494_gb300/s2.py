@@ -103,6 +103,8 @@ def _load():
     lib.s2_profile.restype = C.c_int
     lib.s2_profile_name.argtypes = [C.c_int]
     lib.s2_profile_name.restype = C.c_char_p
+    lib.s2_fma_rate.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+    lib.s2_fma_rate.restype = C.c_int
     lib.s2_cfl_dt_noalloc.argtypes = [C.POINTER(s2_grid), C.POINTER(s2_gas), P, P, C.c_double, P, P]
     lib.s2_cfl_dt_noalloc.restype = C.c_int
     lib.s2_batch_create.argtypes = [C.POINTER(P), C.c_int, P, C.POINTER(P)]
@@ -232,6 +234,13 @@ def s2_profile(h, n: int) -> dict:
     cnt = (C.c_longlong * S2_PROF_KINDS)()
     _check(_lib.s2_profile(h, int(n), ms, cnt), "s2_profile")
     return {s2_profile_name(k): (ms[k], cnt[k]) for k in range(S2_PROF_KINDS)}
+
+
+def s2_fma_rate(precision: str = "fp64", device: int = -1) -> float:
+    """Issue-limited FMA rate of the GPU in GFLOP/s (double or single precision)."""
+    g = C.c_double(0.0)
+    _check(_lib.s2_fma_rate(S2_FP64 if precision == "fp64" else S2_MIXED, int(device), C.byref(g)), "s2_fma_rate")
+    return g.value
 
 
 def s2_cfl_dt_noalloc(grid, gas, w, eta_y, cfl: float, dt, stream=None) -> int:
