@@ -29,7 +29,8 @@
  * Errors: every int-returning call returns S2_OK (0) or a negative code;
  * s2_strerror names it.  Handles are not thread-safe; each solver issues
  * all its work on one CUDA stream.  No call allocates device memory except
- * s2_create (which allocates everything up front).
+ * s2_create (which allocates everything up front) and s2_batch_create
+ * (its work-list tables).
  */
 #ifndef S2_H
 #define S2_H
@@ -275,18 +276,44 @@ void s2_destroy(s2_solver *s);
 /* Batched stepping, for many independent boxes (ensembles, serving).  A
  * batch groups count distinct solvers created on the same device;
  * s2_batch_step advances every member by n RK3 steps, each step one CUDA
- * graph launch in which the members' kernel sequences are independent
- * branches that the GPU runs concurrently, so that boxes too small to fill
- * the GPU alone (the paper finds ~2M points are needed, Sec. 4.1) fill it
- * together.  Members keep their own state, parameters, streams and clocks;
- * no buffer is shared, so a member's results are the same alone and in a
- * batch.  stream: the batch's cudaStream_t, or NULL for a private one.
- * s2_batch_create waits for the members' pending work.  s2_batch_step is
- * asynchronous on the batch stream; s2_batch_sync waits for it and returns
- * the first member error.  Do not step a member on its own while its batch
- * is in flight, and destroy the batch before any of its members. */
+ * graph launch, so that boxes too small to fill the GPU alone (the paper
+ * finds ~2M points are needed, Sec. 4.1) fill it together.
+ *
+ * Work-list mode (S2_BATCH_WORKLIST, the default of s2_batch_create):
+ * members that share their kernels (same precision, orders, WENO order,
+ * tile shapes, gas model and viscous / WENO / forcing / CFL switches) form
+ * a group, and each kernel of an RK stage is one launch for the whole
+ * group: a work list in device memory gives every CTA of the launch its
+ * box and its tile in that box, the box's parameters come from a table in
+ * device memory, and the persistent single-precision flux grids are
+ * shared out over the boxes by their tile counts.  A step costs the same
+ * ~40 launches for 1 box or 100.  Members of S2_BATCH_SOLO_POINTS points
+ * or more fill enough of the GPU on their own and keep their own launch
+ * sequence.  Groups and such members run as concurrent branches of the
+ * step graph.  Branch mode (S2_BATCH_BRANCHES): every member's own
+ * launch sequence is a concurrent branch.  Either way each box's
+ * arithmetic is exactly that of its solo run (results identical bit for
+ * bit), members keep their own state, parameters, streams and clocks, and
+ * no buffer is shared.
+ *
+ * stream: the batch's cudaStream_t, or NULL for a private one.  Creation
+ * waits for the members' pending work; in work-list mode it allocates the
+ * groups' tables (a few KB per member, through the first member's
+ * allocator callbacks if it has them), released by s2_batch_destroy.
+ * Members' parameters (s2_set_tiles, the clock's dt switch) are taken at
+ * creation.  s2_batch_step is asynchronous on the batch stream;
+ * s2_batch_sync waits for it and returns the first member error.  Do not
+ * step a member on its own while its batch is in flight, and destroy the
+ * batch before any of its members. */
+#define S2_BATCH_WORKLIST 0
+#define S2_BATCH_BRANCHES 1
+#define S2_BATCH_WORKLIST_ALL 2   /* work list for every member, whatever its size */
+#define S2_BATCH_SOLO_POINTS 262144 /* 64^3 */
 typedef struct s2_batch s2_batch;
 int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out);
+int s2_batch_create_ex(s2_solver *const *members, int count, void *stream, int mode, s2_batch **out);
+/* Kernel launches per batch step (all groups or branches); -1 for NULL. */
+long long s2_batch_launches(const s2_batch *b);
 int s2_batch_step(s2_batch *b, int n);
 int s2_batch_sync(s2_batch *b);
 void s2_batch_destroy(s2_batch *b);

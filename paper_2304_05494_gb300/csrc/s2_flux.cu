@@ -36,6 +36,8 @@
 // kernel (or k_apply when inviscid): deterministic, no atomics on the RHS.
 // Every kernel is instantiated for R = double (FP64 path) and R = float
 // (arithmetic of the mixed path).
+#include <string.h>
+
 #include "s2_internal.cuh"
 
 namespace s2 {
@@ -154,13 +156,13 @@ constexpr size_t flux_smem() {
   return Ly::BAR_BYTES + sizeof(R) * ((size_t)Ly::NBUF * NFLD * Ly::SFA + (size_t)NP * (Ly::L + NP) * Ly::W);
 }
 
-// CTAs walk the tiles of a direction (t = blockIdx.x, + gridDim.x, ...).
+// CTAs walk the tiles of a direction (t = block index, + grid extent, ...).
 // With NBUF staging buffers, the tensor memory accelerator fills the
 // buffers of the next NBUF - 1 tiles while tile t is computed, so the HBM
 // reads of later tiles overlap the arithmetic of the current one.
 template <int DIR, bool HASW, class R, int TV, int NP>
-__global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d,
-                                                      const TileGrid<DIR, TV, R> tg, int accumulate) {
+__device__ __forceinline__ void flux_body(const FluxMaps &maps, const Dev &__restrict__ d, const TileGrid<DIR, TV, R> &tg,
+                                          int accumulate, const Blk &B) {
   using Ly = FluxLayout<DIR, R, TV>;
   constexpr int L = Ly::L, W = Ly::W, LE = Ly::LE, SF = Ly::SF, SFA = Ly::SFA, NBUF = Ly::NBUF, PPT = Ly::PPT;
   constexpr int LP = L / PPT;          // positions per pass of the CTA's threads
@@ -197,18 +199,18 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
     for (int f = 0; f < NFLD; ++f) tma_load_3d(Sbuf + (buf * NFLD + f) * SFA, &maps.m[f], bx, by, bz, &bar[buf]);
   };
   // tile of this CTA's iteration it, its buffer and that buffer's use count
-  const int G = gridDim.x;
+  const int G = (int)B.nx;
   if (tid == 0) {
     for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     for (int j = 0; j < NBUF - 1; ++j)
-      if ((int)blockIdx.x + j * G < ntiles) issue(blockIdx.x + j * G, j);
+      if ((int)B.x + j * G < ntiles) issue((int)B.x + j * G, j);
   }
   __syncthreads();
 
   int it = 0;
-  for (int t = blockIdx.x; t < ntiles; t += G, ++it) {
+  for (int t = (int)B.x; t < ntiles; t += G, ++it) {
     const int buf = it % NBUF;
     // the buffer of tile it + NBUF - 1 was released by the barrier that
     // ended the previous tile
@@ -369,6 +371,22 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ Fl
   }
 }
 
+template <int DIR, bool HASW, class R, int TV, int NP>
+__global__ void __launch_bounds__(NTHREADS, 4) k_flux(const __grid_constant__ FluxMaps maps, Dev d,
+                                                      const TileGrid<DIR, TV, R> tg, int accumulate) {
+  flux_body<DIR, HASW, R, TV, NP>(maps, d, tg, accumulate, grid_blk());
+}
+
+// Batched: box b's tiles with its tensor maps maps[b] (device memory,
+// 64-byte aligned) and tile grid tgs[b].
+template <int DIR, bool HASW, class R, int TV, int NP>
+__global__ void __launch_bounds__(NTHREADS, 4) kb_flux(BatchArgs ba, const FluxMaps *maps,
+                                                       const TileGrid<DIR, TV, R> *tgs, int accumulate) {
+  S2_BATCH_ENTER(ba, sd, B, b);
+  const TileGrid<DIR, TV, R> tg = tgs[b];
+  flux_body<DIR, HASW, R, TV, NP>(maps[b], sd, tg, accumulate, B);
+}
+
 // ------------------------------------------------------------------ WENO
 // Reconstruction at i+1/2 from 2r-1 values g[0..2r-2] centred on g[r-1]:
 // Jiang & Shu (r=3), Balsara & Shu (r=4), alpha_k = d_k/(eps+beta_k)^2.
@@ -469,7 +487,7 @@ __device__ __forceinline__ R weno_rec(const R *g, R eps) {
 // dissipation is the largest |eigenvalue| (u_n - c, u_n, u_n + c) over the
 // stencil points.  The result goes back with the right eigenvectors.
 template <int DIR, int WR, class R>
-__global__ void __launch_bounds__(WENO_NT) k_weno(Dev d) {
+__device__ __forceinline__ void weno_body(const Dev &__restrict__ d, const Blk &B) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int NP = 2 * WR;  // stencil points s-WR+1 .. s+WR
   const View<R> V = view<R>(d);
@@ -477,7 +495,7 @@ __global__ void __launch_bounds__(WENO_NT) k_weno(Dev d) {
   const unsigned cnt = d.scal->nlist[DIR];
   const R *vel[3] = {V.u, V.v, V.ww};
   const R bq = K.gamma - R(1);
-  for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < cnt; e0 += gridDim.x * blockDim.x) {
+  for (unsigned e0 = B.x * blockDim.x + threadIdx.x; e0 < cnt; e0 += B.nx * blockDim.x) {
     if (!S2_OK_IDX(d, e0, d.nslot[DIR])) break;
     const long long slot = d.wlist[DIR][e0];
     int i = 0, j = 0, k = 0, s;
@@ -629,6 +647,17 @@ __global__ void __launch_bounds__(WENO_NT) k_weno(Dev d) {
   }
 }
 
+template <int DIR, int WR, class R>
+__global__ void __launch_bounds__(WENO_NT) k_weno(Dev d) {
+  weno_body<DIR, WR, R>(d, grid_blk());
+}
+
+template <int DIR, int WR, class R>
+__global__ void __launch_bounds__(WENO_NT) kb_weno(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  weno_body<DIR, WR, R>(sd, B);
+}
+
 // Single precision (bound by memory traffic): a persistent grid, as many
 // CTAs as fit on the device at once, each prefetching its next two tiles.
 // Double precision (bound by the double-precision unit): one tile per CTA,
@@ -686,8 +715,11 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
 
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t set_attr_one() {
-  return cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)flux_smem<DIR, HASW, R, TV, NP>());
+  cudaError_t e = cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)flux_smem<DIR, HASW, R, TV, NP>());
+  cudaError_t e2 = cudaFuncSetAttribute(kb_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)flux_smem<DIR, HASW, R, TV, NP>());
+  return e != cudaSuccess ? e : e2;
 }
 
 template <int DIR, class R>
@@ -816,6 +848,130 @@ cudaError_t flux_make_maps(const Dev &d, FluxMaps (&maps)[3][2]) {
 
 cudaError_t launch_weno(const Dev &d, int dir, cudaStream_t st) {
   return d.mixed ? weno_dispatch<float>(d, dir, st) : weno_dispatch<double>(d, dir, st);
+}
+
+// ------------------------------------------------------- batched launches
+// The flux kernel instantiation of a Dev (precision, WENO or not, tile
+// variant, central order): F::run<DIR, HASW, R, TV, NP>().
+namespace {
+
+template <class F, int DIR, bool HASW, class R, int TV>
+cudaError_t sel_np(const Dev &d, F &f) {
+  switch (d.npc) {
+    case 1: return f.template run<DIR, HASW, R, TV, 1>();
+    case 2: return f.template run<DIR, HASW, R, TV, 2>();
+    case 3: return f.template run<DIR, HASW, R, TV, 3>();
+    case 4: return f.template run<DIR, HASW, R, TV, 4>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class F, int DIR, class R>
+cudaError_t sel_w(const Dev &d, F &f) {
+  if (d.weno > 0) return d.tile[DIR] ? sel_np<F, DIR, true, R, 1>(d, f) : sel_np<F, DIR, true, R, 0>(d, f);
+  return d.tile[DIR] ? sel_np<F, DIR, false, R, 1>(d, f) : sel_np<F, DIR, false, R, 0>(d, f);
+}
+
+template <class F, class R>
+cudaError_t sel_dir(const Dev &d, int dir, F &f) {
+  switch (dir) {
+    case 0: return sel_w<F, 0, R>(d, f);
+    case 1: return sel_w<F, 1, R>(d, f);
+    case 2: return sel_w<F, 2, R>(d, f);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class F>
+cudaError_t flux_select(const Dev &d, int dir, F &f) {
+  return d.mixed ? sel_dir<F, float>(d, dir, f) : sel_dir<F, double>(d, dir, f);
+}
+
+struct FluxPlan {
+  const Dev &d;
+  FluxBoxPlan &out;
+  template <int DIR, bool HASW, class R, int TV, int NP>
+  cudaError_t run() {
+    static int per_sm = 0;  // resident CTAs per multiprocessor of the batched kernel
+    if (per_sm == 0) {
+      int b = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flux<DIR, HASW, R, TV, NP>, NTHREADS,
+                                                        flux_smem<DIR, HASW, R, TV, NP>()) != cudaSuccess ||
+          b < 1)
+        b = 1;
+      per_sm = b;
+    }
+    const TileGrid<DIR, TV, R> tg(d);
+    static_assert(sizeof(tg) <= sizeof(out.tg), "tile grid record");
+    memcpy(out.tg, &tg, sizeof(tg));
+    out.tg_size = (int)sizeof(tg);
+    out.tiles = tg.count();
+    out.per_sm = per_sm;
+    out.persistent = sizeof(R) == 4;
+    return cudaSuccess;
+  }
+};
+
+struct FluxBatchLaunch {
+  const BatchArgs &ba;
+  unsigned total;
+  const FluxMaps *maps;
+  const void *tgs;
+  int accumulate;
+  cudaStream_t st;
+  template <int DIR, bool HASW, class R, int TV, int NP>
+  cudaError_t run() {
+    kb_flux<DIR, HASW, R, TV, NP><<<total, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(
+        ba, maps, (const TileGrid<DIR, TV, R> *)tgs, accumulate);
+    return cudaGetLastError();
+  }
+};
+
+template <int DIR, class R>
+cudaError_t weno_batch_wr(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
+  switch ((d0.weno + 1) / 2) {
+    case 1: kb_weno<DIR, 1, R><<<total, WENO_NT, 0, st>>>(ba); break;
+    case 2: kb_weno<DIR, 2, R><<<total, WENO_NT, 0, st>>>(ba); break;
+    case 3: kb_weno<DIR, 3, R><<<total, WENO_NT, 0, st>>>(ba); break;
+    case 4: kb_weno<DIR, 4, R><<<total, WENO_NT, 0, st>>>(ba); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t weno_batch_dir(const Dev &d0, const BatchArgs &ba, unsigned total, int dir, cudaStream_t st) {
+  switch (dir) {
+    case 0: return weno_batch_wr<0, R>(d0, ba, total, st);
+    case 1: return weno_batch_wr<1, R>(d0, ba, total, st);
+    case 2: return weno_batch_wr<2, R>(d0, ba, total, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t flux_batch_plan(const Dev &d, int dir, FluxBoxPlan *out) {
+  FluxPlan f{d, *out};
+  return flux_select(d, dir, f);
+}
+
+unsigned weno_batch_blocks(const Dev &d, int dir) {
+  // as the single-box launch: enough 64-thread CTAs for every slot, at
+  // most 16 per multiprocessor (the list length is known on the device only)
+  long long need = (d.nslot[dir] + WENO_NT - 1) / WENO_NT;
+  long long cap = 16LL * d.nsm;
+  return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total, const FluxMaps *maps,
+                              const void *tgs, int dir, int accumulate, cudaStream_t st) {
+  FluxBatchLaunch f{ba, total, maps, tgs, accumulate, st};
+  return flux_select(d0, dir, f);
+}
+
+cudaError_t launch_weno_batch(const Dev &d0, const BatchArgs &ba, unsigned total, int dir, cudaStream_t st) {
+  return d0.mixed ? weno_batch_dir<float>(d0, ba, total, dir, st) : weno_batch_dir<double>(d0, ba, total, dir, st);
 }
 
 }  // namespace s2

@@ -139,6 +139,80 @@ struct Dev {
   long long nslot[3];
 };
 
+// Block coordinates of a kernel body.  A launch for one box uses the CUDA
+// grid's own (grid_blk); a batched launch, whose CTAs work on many boxes,
+// gives each CTA its box-local coordinates (batch_enter), so the same body
+// computes the same tiles either way.
+struct Blk {
+  unsigned x, y, z;     // block index
+  unsigned nx, ny, nz;  // grid extent
+};
+
+__device__ __forceinline__ Blk grid_blk() {
+  return Blk{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+
+// Batched launches (one launch for all boxes of a batch group): CTAs
+// start .. start + gx gy gz - 1 of the launch form box b's own grid.  The
+// table holds nbox + 1 entries; the last start is the launch's CTA count.
+struct BoxGrid {
+  unsigned start, gx, gy, gz;
+};
+
+struct BatchArgs {
+  const Dev *dev;       // [nbox] parameters of the boxes (device memory)
+  const BoxGrid *grid;  // [nbox + 1] this launch's work list
+  int nbox;
+};
+
+// The box of this CTA (binary search of the work list) and its box-local
+// block coordinates.
+__device__ __forceinline__ int batch_locate(const BatchArgs &ba, Blk &B) {
+  __shared__ int sbox;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = ba.nbox - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ba.grid[mid].start <= blockIdx.x) lo = mid;
+      else hi = mid - 1;
+    }
+    sbox = lo;
+  }
+  __syncthreads();
+  const int b = sbox;
+  const BoxGrid g = ba.grid[b];
+  unsigned l = blockIdx.x - g.start;
+  B.nx = g.gx;
+  B.ny = g.gy;
+  B.nz = g.gz;
+  B.x = l % g.gx;
+  l /= g.gx;
+  B.y = l % g.gy;
+  B.z = l / g.gy;
+  return b;
+}
+
+// The same, and the box's parameters copied to shared memory (sd).
+__device__ __forceinline__ int batch_enter(const BatchArgs &ba, Dev &sd, Blk &B) {
+  const int b = batch_locate(ba, B);
+  static_assert(sizeof(Dev) % 8 == 0, "Dev is copied in 8-byte words");
+  const unsigned long long *src = (const unsigned long long *)(ba.dev + b);
+  unsigned long long *dst = (unsigned long long *)&sd;
+  for (int i = threadIdx.x; i < (int)(sizeof(Dev) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return b;
+}
+
+// Opening of a batched kernel: the CTA's box (int BOX), its block
+// coordinates (Blk BL) and its parameters (const Dev &D, a shared-memory
+// copy of the table entry).
+#define S2_BATCH_ENTER(BA, D, BL, BOX)        \
+  __shared__ Dev D##_s;                       \
+  Blk BL;                                     \
+  const int BOX = batch_enter(BA, D##_s, BL); \
+  const Dev &D = D##_s;                       \
+  (void)BOX
+
 // Typed views of the fields of a Dev in the arithmetic type R.
 template <class R>
 struct View {
@@ -517,6 +591,27 @@ int visc_force_partials(const Dev &d);
 long long z_pass_blocks(const Dev &d);
 cudaError_t launch_apply(const Dev &d, cudaStream_t st);
 cudaError_t flux_set_attributes();
+
+// Batched launches (one launch for every box of a batch group; the boxes
+// share the kernel instantiation of d0).  Planning, per box and direction:
+// the flux kernel's tile count, its resident CTAs per multiprocessor, and
+// its tile-grid record (tg_size bytes, stored per box in a device array
+// that the launch reads); the WENO kernel's CTA count.
+struct FluxBoxPlan {
+  unsigned char tg[64];
+  int tg_size, tiles, per_sm;
+  bool persistent;  // single precision: CTAs walk several tiles
+};
+cudaError_t flux_batch_plan(const Dev &d, int dir, FluxBoxPlan *out);
+unsigned weno_batch_blocks(const Dev &d, int dir);
+cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total, const FluxMaps *maps,
+                              const void *tgs, int dir, int accumulate, cudaStream_t st);
+cudaError_t launch_weno_batch(const Dev &d0, const BatchArgs &ba, unsigned total, int dir, cudaStream_t st);
+// z-marching passes of the mixed path: grid of one box (x, y, z blocks)
+void z_pass_grid(const Dev &d, unsigned g[3]);
+cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
+cudaError_t launch_visc_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
+cudaError_t launch_apply_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
 
 // Gas constants (R, c_v, c_p, viscosity law) of a Dev from s2_gas.
 void set_gas(Dev &d, const s2_gas *gas);

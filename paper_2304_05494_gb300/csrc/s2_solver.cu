@@ -134,7 +134,7 @@ __global__ void k_metric(const double *yn, int ny, double ly, int wall, MetricCo
   dvy[j] = d1;
 }
 
-__device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_dt) {
+__device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_dt, unsigned bx) {
   if (want_dt) {
     __shared__ double red[NT / 32];
     double m = warp_max(sr);
@@ -143,7 +143,7 @@ __device__ __forceinline__ void dt_block_max(const Dev &d, double sr, int want_d
     if (threadIdx.x < 32) {
       double s = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
       s = warp_max(s);
-      if (threadIdx.x == 0 && S2_OK_IDX(d, blockIdx.x, d.nparts)) d.part[blockIdx.x] = s;
+      if (threadIdx.x == 0 && S2_OK_IDX(d, bx, d.nparts)) d.part[bx] = s;
     }
   }
 }
@@ -166,8 +166,8 @@ __device__ __forceinline__ int block_want_dt(const Dev &d, int stage0) {
 // TP: thermally perfect gas (a separate instantiation keeps the
 // calorically perfect kernel free of the Newton iteration's code).
 template <bool TP>
-__global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void prims_body(const Dev &__restrict__ d, const Blk &B, int stage0) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   const View<double> V = view<double>(d);
   const int want_dt = block_want_dt(d, stage0);
   double sr = 0.0;
@@ -213,7 +213,18 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
       atomicOr(&d.scal->status, ERR_NONFINITE);
     if (want_dt) sr = spectral_radius<TP>(d, rho, u, v, ww, T, mu, d.eta_y[j]);
   }
-  dt_block_max(d, sr, want_dt);
+  dt_block_max(d, sr, want_dt, B.x);
+}
+
+template <bool TP>
+__global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
+  prims_body<TP>(d, grid_blk(), stage0);
+}
+
+template <bool TP>
+__global__ void __launch_bounds__(NT) kb_prims(BatchArgs ba, int stage0) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  prims_body<TP>(sd, B, stage0);
 }
 
 // Mixed path: the internal energy per volume rho e = E - rho |u|^2 / 2 is
@@ -223,8 +234,8 @@ __global__ void __launch_bounds__(NT) k_prims(Dev d, int stage0) {
 // 2^-24 (1 + KE / (rho e)), KE/(rho e) = gamma (gamma-1) M^2 / 2.  Everything
 // else, and everything stored, is single precision; the one double
 // operation per point leaves the kernel bound by memory traffic.
-__global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void prims_mixed_body(const Dev &__restrict__ d, const Blk &B, int stage0) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   const View<float> V = view<float>(d);
   const int want_dt = block_want_dt(d, stage0);
   const Consts<float> &K = d.kf;
@@ -283,12 +294,19 @@ __global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) {
       sr = srf;
     }
   }
-  dt_block_max(d, sr, want_dt);
+  dt_block_max(d, sr, want_dt, B.x);
+}
+
+__global__ void __launch_bounds__(NT) k_prims_mixed(Dev d, int stage0) { prims_mixed_body(d, grid_blk(), stage0); }
+
+__global__ void __launch_bounds__(NT) kb_prims_mixed(BatchArgs ba, int stage0) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  prims_mixed_body(sd, B, stage0);
 }
 
 // dt = cfl / max(spectral radius) over the partials of k_prims, at the
 // steps where it is due (no-op otherwise).
-__global__ void k_dt_final(Dev d, int nparts) {
+__device__ __forceinline__ void dt_final_body(const Dev &__restrict__ d, int nparts) {
   if (!dt_due(d)) return;
   double m = 0.0;
   if (!S2_OK_IDX(d, nparts - 1, d.nparts)) nparts = 0;
@@ -305,6 +323,14 @@ __global__ void k_dt_final(Dev d, int nparts) {
       d.scal->dt = d.cfl / s;
     }
   }
+}
+
+__global__ void k_dt_final(Dev d, int nparts) { dt_final_body(d, nparts); }
+
+// one CTA per box; nparts[b]: box b's CFL partials
+__global__ void __launch_bounds__(NT) kb_dt_final(BatchArgs ba, const int *nparts) {
+  S2_BATCH_ENTER(ba, sd, B, b);
+  dt_final_body(sd, nparts[b]);
 }
 
 // ----------------------------------------------------------------- ghosts
@@ -353,9 +379,9 @@ __device__ __forceinline__ bool ghost_map(const Dev &d, long long t, int &di, in
 // node and its ghost: u -> -u, T -> 2 T_w - T, p -> p, rho = p/(R T), H =
 // h(T) + |u|^2/2.
 template <class R>
-__global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
+__device__ __forceinline__ void ghost_prim_body(const Dev &__restrict__ d, const Blk &B) {
   long long total = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
-  long long t = (long long)blockIdx.x * NT + threadIdx.x;
+  long long t = (long long)B.x * NT + threadIdx.x;
   if (t >= total) return;
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
@@ -390,13 +416,24 @@ __global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(NT) k_ghost_prim(Dev d) {
+  ghost_prim_body<R>(d, grid_blk());
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) kb_ghost_prim(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  ghost_prim_body<R>(sd, B);
+}
+
 // Face ghosts of div u and of the sensor.  At a wall the sensor is
 // mirrored and the divergence of the mirrored velocity field is
 // -u_x + v_y - w_z at the mirror node.
 template <class R>
-__global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
+__device__ __forceinline__ void ghost_aux_body(const Dev &__restrict__ d, const Blk &B) {
   long long total = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
-  long long t = (long long)blockIdx.x * NT + threadIdx.x;
+  long long t = (long long)B.x * NT + threadIdx.x;
   if (t >= total) return;
   const View<R> V = view<R>(d);
   int di, dj, dk, si, sj, sk;
@@ -419,19 +456,30 @@ __global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(NT) k_ghost_aux(Dev d) {
+  ghost_aux_body<R>(d, grid_blk());
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) kb_ghost_aux(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  ghost_aux_body<R>(sd, B);
+}
+
 // ---------------------------------------------------------------- forcing
 // force_rhs_1: partial sums of R_rhou dV (dV ~ 1/eta_y), deterministic.
 // One warp per x-row (fixed j, k): the row is summed in the path's
 // precision and weighted by dy/deta once, so the loop carries no index
 // division.
 template <class R>
-__global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
+__device__ __forceinline__ void force_partial_body(const Dev &__restrict__ d, const Blk &B) {
   const View<R> V = view<R>(d);
   const int lane = threadIdx.x & 31;
   const long long rows = (long long)d.ny * d.nz;
   double s = 0.0;
-  for (long long r = (long long)blockIdx.x * (NT / 32) + (threadIdx.x >> 5); r < rows;
-       r += (long long)gridDim.x * (NT / 32)) {
+  for (long long r = (long long)B.x * (NT / 32) + (threadIdx.x >> 5); r < rows;
+       r += (long long)B.nx * (NT / 32)) {
     const R *row = V.fl + d.n + r * d.nx;
     R sr = 0;
     for (int i = lane; i < d.nx; i += 32) sr += row[i];
@@ -440,10 +488,21 @@ __global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
   }
   double v[1] = {s};
   block_sum<1>(v);
-  if (threadIdx.x == 0 && S2_OK_IDX(d, blockIdx.x, d.nparts)) d.part[blockIdx.x] = v[0];
+  if (threadIdx.x == 0 && S2_OK_IDX(d, B.x, d.nparts)) d.part[B.x] = v[0];
 }
 
-__global__ void k_force_final(Dev d, int nparts) {
+template <class R>
+__global__ void __launch_bounds__(NT) k_force_partial(Dev d) {
+  force_partial_body<R>(d, grid_blk());
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) kb_force_partial(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  force_partial_body<R>(sd, B);
+}
+
+__device__ __forceinline__ void force_final_body(const Dev &__restrict__ d, int nparts) {
   double s = 0.0;
   if (!S2_OK_IDX(d, nparts - 1, d.nparts)) nparts = 0;
   for (int b = threadIdx.x; b < nparts; b += NT) s += d.part[b];
@@ -452,12 +511,30 @@ __global__ void k_force_final(Dev d, int nparts) {
   if (threadIdx.x == 0) d.scal->force = -v[0] * d.vol_inv;
 }
 
+__global__ void k_force_final(Dev d, int nparts) { force_final_body(d, nparts); }
+
+// one CTA per box; nparts[b]: box b's forcing partials
+__global__ void __launch_bounds__(NT) kb_force_final(BatchArgs ba, const int *nparts) {
+  S2_BATCH_ENTER(ba, sd, B, b);
+  force_final_body(sd, nparts[b]);
+}
+
+// The per-RHS counters of the hybrid scheme (flagged interfaces and the
+// three list lengths), zeroed for every box of a batch in one launch.
+__global__ void __launch_bounds__(NT) kb_reset_counts(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  if (threadIdx.x == 0) {
+    sd.scal->wcount = 0;
+    for (int a = 0; a < 4; ++a) sd.scal->nlist[a] = 0;
+  }
+}
+
 // ----------------------------------------------------------------- update
 // w <- w + dt gamma_k R + fln ; fln <- dt rho_{k+1} R, with R = fl + the
 // forcing (f on rho u, f u on rho E).  Stage 0 reads no fln; the last
 // stage writes none and advances the clock.
-__global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int stage) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void update_body(const Dev &__restrict__ d, const Blk &B, double gk, double rk1, int stage) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   const View<double> V = view<double>(d);
   const double dt = d.scal->dt;
   if (q < d.n) {
@@ -497,11 +574,20 @@ __global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int
   }
 }
 
+__global__ void __launch_bounds__(NT) k_update(Dev d, double gk, double rk1, int stage) {
+  update_body(d, grid_blk(), gk, rk1, stage);
+}
+
+__global__ void __launch_bounds__(NT) kb_update(BatchArgs ba, double gk, double rk1, int stage) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  update_body(sd, B, gk, rk1, stage);
+}
+
 // Mixed path: the increment dt gamma_k R + fln is formed in single
 // precision (R and the register are single precision) and accumulated
 // into the double-precision state.
-__global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk1, int stage) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void update_mixed_body(const Dev &__restrict__ d, const Blk &B, double gk, double rk1, int stage) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   const View<float> V = view<float>(d);
   // dt gamma_k, dt rho_{k+1} and the forcing in single precision, once per
   // CTA: the per-point path then needs the double-precision unit only for
@@ -547,6 +633,15 @@ __global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk
     d.scal->t += dt;
     d.scal->nstep += 1;
   }
+}
+
+__global__ void __launch_bounds__(NT) k_update_mixed(Dev d, double gk, double rk1, int stage) {
+  update_mixed_body(d, grid_blk(), gk, rk1, stage);
+}
+
+__global__ void __launch_bounds__(NT) kb_update_mixed(BatchArgs ba, double gk, double rk1, int stage) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  update_mixed_body(sd, B, gk, rk1, stage);
 }
 
 // Primitive fields prim[v][k][j][i] = (rho, u, v, w, T) -> conserved
@@ -1558,21 +1653,268 @@ const char *s2_profile_name(int kind) {
 }  // extern "C"
 
 // ======================================================================
-// Batched stepping: one graph whose branches are the members' steps
+// Batched stepping
 // ======================================================================
+// Work-list mode (default): members whose kernels are the same
+// instantiations (precision, orders, WENO order, tile shapes, gas model,
+// and the viscous / WENO / forcing / CFL switches) form a group, and every
+// kernel of a stage is ONE launch over the whole group: a table in device
+// memory lists, per box, the box's parameters and the CTAs of the launch
+// that work on it (BoxGrid); each CTA finds its box, copies the box's
+// parameters to shared memory and runs the same kernel body as a solo
+// launch on its box-local tile.  Persistent single-precision flux grids
+// are shared out over the boxes in proportion to their tiles.  Groups are
+// concurrent branches of the batch's step graph.  Branch mode: the
+// members' own step sequences as concurrent branches.
+enum BatchClass {
+  BC_PRIMS,  // one thread per interior point (prims, update, WENO apply)
+  BC_GHOST,  // one thread per face-ghost point
+  BC_GRAD,
+  BC_VISC,
+  BC_FLUX0,
+  BC_FLUX1,
+  BC_FLUX2,
+  BC_WENO0,
+  BC_WENO1,
+  BC_WENO2,
+  BC_FORCE,  // grid-stride forcing partials (NRED CTAs per box)
+  BC_ONE,    // one CTA per box
+  BC_COUNT
+};
+
+struct BatchGroup {
+  std::vector<s2_solver *> members;
+  cudaStream_t stream;  // the first member's: this group's branch of the step graph
+  void *mem;            // the device tables, one block
+  Dev *dev;             // [n] parameters of the boxes
+  BoxGrid *grid[BC_COUNT];
+  unsigned total[BC_COUNT];
+  int *nparts_dt, *nparts_force;  // [n]
+  FluxMaps *maps[3];              // [n] tensor maps of the group's tile variant
+  void *tgs[3];                   // [n] flux tile-grid records
+  long long launches;             // kernels per step
+};
+
 struct s2_batch {
   std::vector<s2_solver *> members;
   cudaStream_t stream;
   bool own_stream;
   int device;
+  int mode;
   cudaGraphExec_t graph;
   bool ready;
   long long launches_per_step;
-  std::vector<long long> member_launches;  // kernels per step of each member
-  std::vector<cudaEvent_t> events;         // fork + one join per member
+  std::vector<long long> member_launches;  // kernels per step that work on each member
+  std::vector<cudaEvent_t> events;         // fork + one join per branch
+  std::vector<BatchGroup> groups;
+  std::vector<s2_solver *> solo;           // work-list mode: members large enough to run their own launches
 };
 
 namespace {
+
+bool same_kernels(const Dev &a, const Dev &b) {
+  return a.mixed == b.mixed && a.npc == b.npc && a.npv == b.npv && a.weno == b.weno && a.kd.tp == b.kd.tp &&
+         a.tile[0] == b.tile[0] && a.tile[1] == b.tile[1] && a.tile[2] == b.tile[2] && a.viscous == b.viscous &&
+         a.force == b.force && (a.cfl > 0.0) == (b.cfl > 0.0);
+}
+
+void *batch_alloc(s2_solver *s, size_t bytes) {
+  void *p = nullptr;
+  if (s->dev.alloc) return s->dev.alloc(bytes, s->dev.ctx);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void batch_free(s2_solver *s, void *p) {
+  if (!p) return;
+  if (s->dev.free) s->dev.free(p, s->dev.ctx);
+  else cudaFree(p);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// The group's work lists and tables, built on the host and copied once.
+int group_setup(BatchGroup &g) {
+  const int n = (int)g.members.size();
+  const Dev &d0 = g.members[0]->d;
+  std::vector<Dev> devs(n);
+  for (int b = 0; b < n; ++b) devs[b] = g.members[b]->d;
+  std::vector<std::vector<BoxGrid>> grids(BC_COUNT, std::vector<BoxGrid>(n + 1));
+  std::vector<int> ndt(n), nforce(n);
+  FluxBoxPlan fp[3];
+  std::vector<FluxBoxPlan> plans(3 * (size_t)n);
+  long long tiles_sum[3] = {0, 0, 0}, slots_sum[3] = {0, 0, 0};
+  for (int b = 0; b < n; ++b)
+    for (int dir = 0; dir < 3; ++dir) {
+      if (flux_batch_plan(devs[b], dir, &plans[3 * b + dir]) != cudaSuccess) return S2_ECUDA;
+      tiles_sum[dir] += plans[3 * b + dir].tiles;
+      slots_sum[dir] += devs[b].nslot[dir];
+    }
+  for (int dir = 0; dir < 3; ++dir) fp[dir] = plans[dir];
+  auto set = [&](int c, int b, unsigned gx, unsigned gy, unsigned gz) {
+    BoxGrid &e = grids[c][b];
+    e.gx = gx ? gx : 1;
+    e.gy = gy ? gy : 1;
+    e.gz = gz ? gz : 1;
+  };
+  for (int b = 0; b < n; ++b) {
+    const Dev &d = devs[b];
+    const unsigned nb = (unsigned)((d.n + NT - 1) / NT);
+    const long long nghost = 2LL * GH * ((long long)d.ny * d.nz + (long long)d.nx * d.nz + (long long)d.nx * d.ny);
+    const unsigned ngb = (unsigned)((nghost + NT - 1) / NT);
+    set(BC_PRIMS, b, nb, 1, 1);
+    set(BC_GHOST, b, ngb, 1, 1);
+    if (d.mixed) {
+      unsigned zg[3];
+      z_pass_grid(d, zg);
+      set(BC_GRAD, b, zg[0], zg[1], zg[2]);
+      set(BC_VISC, b, zg[0], zg[1], zg[2]);
+    } else {
+      set(BC_GRAD, b, nb, 1, 1);
+      set(BC_VISC, b, nb, 1, 1);
+    }
+    for (int dir = 0; dir < 3; ++dir) {
+      const FluxBoxPlan &pl = plans[3 * b + dir];
+      unsigned c = (unsigned)pl.tiles;
+      if (pl.persistent) {
+        // the resident CTAs of a full device, shared out by tiles
+        const double share = (double)pl.per_sm * d.nsm * pl.tiles / (double)tiles_sum[dir];
+        unsigned k = (unsigned)share;
+        if (k < 1) k = 1;
+        if (k < c) c = k;
+      }
+      set(BC_FLUX0 + dir, b, c, 1, 1);
+      // WENO: the solo launch's CTAs shared out by interface slots
+      const unsigned solo = weno_batch_blocks(d, dir);
+      unsigned w = (unsigned)(16.0 * d.nsm * (double)d.nslot[dir] / (double)slots_sum[dir]) + 1;
+      set(BC_WENO0 + dir, b, w < solo ? w : solo, 1, 1);
+    }
+    set(BC_FORCE, b, NRED, 1, 1);
+    set(BC_ONE, b, 1, 1, 1);
+    ndt[b] = (int)nb;
+    const int fused = visc_force_partials(d);
+    nforce[b] = fused ? fused : NRED;
+  }
+  for (int c = 0; c < BC_COUNT; ++c) {
+    unsigned long long acc = 0;
+    for (int b = 0; b < n; ++b) {
+      grids[c][b].start = (unsigned)acc;
+      acc += (unsigned long long)grids[c][b].gx * grids[c][b].gy * grids[c][b].gz;
+    }
+    if (acc >= (1ull << 31)) return S2_EINVAL;
+    grids[c][n] = BoxGrid{(unsigned)acc, 1, 1, 1};
+    g.total[c] = (unsigned)acc;
+  }
+  // one block: tensor maps (64-byte aligned), parameters, tile grids, work lists
+  size_t off = 0;
+  size_t o_maps[3], o_dev, o_tg[3], o_grid[BC_COUNT], o_ndt, o_nf;
+  for (int dir = 0; dir < 3; ++dir) {
+    o_maps[dir] = off;
+    off = align_up(off + sizeof(FluxMaps) * n, 128);
+  }
+  o_dev = off;
+  off = align_up(off + sizeof(Dev) * n, 128);
+  for (int dir = 0; dir < 3; ++dir) {
+    o_tg[dir] = off;
+    off = align_up(off + (size_t)fp[dir].tg_size * n, 128);
+  }
+  for (int c = 0; c < BC_COUNT; ++c) {
+    o_grid[c] = off;
+    off = align_up(off + sizeof(BoxGrid) * (n + 1), 128);
+  }
+  o_ndt = off;
+  off = align_up(off + sizeof(int) * n, 128);
+  o_nf = off;
+  off = align_up(off + sizeof(int) * n, 128);
+  std::vector<unsigned char> host(off, 0);
+  for (int b = 0; b < n; ++b)
+    for (int dir = 0; dir < 3; ++dir) {
+      const s2_solver *m = g.members[b];
+      memcpy(host.data() + o_maps[dir] + sizeof(FluxMaps) * b, &m->fmaps[dir][d0.tile[dir] ? 1 : 0],
+             sizeof(FluxMaps));
+      memcpy(host.data() + o_tg[dir] + (size_t)fp[dir].tg_size * b, plans[3 * b + dir].tg, fp[dir].tg_size);
+    }
+  memcpy(host.data() + o_dev, devs.data(), sizeof(Dev) * n);
+  for (int c = 0; c < BC_COUNT; ++c) memcpy(host.data() + o_grid[c], grids[c].data(), sizeof(BoxGrid) * (n + 1));
+  memcpy(host.data() + o_ndt, ndt.data(), sizeof(int) * n);
+  memcpy(host.data() + o_nf, nforce.data(), sizeof(int) * n);
+  g.mem = batch_alloc(g.members[0], off);
+  if (!g.mem) return S2_ENOMEM;
+  if (cudaMemcpy(g.mem, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return S2_ECUDA;
+  unsigned char *base = (unsigned char *)g.mem;
+  for (int dir = 0; dir < 3; ++dir) {
+    g.maps[dir] = (FluxMaps *)(base + o_maps[dir]);
+    g.tgs[dir] = base + o_tg[dir];
+  }
+  g.dev = (Dev *)(base + o_dev);
+  for (int c = 0; c < BC_COUNT; ++c) g.grid[c] = (BoxGrid *)(base + o_grid[c]);
+  g.nparts_dt = (int *)(base + o_ndt);
+  g.nparts_force = (int *)(base + o_nf);
+  return S2_OK;
+}
+
+// One RK3 step of every box of a group: the stage sequence of
+// enqueue_step, each kernel launched once for all boxes.
+cudaError_t enqueue_group_step(BatchGroup &g) {
+  const Dev &d0 = g.members[0]->d;
+  const int n = (int)g.members.size();
+  cudaStream_t st = g.stream;
+  auto ba = [&](int c) { return BatchArgs{g.dev, g.grid[c], n}; };
+  long long cnt = 0;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    ++cnt;
+    if (e == cudaSuccess) e = r;
+  };
+  for (int stage = 0; stage < 3 && e == cudaSuccess; ++stage) {
+    const int stage0 = stage == 0;
+    if (d0.mixed) kb_prims_mixed<<<g.total[BC_PRIMS], NT, 0, st>>>(ba(BC_PRIMS), stage0);
+    else if (d0.kd.tp) kb_prims<true><<<g.total[BC_PRIMS], NT, 0, st>>>(ba(BC_PRIMS), stage0);
+    else kb_prims<false><<<g.total[BC_PRIMS], NT, 0, st>>>(ba(BC_PRIMS), stage0);
+    chk(cudaGetLastError());
+    if (stage0 && d0.cfl > 0.0) {
+      kb_dt_final<<<g.total[BC_ONE], NT, 0, st>>>(ba(BC_ONE), g.nparts_dt);
+      chk(cudaGetLastError());
+    }
+    if (d0.mixed) kb_ghost_prim<float><<<g.total[BC_GHOST], NT, 0, st>>>(ba(BC_GHOST));
+    else kb_ghost_prim<double><<<g.total[BC_GHOST], NT, 0, st>>>(ba(BC_GHOST));
+    chk(cudaGetLastError());
+    if (d0.viscous || d0.weno) {
+      chk(launch_grad_batch(d0, ba(BC_GRAD), g.total[BC_GRAD], st));
+      if (d0.mixed) kb_ghost_aux<float><<<g.total[BC_GHOST], NT, 0, st>>>(ba(BC_GHOST));
+      else kb_ghost_aux<double><<<g.total[BC_GHOST], NT, 0, st>>>(ba(BC_GHOST));
+      chk(cudaGetLastError());
+    }
+    if (d0.weno) {
+      kb_reset_counts<<<g.total[BC_ONE], NT, 0, st>>>(ba(BC_ONE));
+      chk(cudaGetLastError());
+    }
+    for (int dir = 0; dir < 3; ++dir)
+      chk(launch_flux_batch(d0, ba(BC_FLUX0 + dir), g.total[BC_FLUX0 + dir], g.maps[dir], g.tgs[dir], dir, dir > 0,
+                            st));
+    if (d0.weno)
+      for (int dir = 0; dir < 3; ++dir) chk(launch_weno_batch(d0, ba(BC_WENO0 + dir), g.total[BC_WENO0 + dir], dir, st));
+    if (d0.viscous) chk(launch_visc_batch(d0, ba(BC_VISC), g.total[BC_VISC], st));
+    else if (d0.weno) chk(launch_apply_batch(d0, ba(BC_PRIMS), g.total[BC_PRIMS], st));
+    if (d0.force) {
+      if (!visc_force_partials(d0)) {
+        if (d0.mixed) kb_force_partial<float><<<g.total[BC_FORCE], NT, 0, st>>>(ba(BC_FORCE));
+        else kb_force_partial<double><<<g.total[BC_FORCE], NT, 0, st>>>(ba(BC_FORCE));
+        chk(cudaGetLastError());
+      }
+      kb_force_final<<<g.total[BC_ONE], NT, 0, st>>>(ba(BC_ONE), g.nparts_force);
+      chk(cudaGetLastError());
+    }
+    if (d0.mixed) kb_update_mixed<<<g.total[BC_PRIMS], NT, 0, st>>>(ba(BC_PRIMS), RK_G[stage], RK_R[stage + 1], stage);
+    else kb_update<<<g.total[BC_PRIMS], NT, 0, st>>>(ba(BC_PRIMS), RK_G[stage], RK_R[stage + 1], stage);
+    chk(cudaGetLastError());
+  }
+  g.launches = cnt;
+  return e;
+}
 
 int batch_build(s2_batch *b) {
   cudaGraph_t g = nullptr;
@@ -1583,15 +1925,41 @@ int batch_build(s2_batch *b) {
   cudaError_t e = cudaEventRecord(b->events[0], b->stream);
   long long total_launches = 0;
   b->member_launches.assign(b->members.size(), 0);
-  for (size_t m = 0; m < b->members.size() && e == cudaSuccess; ++m) {
-    s2_solver *s = b->members[m];
-    e = cudaStreamWaitEvent(s->stream, b->events[0], 0);
-    Trace tr;
-    if (e == cudaSuccess) e = enqueue_step(s, &tr);
-    total_launches += total(tr);
-    b->member_launches[m] = total(tr);
-    if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + m], s->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[1 + m], 0);
+  if (b->mode == S2_BATCH_BRANCHES) {
+    for (size_t m = 0; m < b->members.size() && e == cudaSuccess; ++m) {
+      s2_solver *s = b->members[m];
+      e = cudaStreamWaitEvent(s->stream, b->events[0], 0);
+      Trace tr;
+      if (e == cudaSuccess) e = enqueue_step(s, &tr);
+      total_launches += total(tr);
+      b->member_launches[m] = total(tr);
+      if (e == cudaSuccess) e = cudaEventRecord(b->events[1 + m], s->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[1 + m], 0);
+    }
+  } else {
+    size_t ev = 1;
+    for (size_t k = 0; k < b->groups.size() && e == cudaSuccess; ++k, ++ev) {
+      BatchGroup &grp = b->groups[k];
+      e = cudaStreamWaitEvent(grp.stream, b->events[0], 0);
+      if (e == cudaSuccess) e = enqueue_group_step(grp);
+      total_launches += grp.launches;
+      for (size_t m = 0; m < b->members.size(); ++m)
+        for (s2_solver *s : grp.members)
+          if (s == b->members[m]) b->member_launches[m] = grp.launches;
+      if (e == cudaSuccess) e = cudaEventRecord(b->events[ev], grp.stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[ev], 0);
+    }
+    for (size_t k = 0; k < b->solo.size() && e == cudaSuccess; ++k, ++ev) {
+      s2_solver *s = b->solo[k];
+      e = cudaStreamWaitEvent(s->stream, b->events[0], 0);
+      Trace tr;
+      if (e == cudaSuccess) e = enqueue_step(s, &tr);
+      total_launches += total(tr);
+      for (size_t m = 0; m < b->members.size(); ++m)
+        if (b->members[m] == s) b->member_launches[m] = total(tr);
+      if (e == cudaSuccess) e = cudaEventRecord(b->events[ev], s->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->events[ev], 0);
+    }
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -1616,6 +1984,8 @@ void batch_release(s2_batch *b) {
   if (b->ready) cudaGraphExecDestroy(b->graph);
   for (cudaEvent_t ev : b->events)
     if (ev) cudaEventDestroy(ev);
+  for (BatchGroup &g : b->groups) batch_free(g.members[0], g.mem);
+  b->groups.clear();
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1623,8 +1993,10 @@ void batch_release(s2_batch *b) {
 
 extern "C" {
 
-int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out) {
-  if (!out || !members || count < 1) return S2_EINVAL;
+int s2_batch_create_ex(s2_solver *const *members, int count, void *stream, int mode, s2_batch **out) {
+  if (!out || !members || count < 1 ||
+      (mode != S2_BATCH_WORKLIST && mode != S2_BATCH_BRANCHES && mode != S2_BATCH_WORKLIST_ALL))
+    return S2_EINVAL;
   *out = nullptr;
   int device = members[0] ? members[0]->device : -1;
   for (int m = 0; m < count; ++m) {
@@ -1637,6 +2009,7 @@ int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch
   DeviceGuard guard(device);
   b->members.assign(members, members + count);
   b->device = device;
+  b->mode = mode;
   if (stream) {
     b->stream = (cudaStream_t)stream;
     b->own_stream = false;
@@ -1646,21 +2019,35 @@ int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch
   } else {
     b->own_stream = true;
   }
-  b->events.assign(count + 1, nullptr);
-  for (auto &ev : b->events)
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      batch_release(b);
-      delete b;
-      return S2_ECUDA;
+  int rc = S2_OK;
+  if (mode != S2_BATCH_BRANCHES) {
+    for (s2_solver *s : b->members) {
+      if (mode == S2_BATCH_WORKLIST && s->d.n >= S2_BATCH_SOLO_POINTS) {  // fills enough of the GPU on its own
+        b->solo.push_back(s);
+        continue;
+      }
+      BatchGroup *g = nullptr;
+      for (BatchGroup &x : b->groups)
+        if (same_kernels(x.members[0]->d, s->d)) g = &x;
+      if (!g) {
+        b->groups.emplace_back();
+        g = &b->groups.back();
+        g->stream = s->stream;
+        g->mem = nullptr;
+      }
+      g->members.push_back(s);
     }
+    for (BatchGroup &g : b->groups)
+      if (rc == S2_OK) rc = group_setup(g);
+  }
+  const size_t branches = mode != S2_BATCH_BRANCHES ? b->groups.size() + b->solo.size() : (size_t)count;
+  b->events.assign(branches + 1, nullptr);
+  for (auto &ev : b->events)
+    if (rc == S2_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = S2_ECUDA;
   // the members' own pending work is ordered before the batch's first step
   for (s2_solver *s : b->members)
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-      batch_release(b);
-      delete b;
-      return S2_ECUDA;
-    }
-  int rc = batch_build(b);
+    if (rc == S2_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = S2_ECUDA;
+  if (rc == S2_OK) rc = batch_build(b);
   if (rc != S2_OK) {
     batch_release(b);
     delete b;
@@ -1669,6 +2056,12 @@ int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch
   *out = b;
   return S2_OK;
 }
+
+int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out) {
+  return s2_batch_create_ex(members, count, stream, S2_BATCH_WORKLIST, out);
+}
+
+long long s2_batch_launches(const s2_batch *b) { return b ? b->launches_per_step : -1; }
 
 int s2_batch_step(s2_batch *b, int n) {
   if (!b || n < 0) return S2_EINVAL;

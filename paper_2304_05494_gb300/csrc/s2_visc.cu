@@ -198,8 +198,8 @@ __device__ __forceinline__ void visc_terms(const Consts<R> &K, const R (&g)[3][3
 }
 
 template <class R>
-__global__ void __launch_bounds__(NT) k_apply(Dev d) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void apply_body(const Dev &__restrict__ d, const Blk &B) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   if (q >= d.n) return;
   const View<R> V = view<R>(d);
   int i, j, k;
@@ -212,9 +212,20 @@ __global__ void __launch_bounds__(NT) k_apply(Dev d) {
   for (int f = 0; f < NV; ++f) V.fl[f * d.n + q] = Rv[f];
 }
 
+template <class R>
+__global__ void __launch_bounds__(NT) k_apply(Dev d) {
+  apply_body<R>(d, grid_blk());
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) kb_apply(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  apply_body<R>(sd, B);
+}
+
 template <class R, int NP>
-__global__ void __launch_bounds__(NT) k_grad(Dev d) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void grad_body(const Dev &__restrict__ d, const Blk &B) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   if (q >= d.n) return;
   const View<R> V = view<R>(d);
   int i, j, k;
@@ -242,8 +253,19 @@ __global__ void __launch_bounds__(NT) k_grad(Dev d) {
 }
 
 template <class R, int NP>
-__global__ void __launch_bounds__(NT) k_visc(Dev d) {
-  long long q = (long long)blockIdx.x * NT + threadIdx.x;
+__global__ void __launch_bounds__(NT) k_grad(Dev d) {
+  grad_body<R, NP>(d, grid_blk());
+}
+
+template <class R, int NP>
+__global__ void __launch_bounds__(NT) kb_grad(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  grad_body<R, NP>(sd, B);
+}
+
+template <class R, int NP>
+__device__ __forceinline__ void visc_body(const Dev &__restrict__ d, const Blk &B) {
+  long long q = (long long)B.x * NT + threadIdx.x;
   if (q >= d.n) return;
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
@@ -291,6 +313,17 @@ __global__ void __launch_bounds__(NT) k_visc(Dev d) {
   if (d.weno) V.fl[q] = Rv[0];
 #pragma unroll
   for (int f = 1; f < NV; ++f) V.fl[f * d.n + q] = Rv[f];
+}
+
+template <class R, int NP>
+__global__ void __launch_bounds__(NT) k_visc(Dev d) {
+  visc_body<R, NP>(d, grid_blk());
+}
+
+template <class R, int NP>
+__global__ void __launch_bounds__(NT) kb_visc(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  visc_body<R, NP>(sd, B);
 }
 
 // ------------------------------------------------ z-marching (mixed path)
@@ -345,12 +378,12 @@ struct ZTile {
   long long cbase;                      // padded offset of (i, j, 0)
   long long hbase[ZGeom<NP>::HPT];
   int hoff[ZGeom<NP>::HPT];             // shared offset, -1 when unused
-  __device__ __forceinline__ ZTile(const Dev &d) {
+  __device__ __forceinline__ ZTile(const Dev &d, const Blk &B) {
     constexpr int SX = ZGeom<NP>::SX;
     const int tid = threadIdx.x;
-    x0 = blockIdx.x * ZTX;
-    y0 = blockIdx.y * ZTY;
-    z0 = blockIdx.z * ZS;
+    x0 = B.x * ZTX;
+    y0 = B.y * ZTY;
+    z0 = B.z * ZS;
     z1 = min(z0 + ZS, d.nz);
     i = x0 + tid % ZTX;
     j = y0 + tid / ZTX;
@@ -386,13 +419,13 @@ struct ZTile {
 // z-marching gradient pass: theta = div u (with ghosts at walls) and the
 // sensor test.  NF = 3 staged fields (u, v, w).
 template <int NP>
-__global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
+__device__ __forceinline__ void grad_z_body(const Dev &__restrict__ d, const Blk &B) {
   using R = float;
   constexpr int NF = 3, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
   __shared__ R sm[2][NF][SZ];
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
-  const ZTile<NP> t(d);
+  const ZTile<NP> t(d, B);
   const R *src[NF] = {V.u, V.v, V.ww};
   const long long sz = d.sz;
   C5<R> cx, cy, cz;
@@ -464,16 +497,27 @@ __global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
   }
 }
 
+template <int NP>
+__global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
+  grad_z_body<NP>(d, grid_blk());
+}
+
+template <int NP>
+__global__ void __launch_bounds__(NT, 3) kb_grad_z(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  grad_z_body<NP>(sd, B);
+}
+
 // z-marching viscous pass (velocity gradients recomputed), plus the WENO
 // corrections.  NF = 5 staged fields (u, v, w, T, theta).
 template <int NP>
-__global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
+__device__ __forceinline__ void visc_z_body(const Dev &__restrict__ d, const Blk &B) {
   using R = float;
   constexpr int NF = 5, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
   __shared__ R sm[2][NF][SZ];
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
-  const ZTile<NP> t(d);
+  const ZTile<NP> t(d, B);
   const R *src[NF] = {V.u, V.v, V.ww, V.T, V.div};
   const long long sz = d.sz;
   const int jc = t.active ? t.j : 0;
@@ -591,9 +635,20 @@ __global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
     if (threadIdx.x == 0) {
       double tot = 0.0;
       for (int w = 0; w < NT / 32; ++w) tot += wsum[w];
-      d.part[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+      d.part[((long long)B.z * B.ny + B.y) * B.nx + B.x] = tot;
     }
   }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
+  visc_z_body<NP>(d, grid_blk());
+}
+
+template <int NP>
+__global__ void __launch_bounds__(NT, 2) kb_visc_z(BatchArgs ba) {
+  S2_BATCH_ENTER(ba, sd, B, b_box);
+  visc_z_body<NP>(sd, B);
 }
 
 
@@ -653,6 +708,58 @@ long long z_pass_blocks(const Dev &d) {
 int visc_force_partials(const Dev &d) {
   if (!(d.mixed && d.force && d.viscous)) return 0;
   return (int)z_pass_blocks(d);
+}
+
+void z_pass_grid(const Dev &d, unsigned g[3]) {
+  const dim3 z = zgrid(d);
+  g[0] = z.x;
+  g[1] = z.y;
+  g[2] = z.z;
+}
+
+// Batched: every box of a batch group in one launch (instantiation of d0).
+cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
+  if (d0.mixed) {
+    switch (d0.npv) {
+      case 1: kb_grad_z<1><<<total, NT, 0, st>>>(ba); break;
+      case 2: kb_grad_z<2><<<total, NT, 0, st>>>(ba); break;
+      case 3: kb_grad_z<3><<<total, NT, 0, st>>>(ba); break;
+      default: kb_grad_z<4><<<total, NT, 0, st>>>(ba); break;
+    }
+  } else {
+    switch (d0.npv) {
+      case 1: kb_grad<double, 1><<<total, NT, 0, st>>>(ba); break;
+      case 2: kb_grad<double, 2><<<total, NT, 0, st>>>(ba); break;
+      case 3: kb_grad<double, 3><<<total, NT, 0, st>>>(ba); break;
+      default: kb_grad<double, 4><<<total, NT, 0, st>>>(ba); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_visc_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
+  if (d0.mixed) {
+    switch (d0.npv) {
+      case 1: kb_visc_z<1><<<total, NT, 0, st>>>(ba); break;
+      case 2: kb_visc_z<2><<<total, NT, 0, st>>>(ba); break;
+      case 3: kb_visc_z<3><<<total, NT, 0, st>>>(ba); break;
+      default: kb_visc_z<4><<<total, NT, 0, st>>>(ba); break;
+    }
+  } else {
+    switch (d0.npv) {
+      case 1: kb_visc<double, 1><<<total, NT, 0, st>>>(ba); break;
+      case 2: kb_visc<double, 2><<<total, NT, 0, st>>>(ba); break;
+      case 3: kb_visc<double, 3><<<total, NT, 0, st>>>(ba); break;
+      default: kb_visc<double, 4><<<total, NT, 0, st>>>(ba); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
+  if (d0.mixed) kb_apply<float><<<total, NT, 0, st>>>(ba);
+  else kb_apply<double><<<total, NT, 0, st>>>(ba);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_visc(const Dev &d, cudaStream_t st) {

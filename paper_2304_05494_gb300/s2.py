@@ -107,6 +107,10 @@ def _load():
     lib.s2_fma_rate.restype = C.c_int
     lib.s2_cfl_dt_noalloc.argtypes = [C.POINTER(s2_grid), C.POINTER(s2_gas), P, P, C.c_double, P, P]
     lib.s2_cfl_dt_noalloc.restype = C.c_int
+    lib.s2_batch_create_ex.argtypes = [C.POINTER(P), C.c_int, P, C.c_int, C.POINTER(P)]
+    lib.s2_batch_create_ex.restype = C.c_int
+    lib.s2_batch_launches.argtypes = [P]
+    lib.s2_batch_launches.restype = C.c_longlong
     lib.s2_batch_create.argtypes = [C.POINTER(P), C.c_int, P, C.POINTER(P)]
     lib.s2_batch_create.restype = C.c_int
     lib.s2_batch_step.argtypes = [P, C.c_int]
@@ -250,11 +254,24 @@ def s2_cfl_dt_noalloc(grid, gas, w, eta_y, cfl: float, dt, stream=None) -> int:
                                   eta_y.data_ptr() if eta_y is not None else None, cfl, dt.data_ptr(), stream)
 
 
-def s2_batch_create(handles, stream=None):
+S2_BATCH_WORKLIST, S2_BATCH_BRANCHES, S2_BATCH_WORKLIST_ALL = 0, 1, 2
+_BATCH_MODES = {"worklist": S2_BATCH_WORKLIST, "branches": S2_BATCH_BRANCHES, "worklist_all": S2_BATCH_WORKLIST_ALL}
+
+
+def s2_batch_create(handles, stream=None, mode: str = "worklist"):
+    """mode: "worklist" (one launch per kernel for all boxes of a group;
+    members of 64^3 points or more keep their own launches), "worklist_all"
+    (every member in the work list) or "branches" (each member's own
+    launches as concurrent graph branches)."""
     arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
     b = C.c_void_p()
-    _check(_lib.s2_batch_create(arr, len(handles), stream, C.byref(b)), "s2_batch_create")
+    m = _BATCH_MODES[mode]
+    _check(_lib.s2_batch_create_ex(arr, len(handles), stream, m, C.byref(b)), "s2_batch_create")
     return b
+
+
+def s2_batch_launches(b) -> int:
+    return int(_lib.s2_batch_launches(b))
 
 
 def s2_batch_step(b, n: int) -> None:
@@ -272,9 +289,13 @@ def s2_batch_destroy(b) -> None:
 class Batch:
     """Owning wrapper of a batch of solvers (destroyed before its members)."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, mode: str = "worklist"):
         self.solvers = list(solvers)
-        self.b = s2_batch_create([sv.h for sv in self.solvers], stream)
+        self.b = s2_batch_create([sv.h for sv in self.solvers], stream, mode)
+
+    @property
+    def launches_per_step(self) -> int:
+        return s2_batch_launches(self.b)
 
     def step(self, n: int = 1):
         s2_batch_step(self.b, n)

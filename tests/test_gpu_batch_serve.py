@@ -3,13 +3,19 @@
 A box's results must not depend on what else runs with it: members of a
 batch (one graph launch per step, members as concurrent branches) and
 requests served in a continuous-batching mix must match their solo runs
-bit for bit (the kernels are deterministic and share no buffers).  The
-tile shape of the flux kernels must not change results either.
+bit for bit (the kernels are deterministic and share no buffers), and
+the CPU oracle run on the same box: FP64 members to 1e-11 per conserved
+field, mixed-precision members to 3e-4 of the FP64 oracle.  The tile shape
+of the flux kernels must not change results either.
 """
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2304_05494_gb300 import workloads as W
+
+TOL_FP64 = 1e-11   # field-normalised, FP64 members against the oracle
+TOL_MIXED = 3e-4   # field-normalised, mixed members against the FP64 oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -28,6 +34,22 @@ def solo(s2, case, steps, **kw):
         sv.set_state(case.w0)
         sv.step(steps)
         return sv.get_state()
+
+
+def oracle_steps(case, steps, cfl=None, dt_every=None, threshold=None):
+    """The CPU oracle's state after the given steps from case.w0, with the
+    solver's dt schedule (CFL every dt_every steps)."""
+    pr = O.Problem(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, y=case.y, gamma=case.gamma,
+                   prandtl=case.prandtl, mach=case.mach, re=case.re, visc_exp=case.visc_exp, t_ref=case.t_ref,
+                   wall_y=case.wall_y, t_wall=case.t_wall, force=case.force, weno_order=case.weno_order,
+                   threshold=case.threshold if threshold is None else threshold)
+    w, _, _ = O.step(pr, case.w0, steps, cfl=case.cfl if cfl is None else cfl,
+                     dt_every=case.dt_every if dt_every is None else dt_every)
+    return w
+
+
+def field_err(a, b):
+    return float(np.max(np.max(np.abs(a - b), axis=(1, 2, 3)) / np.max(np.abs(b), axis=(1, 2, 3))))
 
 
 def test_batch_members_match_solo_runs(s2):
@@ -51,6 +73,78 @@ def test_batch_members_match_solo_runs(s2):
     for (c, kw), g, st in zip(cases, got, stats):
         assert st["step"] == 6
         assert np.array_equal(g, solo(s2, c, 6, **kw))
+        ref = oracle_steps(c, 6, cfl=kw["cfl"], dt_every=kw["dt_every"], threshold=kw.get("threshold"))
+        tol = TOL_FP64 if kw["precision"] == "fp64" else TOL_MIXED
+        assert field_err(g, ref) < tol, (c.name, kw["precision"], field_err(g, ref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_worklist_batch_of_uneven_boxes_matches_solo_runs(s2, precision):
+    """Work-list batching: boxes of different sizes and shapes sharing their
+    kernels run as one group (each kernel one launch for all of them, the
+    work list giving every CTA its box and tile); every member equals its
+    solo run bit for bit, and the whole step costs the launches of one box.
+    A member with another scheme forms a second group."""
+    box = W.Case(name="smooth28x20x12", nx=28, ny=20, nz=12, lx=2 * np.pi, ly=2 * np.pi, lz=2 * np.pi,
+                 w0=W.smooth_periodic(28, 20, 12, seed=7, mach=0.5, amp_u=0.4, amp_s=0.1), mach=0.5, re=300.0)
+    cases = [W.taylor_green(24, seed=3), W.taylor_green(32, mach=0.4, re=800.0, seed=4),
+             W.isotropic(20, mach_t=0.6, seed=6, weno_order=5), box]
+    for c in cases:
+        c.weno_order, c.threshold, c.cfl, c.dt_every = 5, 0.1, 0.8, 2
+    odd = W.channel(40, 24, 16, seed=9)  # walls and forcing: its own group
+    kw = dict(precision=precision)
+    solvers = []
+    for c in cases + [odd]:
+        sv = s2.Solver.from_case(c, **kw)
+        sv.set_state(c.w0)
+        solvers.append(sv)
+    with s2.Batch(solvers) as b:
+        n_work = b.launches_per_step
+        b.step(3)
+        b.sync()
+    got = [sv.get_state() for sv in solvers]
+    for sv in solvers:
+        sv.close()
+    for c, g in zip(cases + [odd], got):
+        assert np.array_equal(g, solo(s2, c, 3, **kw)), c.name
+    # the branch graph launches every member's kernels; the work list one
+    # set per group (two groups here)
+    solvers = [s2.Solver.from_case(c, **kw) for c in cases + [odd]]
+    with s2.Batch(solvers, mode="branches") as b:
+        n_branch = b.launches_per_step
+    for sv in solvers:
+        sv.close()
+    assert n_work < n_branch / 2, (n_work, n_branch)
+    assert n_work <= 2 * 45
+
+
+@pytest.mark.parametrize("precision,sizes,factor", [
+    ("mixed", [16] * 16 + [24] * 32 + [32] * 8, 0.8),
+    ("fp64", [16] * 48 + [24] * 16, 0.9)])
+def test_worklist_batch_runs_many_small_boxes_faster(s2, precision, sizes, factor):
+    """Many small boxes: the work list's one launch per kernel for all of
+    them beats launching every member's kernels as graph branches."""
+    import time
+    cases = [W.taylor_green(n, mach=0.3, seed=10 + i) for i, n in enumerate(sizes)]
+    for c in cases:
+        c.weno_order, c.threshold = 5, 0.2
+    times = {}
+    for mode in ("branches", "worklist", "branches", "worklist"):
+        solvers = []
+        for c in cases:
+            sv = s2.Solver.from_case(c, precision=precision)
+            sv.set_state(c.w0)
+            solvers.append(sv)
+        with s2.Batch(solvers, mode=mode) as b:
+            b.step(2)
+            b.sync()
+            t0 = time.perf_counter()
+            b.step(10)
+            b.sync()
+            times[mode] = min(times.get(mode, 1e9), time.perf_counter() - t0)
+        for sv in solvers:
+            sv.close()
+    assert times["worklist"] < factor * times["branches"], times
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -95,6 +189,9 @@ def test_serving_results_same_alone_and_in_the_mix(s2):
         c = serve.initial_case(r)
         alone = solo(s2, c, r.steps, precision=r.precision)
         assert np.array_equal(r.result, alone), r.rid
+        ref = oracle_steps(c, r.steps)
+        tol = TOL_FP64 if r.precision == "fp64" else TOL_MIXED
+        assert field_err(r.result, ref) < tol, (r.rid, r.precision, field_err(r.result, ref))
 
 
 def test_serving_isolates_failed_and_cancelled_requests(s2):
