@@ -50,6 +50,7 @@ class _Cfg(C.Structure):
         ("force", C.c_int), ("weno_order", C.c_int), ("threshold", C.c_double),
         ("central_order", C.c_int), ("visc_order", C.c_int),
         ("cp_coef", C.POINTER(C.c_double)),
+        ("keep", C.c_int),
     ]
 
 
@@ -135,6 +136,8 @@ class Problem:
     visc_order: int = 6                  # 2, 4, 6, 8
     # thermally perfect gas: a_{-2..4} of c_p/R = sum_l a_l T^l; None = calorically perfect
     cp_coef: Optional[np.ndarray] = None
+    # central flux: 0 split form; n >= 1 KEEP-n (log means from n series terms); -1 KEEP, exact log means
+    keep: int = 0
     _y_buf: Optional[np.ndarray] = field(default=None, repr=False)
     _cp_buf: Optional[np.ndarray] = field(default=None, repr=False)
 
@@ -165,6 +168,7 @@ class Problem:
             c.cp_coef = _dp(self._cp_buf)
         else:
             c.cp_coef = None
+        c.keep = self.keep
         return c
 
     @property

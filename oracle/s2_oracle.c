@@ -97,6 +97,7 @@ typedef struct {
   int central_order;    /* 2, 4, 6 or 8: split-form convective flux */
   int visc_order;       /* 2, 4, 6 or 8: viscous terms and the sensor's derivatives */
   const double *cp_coef; /* NULL: calorically perfect; else a_{-2..4} of c_p/R = sum a_l T^l */
+  int keep;             /* central flux: 0 split form; n >= 1 KEEP-n (series of n terms); -1 KEEP, exact log mean */
 } or_cfg;
 
 /* Which terms or_rhs evaluates. */
@@ -187,6 +188,7 @@ static int ws_init(ws_t *s, const or_cfg *c) {
   memset(s, 0, sizeof(*s));
   s->c = c;
   if (!valid_order(c->central_order) || !valid_order(c->visc_order)) return -1;
+  if (c->keep < -1 || (c->keep != 0 && c->cp_coef)) return -1; /* KEEP: calorically perfect gas */
   s->lc = c->central_order / 2;
   s->lv = c->visc_order / 2;
   s->ac = A1_ORD[s->lc];
@@ -778,6 +780,63 @@ static void central_flux(const ws_t *s, int dir, int pos, int i, int j, int k, d
   F[1 + dir] += fp;
 }
 
+/* ---------------------------------------------------------------- KEEP-n ---
+ * Kinetic-energy and entropy preserving central flux (paper Sec. 2: the
+ * optional KEEP-n scheme, which keeps kinetic energy and, for smooth
+ * inviscid flow, entropy locally).  Reading: the same flux-differencing
+ * form as the split-form flux, F = 2 sum_l a_l sum_{m<l} f*(w_{pos-m},
+ * w_{pos-m+l}), with the two-point flux of a calorically perfect gas
+ *   f*_rho  = <rho> {u_n}
+ *   f*_rhou = f*_rho {u} + {p} n
+ *   f*_rhoE = f*_rho (c_v / <1/T> + (u_a . u_b)/2) + (p_a u_n,b + p_b u_n,a)/2
+ * ({.} arithmetic, <.> logarithmic mean), which satisfies Tadmor's
+ * entropy condition for the entropy -rho s/(gamma-1), s = ln(p rho^-gamma)
+ * (Ranocha 2018), so the central scheme conserves that entropy; its
+ * momentum flux (mass flux times the mean velocity plus the mean pressure)
+ * preserves kinetic energy, and uniform velocity and pressure stay
+ * uniform.  KEEP-n takes the logarithmic mean from the first n terms of
+ * its series in z = (a-b)/(a+b): <a,b> = {a} / sum_{k<n} z^2k/(2k+1), an
+ * entropy error of order z^2n per pair; n = -1 takes the exact mean. */
+static double log_mean(double a, double b, int n) {
+  double z = (a - b) / (a + b), u = z * z;
+  if (n < 0) {
+    if (u > 1e-4) return (a - b) / log(a / b);
+    n = 6; /* the series' remainder is below u^6/13: below rounding */
+  }
+  double F = 0.0, zk = 1.0;
+  for (int k = 0; k < n; ++k) {
+    F += zk / (2.0 * k + 1.0);
+    zk *= u;
+  }
+  return 0.5 * (a + b) / F;
+}
+
+/* the two-point flux of points a and b along direction dir */
+static void keep_pair(const ws_t *s, int dir, size_t a, size_t b, double *f) {
+  const double *un = dir == 0 ? s->u : (dir == 1 ? s->v : s->w);
+  double rl = log_mean(s->rho[a], s->rho[b], s->c->keep);
+  double bl = log_mean(1.0 / s->T[a], 1.0 / s->T[b], s->c->keep); /* <1/T> */
+  double unm = 0.5 * (un[a] + un[b]);
+  double fr = rl * unm;
+  f[0] = fr;
+  f[1] = fr * 0.5 * (s->u[a] + s->u[b]);
+  f[2] = fr * 0.5 * (s->v[a] + s->v[b]);
+  f[3] = fr * 0.5 * (s->w[a] + s->w[b]);
+  f[1 + dir] += 0.5 * (s->p[a] + s->p[b]);
+  double uab = s->u[a] * s->u[b] + s->v[a] * s->v[b] + s->w[a] * s->w[b];
+  f[4] = fr * (s->cv / bl + 0.5 * uab) + 0.5 * (s->p[a] * un[b] + s->p[b] * un[a]);
+}
+
+static void keep_flux(const ws_t *s, int dir, int pos, int i, int j, int k, double *F) {
+  for (int f = 0; f < 5; ++f) F[f] = 0.0;
+  for (int l = 1; l <= s->lc; ++l)
+    for (int m = 0; m < l; ++m) {
+      double f2[5];
+      keep_pair(s, dir, at(s, dir, pos - m, i, j, k), at(s, dir, pos - m + l, i, j, k), f2);
+      for (int f = 0; f < 5; ++f) F[f] += 2.0 * s->ac[l] * f2[f];
+    }
+}
+
 /* flags: where the per-interface WENO flags are written, or (given != 0)
  * read from: a caller-supplied decision replaces the sensor test. */
 static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags, int given) {
@@ -816,7 +875,8 @@ static void convective(ws_t *s, int dir, double *rhs, unsigned char *flags, int 
           weno_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
         } else {
           OR_SECTION(SEC_CENTRAL);
-          central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+          if (s->c->keep) keep_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
+          else central_flux(s, dir, pos, i, j, k, Fh + 5 * (pos + 1));
         }
       }
       OR_SECTION(SEC_CENTRAL);

@@ -131,40 +131,57 @@ class Server:
         return BYTES_PER_POINT[req.precision] * (n + 8) ** 3
 
     def run(self, reqs: List[Request], log=None) -> dict:
+        """Serve the requests (arrival times relative to the call).  A request
+        that has arrived has its initial field built on a host thread while
+        the GPU works on the running batch; it is admitted (solver created,
+        state copied in) at the next tick with a free slot and memory."""
+        from concurrent.futures import ThreadPoolExecutor
         s2 = self.s2
         pending = sorted(reqs, key=lambda r: r.arrival)
+        prep = ThreadPoolExecutor(max_workers=2)
+        cases = {}           # rid -> future of its initial case
         active = []           # (req, solver, remaining)
         used = 0.0
         batch = None
         changed = False
         lat = []              # (per-step latency seconds, weight = active boxes)
+        host = {"prepare": 0.0, "batch_build": 0.0, "gpu_ticks": 0.0, "retire": 0.0}
         ticks = 0
         done_points = 0
         t0 = time.perf_counter()
         while pending or active:
             now = time.perf_counter() - t0
-            # admission: arrived requests, while a slot and memory are free
-            while pending and pending[0].arrival <= now and len(active) < self.max_slots \
-                    and used + self._bytes(pending[0]) <= self.budget:
+            # arrived requests: their initial fields are built in the background
+            for r in pending:
+                if r.arrival > now:
+                    break
+                if r.rid not in cases:
+                    cases[r.rid] = prep.submit(initial_case, r)
+            # admission: arrived and prepared requests, while a slot and memory are free
+            while pending and pending[0].arrival <= now and cases[pending[0].rid].done() \
+                    and len(active) < self.max_slots and used + self._bytes(pending[0]) <= self.budget:
                 r = pending.pop(0)
-                c = initial_case(r)
+                tp = time.perf_counter()
+                c = cases.pop(r.rid).result()
                 sv = s2.Solver.from_case(c, precision=r.precision, stream=None)
                 sv.set_state(c.w0)
+                host["prepare"] += time.perf_counter() - tp
                 active.append([r, sv, r.steps])
                 used += self._bytes(r)
                 r.admitted = time.perf_counter() - t0
                 changed = True
             if not active:
-                # idle until the next arrival
+                # idle until the next arrival or preparation
                 wait = pending[0].arrival - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 0.05))
+                time.sleep(min(max(wait, 0.0), 0.05) if wait > 0 else 0.001)
                 continue
             if changed:
+                tb = time.perf_counter()
                 if batch is not None:
                     batch.close()
                 batch = s2.Batch([a[1] for a in active], self.stream)
                 changed = False
+                host["batch_build"] += time.perf_counter() - tb
             # a tick never runs past a request's end or its client's cancel
             k = min(self.k, min(self._left(a) for a in active))
             ts = time.perf_counter()
@@ -182,6 +199,7 @@ class Server:
                     except s2.S2Error as e:
                         failed.append((a, e))
             dt_tick = time.perf_counter() - ts
+            host["gpu_ticks"] += dt_tick
             ticks += 1
             lat.append((dt_tick / k, len(active), k))
             for a in active:
@@ -193,6 +211,7 @@ class Server:
             retire += [(a, "cancelled") for a in active if a[2] > 0 and id(a) not in bad
                        and a[0].cancel_after is not None and a[0].steps - a[2] >= a[0].cancel_after]
             if retire:
+                tr = time.perf_counter()
                 batch.close()
                 batch = None
                 changed = True
@@ -205,10 +224,12 @@ class Server:
                     r.finished = time.perf_counter() - t0
                     used -= self._bytes(r)
                     active.remove(a)
+                host["retire"] += time.perf_counter() - tr
             if log:
                 log(ticks, len(active), len(pending), dt_tick)
         if batch is not None:
             batch.close()
+        prep.shutdown()
         wall = time.perf_counter() - t0
         # per-step latency distribution, weighted by the boxes and steps of each tick
         vals = np.array([l for l, _, _ in lat])
@@ -226,7 +247,8 @@ class Server:
                 "wall_s": wall, "point_steps": done_points,
                 "throughput": done_points / wall, "ticks": ticks,
                 "p50_step_latency_ms": pct(0.5) * 1e3, "p99_step_latency_ms": pct(0.99) * 1e3,
-                "p50_queue_s": float(np.percentile(waits, 50)), "p99_queue_s": float(np.percentile(waits, 99))}
+                "p50_queue_s": float(np.percentile(waits, 50)), "p99_queue_s": float(np.percentile(waits, 99)),
+                "host_s": host}
 
 
 def capacity(precision: str, sizes=SIZES, steps: int = 10) -> float:

@@ -83,6 +83,21 @@ MUTANTS = [
      "static const double RK_RHO[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};",
      "static const double RK_RHO[3] = {0.0, -17.0 / 60.0, -5.0 / 13.0};",
      P.test_rk3_third_order_and_consistency),
+    # KEEP: arithmetic instead of logarithmic mean density
+    ("KEEP arithmetic-mean density",
+     "double rl = log_mean(s->rho[a], s->rho[b], s->c->keep);",
+     "double rl = 0.5 * (s->rho[a] + s->rho[b]);",
+     lambda: P.test_keep_conserves_entropy(6, False)),
+    # KEEP: pressure work without the cross products
+    ("KEEP pressure work",
+     "0.5 * (s->p[a] * un[b] + s->p[b] * un[a]);",
+     "0.5 * (s->p[a] * un[a] + s->p[b] * un[b]);",
+     lambda: P.test_keep_conserves_entropy(6, False)),
+    # KEEP: internal energy from the arithmetic mean of 1/T
+    ("KEEP internal-energy mean",
+     "double bl = log_mean(1.0 / s->T[a], 1.0 / s->T[b], s->c->keep); /* <1/T> */",
+     "double bl = 0.5 * (1.0 / s->T[a] + 1.0 / s->T[b]);",
+     lambda: P.test_keep_conserves_entropy(6, False)),
     # forcing: the work of the body force dropped from the energy equation
     ("forcing power dropped",
      "rhs[4 * n + q] += f * s->u[PI(s, i, j, k)];",

@@ -809,3 +809,123 @@ def test_weno7_indicator_evaluation_form():
     assert err_sos["unit"] < 1e-13 and err_exp["unit"] < 1e-12
     assert err_sos["offset"] < 1e-6
     assert err_exp["offset"] > 1e3 * err_sos["offset"]
+
+
+# --------------------------------------------------------------- KEEP-n ---
+def _entropy_vars(w, gamma=1.4):
+    """Entropy variables of U = -rho s/(gamma-1), s = ln(p rho^-gamma)."""
+    rho = w[0]
+    u, v, ww = w[1] / rho, w[2] / rho, w[3] / rho
+    q2 = u * u + v * v + ww * ww
+    p = (gamma - 1.0) * (w[4] - 0.5 * rho * q2)
+    s = np.log(p) - gamma * np.log(rho)
+    b = rho / p
+    return np.stack([(gamma - s) / (gamma - 1.0) - 0.5 * b * q2, b * u, b * v, b * ww, -b])
+
+
+def _entropy_production(keep, order, stretched=False, seed=31):
+    n = (14, 12, 10)
+    xi = np.arange(n[1]) * 2 * np.pi / n[1]
+    y = xi + 0.25 * np.sin(xi) if stretched else None
+    p = _prob(n[0], n[1], n[2], y=y, mach=0.5, re=-1.0, weno_order=0, central_order=order, keep=keep)
+    w = W.smooth_periodic(*n, seed=seed, mach=0.5, amp_u=0.6, amp_s=0.3)
+    r = O.rhs(p, w, terms=O.CONV)
+    ey, _ = O.metric(p)
+    dv = (1.0 / ey)[None, :, None]
+    prod = np.sum(_entropy_vars(w) * r, axis=0)
+    return abs(np.sum(prod * dv)) / np.sum(np.abs(prod) * dv)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+@pytest.mark.parametrize("stretched", [False, True])
+def test_keep_conserves_entropy(order, stretched):
+    """KEEP with exact logarithmic means: the inviscid central RHS conserves
+    the entropy -rho s/(gamma-1) exactly (sum of v . R dV over a periodic
+    box is round-off, v the entropy variables, dV = 1/eta_y), by Tadmor's
+    condition of the two-point flux and the antisymmetric flux-
+    differencing form; the split form of the default scheme does not."""
+    assert _entropy_production(-1, order, stretched) < 1e-12
+    assert _entropy_production(0, order, stretched) > 1e-5
+
+
+def test_keep_n_entropy_error_falls_with_n():
+    """KEEP-n: logarithmic means from n terms of their series; the entropy
+    production falls with the number of terms (error of order z^2n)."""
+    e = {n: _entropy_production(n, 6) for n in (1, 2, 5, 6)}
+    # (the net production sums signed per-pair errors, so single steps of n
+    # can cancel; the trend over several terms cannot)
+    assert e[1] > 10 * e[2] > 1000 * e[5]
+    assert e[6] < 1e-11
+
+
+@pytest.mark.parametrize("keep", [-1, 2])
+def test_keep_preserves_kinetic_energy_and_pressure_equilibrium(keep):
+    """KEEP's momentum flux (mass flux times the mean velocity plus the mean
+    pressure) gives the split form's kinetic-energy identity
+    sum(u.R_mom - |u|^2/2 R_rho) = sum(p div_h u); with uniform velocity and
+    pressure and a varying density, the pressure stays uniform (dp/dt = 0),
+    which the split form with the total enthalpy does not give."""
+    n = (14, 12, 10)
+    p = _prob(n[0], n[1], n[2], mach=0.5, re=-1.0, weno_order=0, keep=keep)
+    w = W.smooth_periodic(*n, seed=21, mach=0.5, amp_u=0.7, amp_s=0.3)
+    r = O.rhs(p, w, terms=O.CONV)
+    rho = w[0]
+    u, v, ww = w[1] / rho, w[2] / rho, w[3] / rho
+    Rg = 1 / (1.4 * 0.25)
+    T = (w[4] / rho - 0.5 * (u * u + v * v + ww * ww)) / (Rg / 0.4)
+    pr = rho * Rg * T
+    h = [2 * np.pi / m for m in n]
+    lhs = np.sum(u * r[1] + v * r[2] + ww * r[3] - 0.5 * (u * u + v * v + ww * ww) * r[0])
+    div = _d1_periodic(u, 2, h[0]) + _d1_periodic(v, 1, h[1]) + _d1_periodic(ww, 0, h[2])
+    rhs_ = np.sum(pr * div)
+    scale = np.sum(np.abs(u * r[1])) + np.sum(np.abs(pr * div))
+    assert abs(lhs - rhs_) < 1e-13 * scale
+    # pressure equilibrium
+    shape = (n[2], n[1], n[0])
+    rng = np.random.default_rng(4)
+    x = np.arange(n[0]) * h[0]
+    rho2 = 1.0 + 0.3 * np.sin(x)[None, None, :] * np.ones(shape) + 0.05 * rng.uniform(-1, 1, shape)
+    U0 = [0.4 * np.ones(shape), -0.3 * np.ones(shape), 0.2 * np.ones(shape)]
+    w2 = W.conserved(rho2, *U0, 1.0 / rho2, 1.4, 0.5)  # p = R uniform
+    out = {}
+    for k in (keep, 0):
+        r2 = O.rhs(_prob(n[0], n[1], n[2], mach=0.5, re=-1.0, weno_order=0, keep=k), w2, terms=O.CONV)
+        # dp/dt = (gamma-1) (R_E - u . R_mom + |u|^2/2 R_rho) at uniform u
+        uu = [f[0, 0, 0] for f in U0]
+        dp = 0.4 * (r2[4] - uu[0] * r2[1] - uu[1] * r2[2] - uu[2] * r2[3] + 0.5 * sum(c * c for c in uu) * r2[0])
+        out[k] = np.max(np.abs(dp)) / np.max(np.abs(r2[4]))
+    # (dp/dt is a difference of terms each of the size of R_E: rounding
+    # level is ~1e-12 of it)
+    assert out[keep] < 1e-11
+    assert out[0] > 1e-6
+
+
+def test_keep_design_order_and_conservation(mms):
+    """KEEP is a consistent central scheme of the chosen order: R_h(w*) -
+    R(w*) falls as h^6 with the 6th-order coefficients (viscous terms
+    included); its flux form conserves mass, momentum and energy to
+    round-off on a stretched periodic box, with and without WENO."""
+    fields, rhs = mms
+    errs = []
+    for n in (16, 32):
+        xi = np.arange(n) * 2 * np.pi / n
+        Z, Y, X = np.meshgrid(xi, xi, xi, indexing="ij")
+        vals = [f(X, Y, Z) * np.ones_like(X) for f in fields]
+        w = W.conserved(*vals, 1.4, 0.5)
+        p = _prob(n, n, n, mach=0.5, re=100.0, prandtl=0.72, visc_exp=0.76, weno_order=0, keep=-1)
+        r = O.rhs(p, w)
+        ex = np.stack([g(X, Y, Z) * np.ones_like(X) for g in rhs])
+        errs.append(np.max(np.abs(r - ex), axis=(1, 2, 3)) / np.max(np.abs(ex), axis=(1, 2, 3)))
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(rates > 5.4), rates
+    xi = np.arange(14) * 2 * np.pi / 14
+    y = xi + 0.25 * np.sin(xi)
+    w = W.smooth_periodic(12, 14, 10, seed=5, mach=0.6, amp_u=0.8, amp_s=0.3)
+    for weno in (0, 5):
+        p = _prob(12, 14, 10, y=y, mach=0.6, re=-1.0, weno_order=weno, threshold=0.3, keep=-1)
+        r = O.rhs(p, w)
+        ey, _ = O.metric(p)
+        dv = (1.0 / ey)[None, None, :, None]
+        tot = np.sum(r * dv, axis=(1, 2, 3))
+        scale = np.sum(np.abs(r) * dv, axis=(1, 2, 3))
+        assert np.all(np.abs(tot) < 1e-13 * scale)
