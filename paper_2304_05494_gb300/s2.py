@@ -270,6 +270,13 @@ def s2_batch_create(handles, stream=None, mode: str = "worklist"):
     return b
 
 
+def s2_batch_create_ex(handles, stream=None, mode: int = S2_BATCH_WORKLIST):
+    """The C call with its integer mode (S2_BATCH_WORKLIST, S2_BATCH_BRANCHES
+    or S2_BATCH_WORKLIST_ALL)."""
+    name = {v: k for k, v in _BATCH_MODES.items()}[int(mode)]
+    return s2_batch_create(handles, stream, name)
+
+
 def s2_batch_launches(b) -> int:
     return int(_lib.s2_batch_launches(b))
 
