@@ -115,7 +115,7 @@ typedef struct {
 } s2_bcs;
 
 /* Scheme (paper Sec. 2: central schemes up to 8th order, WENO up to 7th).
- * central_order: 2, 4, 6 or 8 for the split-form convective flux;
+ * central_order: 2, 4, 6 or 8 for the central convective flux;
  * visc_order: 2, 4, 6 or 8 for the viscous terms and the sensor's
  * derivatives (the y metric uses the higher of the two).  weno_order: 0
  * (central everywhere), 1, 3, 5 or 7.  An interface is WENO iff the sensor's maximum over
@@ -123,13 +123,26 @@ typedef struct {
  * S2_MIXED (the sensor then decides in single precision).
  * dt: if cfl > 0 it is recomputed from the CFL condition (compute_dt of
  * Table 2) at every step whose counter is a multiple of dt_every and
- * frozen within a step; otherwise dt_fixed is used. */
+ * frozen within a step; otherwise dt_fixed is used.
+ * keep: the central flux (Sec. 2).  0: the energy-preserving split form
+ * (Pirozzoli 2010), two-point flux {rho}{u_n}{phi} with phi = 1, u, v, w,
+ * H.  n >= 1: KEEP-n, the kinetic-energy and entropy preserving flux of
+ * the same flux-differencing form with the two-point flux
+ * <rho>{u_n} (1, {u}, c_v/<1/T> + (u_a . u_b)/2) plus the pressure terms
+ * {p} n and (p_a u_n,b + p_b u_n,a)/2 ({.} arithmetic, <.> logarithmic
+ * means), its logarithmic means from the first n terms of their series in
+ * (a-b)/(a+b) (entropy error of order ((a-b)/(a+b))^2n per pair); -1:
+ * the same with exact logarithmic means (entropy conserved to rounding in
+ * smooth inviscid flow).  KEEP needs a calorically perfect gas (else
+ * S2_EINVAL).  A field at the end of the struct: code that zero-fills or
+ * omits it gets the split form. */
 typedef struct {
   int central_order, weno_order, visc_order;
   double sensor_threshold;
   int precision;
   double cfl, dt_fixed;
   int dt_every;
+  int keep;
 } s2_scheme;
 
 /* Device options.  alloc/free: optional allocator callbacks (device

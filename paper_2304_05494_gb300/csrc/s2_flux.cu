@@ -149,11 +149,15 @@ struct FluxLayout {
   static constexpr int NBUF = sizeof(R) == 4 ? (DIR == 0 ? 3 : 2) : 1;
 };
 
+// Dynamic shared memory of a flux CTA: barriers, staging buffers and the
+// pair fluxes (one mass flux per pair for the split form, the five
+// components of the two-point flux for KEEP).
 template <int DIR, bool HASW, class R, int TV, int NP>
-constexpr size_t flux_smem() {
+constexpr size_t flux_smem(bool keep = false) {
   using Ly = FluxLayout<DIR, R, TV>;
   constexpr int NFLD = HASW ? 7 : 6;
-  return Ly::BAR_BYTES + sizeof(R) * ((size_t)Ly::NBUF * NFLD * Ly::SFA + (size_t)NP * (Ly::L + NP) * Ly::W);
+  return Ly::BAR_BYTES +
+         sizeof(R) * ((size_t)Ly::NBUF * NFLD * Ly::SFA + (size_t)(keep ? 5 : 1) * NP * (Ly::L + NP) * Ly::W);
 }
 
 // CTAs walk the tiles of a direction (t = block index, + grid extent, ...).
@@ -256,6 +260,26 @@ __device__ __forceinline__ void flux_body(const FluxMaps &maps, const Dev &__res
     static_assert(SFA >= SF, "staging layout");
 
     // ---- 2. weighted pair mass fluxes m_l(a), a = -NP .. L-1 ----
+    // (KEEP: the five components of a_l f*(a, a+l) instead)
+    if (d.keep) {
+      for (int idx = tid; idx < ST; idx += NTHREADS) {
+        int a, cc;
+        if (DIR == 0) { a = idx % LT; cc = idx / LT; }
+        else { a = idx / W; cc = idx % W; }
+        const int q0 = (a - NP + GH) * SA + cc * SCS;
+        const R ra = S[F_RHO * SFA + q0], ua = S[F_U * SFA + q0], va = S[F_V * SFA + q0];
+        const R wa = S[F_W * SFA + q0], pa = S[F_P * SFA + q0];
+#pragma unroll
+        for (int l = 1; l <= NP; ++l) {
+          const int q1 = q0 + l * SA;
+          R f[5];
+          keep_pair<DIR, R>(ra, ua, va, wa, pa, S[F_RHO * SFA + q1], S[F_U * SFA + q1], S[F_V * SFA + q1],
+                            S[F_W * SFA + q1], S[F_P * SFA + q1], K.gamma - R(1), d.keep, f);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) TP[((l - 1) * 5 + c) * ST + a * SA + cc * SCT] = R(acoef<NP>(l)) * f[c];
+        }
+      }
+    } else
     for (int idx = tid; idx < ST; idx += NTHREADS) {
       int a, cc;                            // a in 0..LT-1 <-> position a-NP
       if (DIR == 0) { a = idx % LT; cc = idx / LT; }
@@ -326,6 +350,26 @@ __device__ __forceinline__ void flux_body(const FluxMaps &maps, const Dev &__res
     __syncthreads();
 
     // ---- 3. central flux difference of the thread's points -> RHS ----
+    if (d.keep) {
+      // KEEP: D = 2 sum_l [P_l(a) - P_l(a-l)], P_l the stored a_l f*
+#pragma unroll
+      for (int pp = 0; pp < PPT; ++pp) {
+        if (!mine[pp]) continue;
+        const int at = (ta[pp] + NP) * SA + tc * SCT;
+        const int pj = DIR == 0 ? y0 + tc : (DIR == 1 ? y0 + ta[pp] : y0);
+        if (DIR == 1 && !S2_OK_IDX(d, pj, d.ny)) continue;
+        const R scale2 = DIR == 0 ? K.idx2 : (DIR == 1 ? R(2) * __ldg(V.eta_y + pj) : K.idz2);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          R Dc = R(0);
+#pragma unroll
+          for (int l = 1; l <= NP; ++l) Dc += TP[((l - 1) * 5 + c) * ST + at] - TP[((l - 1) * 5 + c) * ST + at - l * SA];
+          V.fl[c * d.n + q[pp]] = fma(-scale2, Dc, prev[pp][c]);
+        }
+      }
+      __syncthreads();  // staging buffer and TP free for the next tile
+      continue;
+    }
 #pragma unroll
     for (int pp = 0; pp < PPT; ++pp) {
       if (!mine[pp]) continue;
@@ -526,11 +570,24 @@ __device__ __forceinline__ void weno_body(const Dev &__restrict__ d, const Blk &
           S2_OK_IDX(d, p0 + 4 * stride, d.np)))
       continue;
 
-    // --- central split-form flux at this interface (order 2 npc)
+    // --- central flux at this interface (order 2 npc): split form, or KEEP
     R FC[5] = {R(0), R(0), R(0), R(0), R(0)}, fp = R(0);
+    if (d.keep) {
+      for (int l = 1; l <= d.npc; ++l)
+        for (int m = 0; m < l; ++m) {
+          const long long a = p0 - m * stride, b = p0 + (l - m) * stride;
+          R f[5];
+          keep_pair<DIR, R>(__ldg(V.rho + a), __ldg(V.u + a), __ldg(V.v + a), __ldg(V.ww + a), __ldg(V.p + a),
+                            __ldg(V.rho + b), __ldg(V.u + b), __ldg(V.v + b), __ldg(V.ww + b), __ldg(V.p + b),
+                            K.gamma - R(1), d.keep, f);
+          const R al2 = R(2) * K.acen[l];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) FC[c] = fma(al2, f[c], FC[c]);
+        }
+    }
 #pragma unroll
     for (int l = 1; l <= 4; ++l) {
-      if (l > d.npc) break;
+      if (l > d.npc || d.keep) break;
       R acc[5] = {R(0), R(0), R(0), R(0), R(0)}, ps = R(0);
 #pragma unroll
       for (int m = 0; m < l; ++m) {
@@ -665,19 +722,21 @@ __global__ void __launch_bounds__(WENO_NT) kb_weno(BatchArgs ba) {
 // that unit busy (measured faster than the persistent loop).
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaStream_t st) {
-  static int per_sm = 0;  // resident CTAs per multiprocessor (per instantiation)
-  if (per_sm == 0) {
+  static int per_sm[2] = {0, 0};  // resident CTAs per multiprocessor (per instantiation; split form, KEEP)
+  const int kp = d.keep != 0;
+  const size_t smem = flux_smem<DIR, HASW, R, TV, NP>(kp);
+  if (per_sm[kp] == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flux<DIR, HASW, R, TV, NP>, NTHREADS,
-                                                      flux_smem<DIR, HASW, R, TV, NP>()) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flux<DIR, HASW, R, TV, NP>, NTHREADS, smem) !=
+            cudaSuccess ||
         b < 1)
       b = 1;
-    per_sm = b;
+    per_sm[kp] = b;
   }
   const TileGrid<DIR, TV, R> tg(d);
   const int ntiles = tg.count();
-  const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm * d.nsm ? ntiles : per_sm * d.nsm);
-  k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(maps, d, tg, accumulate);
+  const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm[kp] * d.nsm ? ntiles : per_sm[kp] * d.nsm);
+  k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, smem, st>>>(maps, d, tg, accumulate);
   return cudaGetLastError();
 }
 
@@ -715,10 +774,11 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
 
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t set_attr_one() {
+  // the larger (KEEP) size; a launch passes the size its scheme needs
   cudaError_t e = cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)flux_smem<DIR, HASW, R, TV, NP>());
+                                       (int)flux_smem<DIR, HASW, R, TV, NP>(true));
   cudaError_t e2 = cudaFuncSetAttribute(kb_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)flux_smem<DIR, HASW, R, TV, NP>());
+                                        (int)flux_smem<DIR, HASW, R, TV, NP>(true));
   return e != cudaSuccess ? e : e2;
 }
 
@@ -892,21 +952,22 @@ struct FluxPlan {
   FluxBoxPlan &out;
   template <int DIR, bool HASW, class R, int TV, int NP>
   cudaError_t run() {
-    static int per_sm = 0;  // resident CTAs per multiprocessor of the batched kernel
-    if (per_sm == 0) {
+    static int per_sm[2] = {0, 0};  // resident CTAs per multiprocessor of the batched kernel
+    const int kp = d.keep != 0;
+    if (per_sm[kp] == 0) {
       int b = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flux<DIR, HASW, R, TV, NP>, NTHREADS,
-                                                        flux_smem<DIR, HASW, R, TV, NP>()) != cudaSuccess ||
+                                                        flux_smem<DIR, HASW, R, TV, NP>(kp)) != cudaSuccess ||
           b < 1)
         b = 1;
-      per_sm = b;
+      per_sm[kp] = b;
     }
     const TileGrid<DIR, TV, R> tg(d);
     static_assert(sizeof(tg) <= sizeof(out.tg), "tile grid record");
     memcpy(out.tg, &tg, sizeof(tg));
     out.tg_size = (int)sizeof(tg);
     out.tiles = tg.count();
-    out.per_sm = per_sm;
+    out.per_sm = per_sm[kp];
     out.persistent = sizeof(R) == 4;
     return cudaSuccess;
   }
@@ -914,6 +975,7 @@ struct FluxPlan {
 
 struct FluxBatchLaunch {
   const BatchArgs &ba;
+  bool keep;
   unsigned total;
   const FluxMaps *maps;
   const void *tgs;
@@ -921,7 +983,7 @@ struct FluxBatchLaunch {
   cudaStream_t st;
   template <int DIR, bool HASW, class R, int TV, int NP>
   cudaError_t run() {
-    kb_flux<DIR, HASW, R, TV, NP><<<total, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(), st>>>(
+    kb_flux<DIR, HASW, R, TV, NP><<<total, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(keep), st>>>(
         ba, maps, (const TileGrid<DIR, TV, R> *)tgs, accumulate);
     return cudaGetLastError();
   }
@@ -966,7 +1028,7 @@ unsigned weno_batch_blocks(const Dev &d, int dir) {
 
 cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total, const FluxMaps *maps,
                               const void *tgs, int dir, int accumulate, cudaStream_t st) {
-  FluxBatchLaunch f{ba, total, maps, tgs, accumulate, st};
+  FluxBatchLaunch f{ba, d0.keep != 0, total, maps, tgs, accumulate, st};
   return flux_select(d0, dir, f);
 }
 

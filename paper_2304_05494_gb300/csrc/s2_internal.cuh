@@ -96,6 +96,7 @@ struct Dev {
   double ax[5], az[5];     // a_l/dx, a_l/dz (first derivative, viscous order, l = 1..4)
   double bx[5], bz[5];     // b_l/dx^2, b_l/dz^2 (second derivative, viscous order, l = 0..4)
   int npc, npv;            // stencil pairs of the central and the viscous order (order / 2)
+  int keep;                // central flux: 0 split form; n >= 1 KEEP-n; -1 KEEP with exact log means
   double R, cv, icv, cp, gamma, prandtl, re, visc_exp, inv_t_ref, t_wall, cp_over_pr;
   double inv_re;           // 1 / Re
   float visc_exp_f;        // omega in single precision (seed of the viscosity law)
@@ -482,6 +483,45 @@ __device__ __forceinline__ double spectral_radius(const Dev &d, double rho, doub
   double sr = (fabs(u) + cs) / d.dx + (fabs(v) + cs) * ey + (fabs(ww) + cs) / d.dz;
   if (d.viscous) sr += gam * mu / (d.prandtl * rho) * (1.0 / (d.dx * d.dx) + ey * ey + 1.0 / (d.dz * d.dz));
   return sr;
+}
+
+// Logarithmic mean (a - b) / (ln a - ln b) of a, b > 0, the averages of
+// the KEEP-n flux: from the first n terms of its series in z = (a-b)/(a+b),
+// <a,b> = (a+b)/2 / sum_{k<n} z^2k/(2k+1); n < 0: exactly, as the
+// quotient of logarithms unless z^2 is small, where the series is summed
+// below rounding (6 terms in double, 4 in single precision).
+template <class R>
+__device__ __forceinline__ R log_mean(R a, R b, int n) {
+  const R s = a + b, z = (a - b) / s, u = z * z;
+  if (n < 0) {
+    if (u > (sizeof(R) == 8 ? R(1e-4) : R(1e-2))) return (a - b) / tp_log(a / b);
+    n = sizeof(R) == 8 ? 6 : 4;
+  }
+  R F = R(0), zk = R(1);
+  for (int k = 0; k < n; ++k) {
+    F += zk / R(2 * k + 1);
+    zk *= u;
+  }
+  return R(0.5) * s / F;
+}
+
+// KEEP-n two-point flux of the points a and b along the direction with
+// normal velocity un: <rho>{u_n} (1, {u}, e~ + (u_a . u_b)/2) + ({p} n,
+// (p_a un_b + p_b un_a)/2), e~ = 1/((gamma-1) <rho/p>) (c_v/<1/T> of the
+// ideal gas).  f[0..4].
+template <int DIR, class R>
+__device__ __forceinline__ void keep_pair(R ra, R ua, R va, R wa, R pa, R rb, R ub, R vb, R wb, R pb, R gm1, int n,
+                                          R *f) {
+  const R una = DIR == 0 ? ua : (DIR == 1 ? va : wa), unb = DIR == 0 ? ub : (DIR == 1 ? vb : wb);
+  const R rl = log_mean(ra, rb, n), bl = log_mean(ra / pa, rb / pb, n);
+  const R fr = rl * (R(0.5) * (una + unb));
+  f[0] = fr;
+  f[1] = fr * (R(0.5) * (ua + ub));
+  f[2] = fr * (R(0.5) * (va + vb));
+  f[3] = fr * (R(0.5) * (wa + wb));
+  f[1 + DIR] += R(0.5) * (pa + pb);
+  const R uab = ua * ub + va * vb + wa * wb;
+  f[4] = fr * (R(1) / (gm1 * bl) + R(0.5) * uab) + R(0.5) * (pa * unb + pb * una);
 }
 
 // Slot of the interface between points s and s+1 (s = -1 .. n_d - 1) of

@@ -1126,6 +1126,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
       scheme->weno_order != 7)
     return S2_EINVAL;
   if (scheme->precision != S2_FP64 && scheme->precision != S2_MIXED) return S2_EINVAL;
+  if (scheme->keep < -1 || scheme->keep > 16 || (scheme->keep != 0 && gas->cp_coeffs)) return S2_EINVAL;
   if (!(scheme->cfl > 0) && !(scheme->dt_fixed > 0)) return S2_EINVAL;
   if (check_gas(gas, bcs->y == S2_BC_ISOTHERMAL_WALL ? bcs->t_wall : 0.0) != S2_OK) return S2_EINVAL;
   long long n = (long long)grid->nx * grid->ny * grid->nz;
@@ -1226,6 +1227,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   d.idx = 1.0 / d.dx;
   d.idz = 1.0 / d.dz;
   d.npc = scheme->central_order / 2;
+  d.keep = scheme->keep;
   d.npv = scheme->visc_order / 2;
   for (int l = 0; l <= 4; ++l) {
     d.ax[l] = l ? A1_ORD[d.npv][l] / d.dx : 0.0;
@@ -1843,7 +1845,11 @@ int group_setup(BatchGroup &g) {
   memcpy(host.data() + o_nf, nforce.data(), sizeof(int) * n);
   g.mem = batch_alloc(g.members[0], off);
   if (!g.mem) return S2_ENOMEM;
-  if (cudaMemcpy(g.mem, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) return S2_ECUDA;
+  // on the group's (idle) stream: a legacy-stream copy would wait for
+  // unrelated work on blocking streams
+  if (cudaMemcpyAsync(g.mem, host.data(), off, cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
+      cudaStreamSynchronize(g.stream) != cudaSuccess)
+    return S2_ECUDA;
   unsigned char *base = (unsigned char *)g.mem;
   for (int dir = 0; dir < 3; ++dir) {
     g.maps[dir] = (FluxMaps *)(base + o_maps[dir]);

@@ -54,7 +54,7 @@ class s2_bcs(C.Structure):
 class s2_scheme(C.Structure):
     _fields_ = [("central_order", C.c_int), ("weno_order", C.c_int), ("visc_order", C.c_int),
                 ("sensor_threshold", C.c_double), ("precision", C.c_int), ("cfl", C.c_double),
-                ("dt_fixed", C.c_double), ("dt_every", C.c_int)]
+                ("dt_fixed", C.c_double), ("dt_every", C.c_int), ("keep", C.c_int)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -338,7 +338,7 @@ class Solver:
     def __init__(self, nx, ny, nz, lx, ly, lz, *, y=None, gamma=1.4, prandtl=0.72, mach=0.1, re=1600.0,
                  visc_exp=0.76, t_ref=1.0, wall_y=False, t_wall=1.0, force=False, weno_order=0,
                  threshold=0.2, cfl=0.8, dt_fixed=0.0, dt_every=10, stream=None, device=-1, precision="fp64",
-                 central_order=6, visc_order=6, cp_coeffs=None):
+                 central_order=6, visc_order=6, cp_coeffs=None, keep=0):
         self.shape = (5, nz, ny, nx)
         self.n = nx * ny * nz
         grid = s2_grid(nx, ny, nz, lx, ly, lz)
@@ -357,7 +357,7 @@ class Solver:
         bcs = s2_bcs(S2_BC_PERIODIC, S2_BC_ISOTHERMAL_WALL if wall_y else S2_BC_PERIODIC, S2_BC_PERIODIC,
                      t_wall, 1 if force else 0)
         prec = {"fp64": S2_FP64, "mixed": S2_MIXED}[precision]
-        sch = s2_scheme(central_order, weno_order, visc_order, threshold, prec, cfl, dt_fixed, dt_every)
+        sch = s2_scheme(central_order, weno_order, visc_order, threshold, prec, cfl, dt_fixed, dt_every, keep)
         dev = s2_device()
         dev.stream = stream
         dev.device = device

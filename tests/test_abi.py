@@ -58,6 +58,7 @@ def test_strerror_and_invalid_arguments(lib):
     assert create(b__y=1, g__ny=2) == s2.S2_EINVAL         # walls need ny >= 4
     assert create(sch__weno_order=4) == s2.S2_EINVAL
     assert create(sch__central_order=5) == s2.S2_EINVAL
+    assert create(sch__keep=-2) == s2.S2_EINVAL             # KEEP-n: n >= 1, or -1 for exact means
     assert create(sch__visc_order=10) == s2.S2_EINVAL
     assert create(sch__cfl=0.0, sch__dt_fixed=0.0) == s2.S2_EINVAL
     assert create(gas__gamma=1.0) == s2.S2_EINVAL

@@ -66,6 +66,20 @@ def test_mixed_rhs_tgv_and_channel(s2):
     assert flips <= 1e-3 * total
 
 
+@pytest.mark.parametrize("weno", [0, 5])
+def test_mixed_rhs_keep(s2, weno):
+    """KEEP central flux (exact logarithmic means) in single precision
+    against the FP64 oracle, central and hybrid."""
+    nx, ny, nz = 37, 29, 19
+    L = 2 * np.pi
+    w0 = W.smooth_periodic(nx, ny, nz, seed=81, mach=0.7, amp_u=0.7, amp_s=0.25)
+    xi = np.arange(ny) * L / ny
+    kw = dict(y=xi + 0.25 * np.sin(xi), mach=0.7, re=150.0, weno_order=weno, threshold=0.15, keep=-1)
+    e, flips, total = mixed_rhs_err(s2, w0, (nx, ny, nz, L, L, L), kw)
+    assert np.all(e < MIX_RHS_TOL), e
+    assert flips <= 1e-3 * total
+
+
 @pytest.mark.parametrize("weno", [5, 7])
 def test_mixed_rhs_ragged_hybrid(s2, weno):
     nx, ny, nz = 37, 29, 19

@@ -72,7 +72,7 @@ def make(s2, nx, ny, nz, lx, ly, lz, **kw):
     sk = dict(kw)
     ok = {k: v for k, v in kw.items() if k in ("y", "gamma", "prandtl", "mach", "re", "visc_exp", "t_ref",
                                                "wall_y", "t_wall", "force", "weno_order", "threshold",
-                                               "central_order", "visc_order")}
+                                               "central_order", "visc_order", "keep")}
     return s2.Solver(nx, ny, nz, lx, ly, lz, **sk), O.Problem(nx, ny, nz, lx, ly, lz, **ok)
 
 
@@ -319,6 +319,67 @@ def test_scheme_variants_channel_10_steps(s2, orders):
     err = field_err(w, ref)
     print("orders %s: state error after 10 steps" % (orders,), err)
     assert np.all(err < STEP_TOL), err
+
+
+@pytest.mark.parametrize("keep,orders", [(-1, (6, 6, 0)), (-1, (8, 6, 5)), (3, (6, 6, 7)), (1, (4, 4, 0)),
+                                         (-1, (2, 2, 3))])
+def test_keep_rhs_parity(s2, keep, orders):
+    """KEEP-n central flux (exact logarithmic means, and n = 1, 3 series
+    terms), central only and hybrid with WENO, on a ragged stretched
+    periodic grid: RHS and flags match the oracle."""
+    co, vo, wo = orders
+    nx, ny, nz = 37, 29, 19
+    L = 2 * np.pi
+    w0 = W.smooth_periodic(nx, ny, nz, seed=70 + co + wo, mach=0.7, amp_u=0.7, amp_s=0.25)
+    xi = np.arange(ny) * L / ny
+    kw = dict(y=xi + 0.25 * np.sin(xi), mach=0.7, re=150.0, weno_order=wo, threshold=0.15,
+              central_order=co, visc_order=vo, keep=keep)
+    e, f, of = rhs_parity(s2, w0, nx, ny, nz, L, L, L, **kw)
+    assert np.all(e < RHS_TOL), e
+    if wo:
+        for a, b in zip(f, of):
+            assert np.array_equal(a, b)
+
+
+def test_keep_channel_10_steps_and_entropy(s2):
+    """KEEP with walls, stretched y, forcing and hybrid WENO5: states after
+    10 steps match the oracle.  Inviscid, central and periodic, the GPU's
+    RHS conserves the entropy -rho s/(gamma-1) to rounding (sum of v . R dV,
+    v the entropy variables), as the oracle's does."""
+    c = W.channel(48, 40, 24, seed=13)
+    kw = case_kw(c)
+    kw.update(weno_order=5, threshold=0.05, keep=-1)
+    sv, pr = make(s2, c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, cfl=0.8, dt_every=10, **kw)
+    with sv:
+        sv.set_state(c.w0)
+        sv.step(10)
+        w = sv.get_state()
+    ref, _, _ = O.step(pr, c.w0, 10, cfl=0.8, dt_every=10)
+    err = field_err(w, ref)
+    print("KEEP channel: state error after 10 steps", err)
+    assert np.all(err < STEP_TOL), err
+    # entropy of the inviscid central GPU RHS
+    nx, ny, nz = 30, 26, 22
+    L = 2 * np.pi
+    xi = np.arange(ny) * L / ny
+    y = xi + 0.25 * np.sin(xi)
+    w0 = W.smooth_periodic(nx, ny, nz, seed=41, mach=0.5, amp_u=0.6, amp_s=0.3)
+    sv, pr = make(s2, nx, ny, nz, L, L, L, cfl=0.0, dt_fixed=1e-3, y=y, mach=0.5, re=-1.0, weno_order=0, keep=-1)
+    with sv:
+        sv.set_state(w0)
+        r = sv.rhs()
+    rho = w0[0]
+    u, v, ww = w0[1] / rho, w0[2] / rho, w0[3] / rho
+    q2 = u * u + v * v + ww * ww
+    p = 0.4 * (w0[4] - 0.5 * rho * q2)
+    s = np.log(p) - 1.4 * np.log(rho)
+    b = rho / p
+    ev = np.stack([(1.4 - s) / 0.4 - 0.5 * b * q2, b * u, b * v, b * ww, -b])
+    ey, _ = O.metric(pr)
+    prod = np.sum(ev * r, axis=0) * (1.0 / ey)[None, :, None]
+    rel = abs(np.sum(prod)) / np.sum(np.abs(prod))
+    print("KEEP entropy production of the GPU RHS (relative):", rel)
+    assert rel < 1e-12
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
