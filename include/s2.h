@@ -229,6 +229,27 @@ int s2_sync(s2_solver *s);
  * do not depend on it. */
 int s2_set_tiles(s2_solver *s, const int *tiles);
 
+/* Launch shape of the kernels, the knobs of the paper's block-shape study
+ * (Table 3) and of its translator's configuration (Sec. 3.3), searched by
+ * the autotuner (paper_2304_05494_gb300/autotune.py).  tiles: as
+ * s2_set_tiles.  flux_ctas_per_sm: CTAs per multiprocessor of the
+ * persistent single-precision flux grids (0: as many as fit, up to 16).
+ * z_planes: z-planes each CTA of the mixed path's z-marching gradient and
+ * viscous passes walks (0: 12; else 4..64).  weno_ctas_per_sm: cap of the
+ * WENO kernels' 64-thread CTAs per multiprocessor (0: 16; else 1..64).
+ * Takes effect at the next s2_step; results do not depend on it, except
+ * that with channel forcing in S2_MIXED the viscous pass sums the forcing
+ * per CTA, so z_planes changes the order of that sum (single-precision
+ * rounding). */
+typedef struct {
+  int tiles[3];
+  int flux_ctas_per_sm;
+  int z_planes;
+  int weno_ctas_per_sm;
+} s2_tuning;
+int s2_set_tuning(s2_solver *s, const s2_tuning *t);
+int s2_get_tuning(const s2_solver *s, s2_tuning *t);
+
 /* Restore the clock (for a restart from a saved state). */
 int s2_set_clock(s2_solver *s, double t, long long step, double dt);
 

@@ -735,7 +735,8 @@ cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaS
   }
   const TileGrid<DIR, TV, R> tg(d);
   const int ntiles = tg.count();
-  const int nb = sizeof(R) == 8 ? ntiles : (ntiles < per_sm[kp] * d.nsm ? ntiles : per_sm[kp] * d.nsm);
+  const int cps = d.flux_cps > 0 && d.flux_cps < per_sm[kp] ? d.flux_cps : per_sm[kp];
+  const int nb = sizeof(R) == 8 ? ntiles : (ntiles < cps * d.nsm ? ntiles : cps * d.nsm);
   k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, smem, st>>>(maps, d, tg, accumulate);
   return cudaGetLastError();
 }
@@ -765,7 +766,7 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
   // small CTAs: the flagged interfaces (a device-side count, often a few
   // per cent of the slots) then spread evenly over the multiprocessors
   long long need = (d.nslot[DIR] + WENO_NT - 1) / WENO_NT;
-  long long cap = 16LL * sms;
+  long long cap = (long long)(d.weno_cps > 0 ? d.weno_cps : 16) * sms;
   unsigned nb = (unsigned)(need < cap ? need : cap);
   if (nb == 0) nb = 1;
   k_weno<DIR, WR, R><<<nb, WENO_NT, 0, st>>>(d);
@@ -967,7 +968,7 @@ struct FluxPlan {
     memcpy(out.tg, &tg, sizeof(tg));
     out.tg_size = (int)sizeof(tg);
     out.tiles = tg.count();
-    out.per_sm = per_sm[kp];
+    out.per_sm = d.flux_cps > 0 && d.flux_cps < per_sm[kp] ? d.flux_cps : per_sm[kp];
     out.persistent = sizeof(R) == 4;
     return cudaSuccess;
   }
@@ -1022,7 +1023,7 @@ unsigned weno_batch_blocks(const Dev &d, int dir) {
   // as the single-box launch: enough 64-thread CTAs for every slot, at
   // most 16 per multiprocessor (the list length is known on the device only)
   long long need = (d.nslot[dir] + WENO_NT - 1) / WENO_NT;
-  long long cap = 16LL * d.nsm;
+  long long cap = (long long)(d.weno_cps > 0 ? d.weno_cps : 16) * d.nsm;
   return (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
 }
 

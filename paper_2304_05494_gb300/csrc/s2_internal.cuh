@@ -110,6 +110,9 @@ struct Dev {
   int viscous, wall_y, weno, force;
   int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
   int tile[3];             // flux tile variant per direction (0 default, 1 narrow)
+  int flux_cps;            // single-precision flux grids: resident CTAs per SM to use (0: all that fit)
+  int zs;                  // planes per CTA of the z-marching passes (mixed path)
+  int weno_cps;            // WENO grids: CTAs per SM
   int nsm;                 // multiprocessors of the device
   unsigned long long wait_ns;  // limit of a kernel's wait for an asynchronous copy
   unsigned tx_extra;       // bytes a staging barrier expects beyond its copies (0; test hook)
@@ -649,6 +652,9 @@ cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total
 cudaError_t launch_weno_batch(const Dev &d0, const BatchArgs &ba, unsigned total, int dir, cudaStream_t st);
 // z-marching passes of the mixed path: grid of one box (x, y, z blocks)
 void z_pass_grid(const Dev &d, unsigned g[3]);
+// Smallest planes per CTA of the z-marching passes s2_set_tuning accepts
+// (the forcing partials are sized for it).
+constexpr int ZS_MIN = 4, ZS_MAX = 64, ZS_DEFAULT = 12;
 cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
 cudaError_t launch_visc_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
 cudaError_t launch_apply_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);

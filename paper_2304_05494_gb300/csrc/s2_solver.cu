@@ -1249,6 +1249,9 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   // 256 x 128 x 128 channel)
   d.tile[0] = 0;
   d.tile[1] = d.tile[2] = d.mixed;
+  d.flux_cps = 0;
+  d.zs = ZS_DEFAULT;
+  d.weno_cps = 16;
   // scheme constants in both arithmetic types
   {
     Consts<double> &k = d.kd;
@@ -1337,7 +1340,11 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   if (!etaf || !ayf || !byf || !ryf) ok = false;
   size_t nparts = (size_t)((n + NT - 1) / NT);
   if (nparts < (size_t)NRED * NSTAT) nparts = (size_t)NRED * NSTAT;
-  if (nparts < (size_t)z_pass_blocks(d)) nparts = (size_t)z_pass_blocks(d);  // forcing partials of k_visc_z
+  {  // forcing partials of k_visc_z, for the smallest tunable plane count
+    Dev dz = d;
+    dz.zs = ZS_MIN;
+    if (nparts < (size_t)z_pass_blocks(dz)) nparts = (size_t)z_pass_blocks(dz);
+  }
   d.part = A(nparts);
   d.nparts = (long long)nparts;
   d.scal = (Scal *)dalloc(s, sizeof(Scal));
@@ -1524,6 +1531,35 @@ int s2_sync(s2_solver *s) {
   if (!s) return S2_EINVAL;
   DeviceGuard guard(s->device);
   return read_status(s);
+}
+
+int s2_set_tuning(s2_solver *s, const s2_tuning *t) {
+  if (!s || !t) return S2_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (t->tiles[a] != 0 && t->tiles[a] != 1) return S2_EINVAL;
+  if (t->flux_ctas_per_sm < 0 || t->flux_ctas_per_sm > 16) return S2_EINVAL;
+  if (t->z_planes != 0 && (t->z_planes < ZS_MIN || t->z_planes > ZS_MAX)) return S2_EINVAL;
+  if (t->weno_ctas_per_sm < 0 || t->weno_ctas_per_sm > 64) return S2_EINVAL;
+  DeviceGuard guard(s->device);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
+  for (int a = 0; a < 3; ++a) s->d.tile[a] = t->tiles[a];
+  s->d.flux_cps = t->flux_ctas_per_sm;
+  s->d.zs = t->z_planes ? t->z_planes : ZS_DEFAULT;
+  s->d.weno_cps = t->weno_ctas_per_sm ? t->weno_ctas_per_sm : 16;
+  if (s->graph_ready) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph_ready = false;
+  }
+  return S2_OK;
+}
+
+int s2_get_tuning(const s2_solver *s, s2_tuning *t) {
+  if (!s || !t) return S2_EINVAL;
+  for (int a = 0; a < 3; ++a) t->tiles[a] = s->d.tile[a];
+  t->flux_ctas_per_sm = s->d.flux_cps;
+  t->z_planes = s->d.zs;
+  t->weno_ctas_per_sm = s->d.weno_cps;
+  return S2_OK;
 }
 
 int s2_set_tiles(s2_solver *s, const int *tiles) {

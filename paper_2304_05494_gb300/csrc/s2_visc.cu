@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(NT) kb_visc(BatchArgs ba) {
 // The single-precision path is bound by memory traffic, not arithmetic, so
 // its gradient and viscous kernels march through z instead of giving each
 // point its own 3-D stencil gathers.  A CTA owns a ZTX x ZTY tile of x-y
-// columns over ZS consecutive z-planes.  Per plane, the fields are staged
+// columns over d.zs consecutive z-planes.  Per plane, the fields are staged
 // once in shared memory with an NP-point x-y halo (x and y derivatives);
 // along z each thread keeps its column's 2 NP + 1 values in registers
 // (z derivatives).  The next plane's column values and halo values are
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NT) kb_visc(BatchArgs ba) {
 // double-buffered, so one barrier per plane suffices.  The viscous pass
 // recomputes the velocity gradients from the staged values rather than
 // reading nine stored ones.
-constexpr int ZTX = 32, ZTY = 8, ZS = 12;
+constexpr int ZTX = 32, ZTY = 8;  // x-y tile; d.zs planes per CTA (tunable)
 
 template <int NP>
 struct ZGeom {
@@ -383,8 +383,8 @@ struct ZTile {
     const int tid = threadIdx.x;
     x0 = B.x * ZTX;
     y0 = B.y * ZTY;
-    z0 = B.z * ZS;
-    z1 = min(z0 + ZS, d.nz);
+    z0 = B.z * d.zs;
+    z1 = min(z0 + d.zs, d.nz);
     i = x0 + tid % ZTX;
     j = y0 + tid / ZTX;
     active = i < d.nx && j < d.ny;
@@ -675,7 +675,7 @@ void visc_np(const Dev &d, unsigned nb, cudaStream_t st) {
 }  // namespace
 
 static dim3 zgrid(const Dev &d) {
-  return dim3((d.nx + ZTX - 1) / ZTX, (d.ny + ZTY - 1) / ZTY, (d.nz + ZS - 1) / ZS);
+  return dim3((d.nx + ZTX - 1) / ZTX, (d.ny + ZTY - 1) / ZTY, (d.nz + d.zs - 1) / d.zs);
 }
 
 cudaError_t launch_grad(const Dev &d, cudaStream_t st) {

@@ -57,6 +57,11 @@ class s2_scheme(C.Structure):
                 ("dt_fixed", C.c_double), ("dt_every", C.c_int), ("keep", C.c_int)]
 
 
+class s2_tuning(C.Structure):
+    _fields_ = [("tiles", C.c_int * 3), ("flux_ctas_per_sm", C.c_int), ("z_planes", C.c_int),
+                ("weno_ctas_per_sm", C.c_int)]
+
+
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -121,6 +126,10 @@ def _load():
     lib.s2_batch_destroy.restype = None
     lib.s2_set_tiles.argtypes = [P, C.POINTER(C.c_int)]
     lib.s2_set_tiles.restype = C.c_int
+    lib.s2_set_tuning.argtypes = [P, C.POINTER(s2_tuning)]
+    lib.s2_set_tuning.restype = C.c_int
+    lib.s2_get_tuning.argtypes = [P, C.POINTER(s2_tuning)]
+    lib.s2_get_tuning.restype = C.c_int
     lib.s2_strerror.argtypes = [C.c_int]
     lib.s2_strerror.restype = C.c_char_p
     for f in ("s2_set_state", "s2_get_state", "s2_step", "s2_sync", "s2_set_clock", "s2_stats", "s2_rhs",
@@ -204,6 +213,19 @@ def s2_set_clock(h, t: float, step: int, dt: float) -> None:
 def s2_set_tiles(h, tiles) -> None:
     arr = (C.c_int * 3)(*[int(t) for t in tiles])
     _check(_lib.s2_set_tiles(h, arr), "s2_set_tiles")
+
+
+def s2_set_tuning(h, tiles=(0, 0, 0), flux_ctas_per_sm=0, z_planes=0, weno_ctas_per_sm=0) -> None:
+    t = s2_tuning((C.c_int * 3)(*[int(x) for x in tiles]), int(flux_ctas_per_sm), int(z_planes),
+                  int(weno_ctas_per_sm))
+    _check(_lib.s2_set_tuning(h, C.byref(t)), "s2_set_tuning")
+
+
+def s2_get_tuning(h) -> dict:
+    t = s2_tuning()
+    _check(_lib.s2_get_tuning(h, C.byref(t)), "s2_get_tuning")
+    return {"tiles": list(t.tiles), "flux_ctas_per_sm": t.flux_ctas_per_sm, "z_planes": t.z_planes,
+            "weno_ctas_per_sm": t.weno_ctas_per_sm}
 
 
 def s2_stats(h) -> dict:
@@ -341,6 +363,7 @@ class Solver:
                  central_order=6, visc_order=6, cp_coeffs=None, keep=0):
         self.shape = (5, nz, ny, nx)
         self.n = nx * ny * nz
+        self.precision = precision
         grid = s2_grid(nx, ny, nz, lx, ly, lz)
         self._y = None
         met = s2_metrics()
@@ -407,6 +430,15 @@ class Solver:
 
     def set_tiles(self, tiles):
         s2_set_tiles(self.h, tiles)
+
+    def set_tuning(self, **knobs):
+        """tiles, flux_ctas_per_sm, z_planes, weno_ctas_per_sm (see s2_tuning)."""
+        cur = s2_get_tuning(self.h)
+        cur.update(knobs)
+        s2_set_tuning(self.h, **cur)
+
+    def get_tuning(self) -> dict:
+        return s2_get_tuning(self.h)
 
     def set_clock(self, t, step, dt):
         s2_set_clock(self.h, t, step, dt)

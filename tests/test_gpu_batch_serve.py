@@ -166,14 +166,52 @@ def test_tile_variants_give_identical_results(s2, precision):
 def test_autotuner_caches_a_choice(s2, tmp_path):
     from paper_2304_05494_gb300 import autotune
     c = W.taylor_green(32)
+    c.weno_order, c.threshold = 5, 0.1
     path = str(tmp_path / "tiles.json")
     with s2.Solver.from_case(c, precision="mixed") as sv:
-        tiles = autotune.tiles_for(sv, c.w0, (c.nx, c.ny, c.nz), "mixed", 0, path=path, steps=2)
-        assert all(t in (0, 1) for t in tiles)
+        t = autotune.tuning_for(sv, c.w0, (c.nx, c.ny, c.nz), "mixed", 5, path=path, steps=2)
+        assert all(x in (0, 1) for x in t["tiles"])
+        assert t["flux_ctas_per_sm"] in autotune.FLUX_CTAS and t["z_planes"] in autotune.Z_PLANES
+        assert t["weno_ctas_per_sm"] in autotune.WENO_CTAS
+        assert sv.get_tuning() == t
         sv.step(1)  # the solver still runs after tuning
         sv.sync()
     cache = autotune.load_cache(path)
-    assert len(cache) == 1 and list(cache.values())[0]["tiles"] == tiles
+    assert len(cache) == 1 and list(cache.values())[0]["tuning"] == t
+    # a second solver of the same class takes the cached choice without tuning
+    with s2.Solver.from_case(c, precision="mixed") as sv:
+        assert autotune.tiles_for(sv, c.w0, (c.nx, c.ny, c.nz), "mixed", 5, path=path) == t["tiles"]
+        assert sv.get_tuning() == t
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_launch_knobs_give_identical_results(s2, precision):
+    """CTAs per SM of the flux and WENO grids and z-planes per CTA of the
+    z-marching passes change the launch shape, not the results.  The one
+    exception: with channel forcing in single precision, the viscous
+    z-pass sums the bulk forcing per CTA, so the plane count changes the
+    order of that sum (results then agree to single-precision rounding)."""
+    def run(c, **knobs):
+        with s2.Solver.from_case(c, cfl=0.8, threshold=0.05, precision=precision) as sv:
+            if knobs:
+                sv.set_tuning(**knobs)
+            sv.set_state(c.w0)
+            sv.step(3)
+            return sv.get_state()
+
+    chan = W.channel(40, 36, 30, seed=2)
+    ref = run(chan)
+    for knobs in (dict(flux_ctas_per_sm=1, weno_ctas_per_sm=4), dict(flux_ctas_per_sm=3, weno_ctas_per_sm=32)):
+        assert np.array_equal(ref, run(chan, **knobs)), knobs
+    zc = run(chan, z_planes=7)
+    if precision == "fp64":
+        assert np.array_equal(ref, zc)
+    else:
+        assert field_err(zc, ref) < 1e-6
+    box = W.isotropic(24, mach_t=0.6, seed=3, weno_order=5)
+    refb = run(box)
+    for knobs in (dict(z_planes=4, flux_ctas_per_sm=2), dict(z_planes=48, weno_ctas_per_sm=8), dict(z_planes=7)):
+        assert np.array_equal(refb, run(box, **knobs)), knobs
 
 
 def test_serving_results_same_alone_and_in_the_mix(s2):

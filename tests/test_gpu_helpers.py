@@ -105,4 +105,4 @@ def test_halley_power_law_reaches_double_precision(lib, p, q):
     mine = run(lib, 4, x, p, q)
     ref = run(lib, 5, x, p, q)  # CUDA's pow in double precision
     rel = np.abs(mine - ref) / ref
-    assert np.max(rel) < 6e-16, np.max(rel)  # ~3 ulp: the step's own rounding and pow's
+    assert np.max(rel) < 9e-16, np.max(rel)  # 4 ulp: the step's own rounding and pow's (measured <= 2.7)
