@@ -235,7 +235,7 @@ int s2_set_tiles(s2_solver *s, const int *tiles);
  * s2_set_tiles.  flux_ctas_per_sm: CTAs per multiprocessor of the
  * persistent single-precision flux grids (0: as many as fit, up to 16).
  * z_planes: z-planes each CTA of the mixed path's z-marching gradient and
- * viscous passes walks (0: 12; else 4..64).  weno_ctas_per_sm: cap of the
+ * viscous passes walks (0: 12; else 4, 8, 16 or 24, compiled variants).  weno_ctas_per_sm: cap of the
  * WENO kernels' 64-thread CTAs per multiprocessor (0: 16; else 1..64).
  * Takes effect at the next s2_step; results do not depend on it, except
  * that with channel forcing in S2_MIXED the viscous pass sums the forcing

@@ -12,7 +12,7 @@ library's own CUDA-event trace (s2_profile) per kernel class:
 * single precision: the resident CTAs per multiprocessor of the persistent
   flux grids (1..4, or all that fit), timed on the three flux classes;
 * single precision: the z-planes each CTA of the z-marching gradient and
-  viscous passes walks (4..48), timed on grad + visc;
+  viscous passes walks (4, 8, 12, 16, 24), timed on grad + visc;
 * the CTAs per multiprocessor of the WENO kernels' grids (4..32), timed on
   the WENO class (hybrid schemes only).
 
@@ -37,7 +37,7 @@ CACHE_PATH = os.environ.get("S2_TUNE_CACHE",
 _lock = threading.Lock()
 _DIRS = ("flux_x", "flux_y", "flux_z")
 FLUX_CTAS = (1, 2, 3, 4, 0)
-Z_PLANES = (4, 8, 12, 16, 24, 32, 48)
+Z_PLANES = (4, 8, 12, 16, 24)
 WENO_CTAS = (4, 8, 16, 32)
 
 

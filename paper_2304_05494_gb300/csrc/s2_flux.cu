@@ -82,6 +82,10 @@ template <>
 struct Tile<2, 1> {  // z: 16 along z, 16 columns
   static constexpr int L = 16, W = 16;
 };
+// Variant 2: the default tile with the KEEP central flux (a separate
+// instantiation keeps the split-form kernels' register allocation).
+template <int DIR>
+struct Tile<DIR, 2> : Tile<DIR, 0> {};
 
 constexpr int NTHREADS = 256;
 constexpr int WENO_NT = 64;  // threads per CTA of the WENO kernels
@@ -158,6 +162,30 @@ constexpr size_t flux_smem(bool keep = false) {
   constexpr int NFLD = HASW ? 7 : 6;
   return Ly::BAR_BYTES +
          sizeof(R) * ((size_t)Ly::NBUF * NFLD * Ly::SFA + (size_t)(keep ? 5 : 1) * NP * (Ly::L + NP) * Ly::W);
+}
+
+// KEEP pair fluxes of a staged tile: P_l(a) = a_l f*(a, a+l), the five
+// components per pair, a = -NP .. L-1 (TP[(l-1) 5 + c][position, pencil]).
+template <int DIR, class R, int NP, int LT, int W, int SA, int SCS, int SCT, int SFA>
+__device__ __forceinline__ void keep_pairs_tile(const R *S, R *TP, R gm1, int n) {
+  constexpr int ST = LT * W;
+  for (int idx = threadIdx.x; idx < ST; idx += NTHREADS) {
+    int a, cc;
+    if (DIR == 0) { a = idx % LT; cc = idx / LT; }
+    else { a = idx / W; cc = idx % W; }
+    const int q0 = (a - NP + GH) * SA + cc * SCS;
+    const R ra = S[F_RHO * SFA + q0], ua = S[F_U * SFA + q0], va = S[F_V * SFA + q0];
+    const R wa = S[F_W * SFA + q0], pa = S[F_P * SFA + q0];
+#pragma unroll
+    for (int l = 1; l <= NP; ++l) {
+      const int q1 = q0 + l * SA;
+      R f[5];
+      keep_pair<DIR, R>(ra, ua, va, wa, pa, S[F_RHO * SFA + q1], S[F_U * SFA + q1], S[F_V * SFA + q1],
+                        S[F_W * SFA + q1], S[F_P * SFA + q1], gm1, n, f);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) TP[((l - 1) * 5 + c) * ST + a * SA + cc * SCT] = R(acoef<NP>(l)) * f[c];
+    }
+  }
 }
 
 // CTAs walk the tiles of a direction (t = block index, + grid extent, ...).
@@ -261,24 +289,8 @@ __device__ __forceinline__ void flux_body(const FluxMaps &maps, const Dev &__res
 
     // ---- 2. weighted pair mass fluxes m_l(a), a = -NP .. L-1 ----
     // (KEEP: the five components of a_l f*(a, a+l) instead)
-    if (d.keep) {
-      for (int idx = tid; idx < ST; idx += NTHREADS) {
-        int a, cc;
-        if (DIR == 0) { a = idx % LT; cc = idx / LT; }
-        else { a = idx / W; cc = idx % W; }
-        const int q0 = (a - NP + GH) * SA + cc * SCS;
-        const R ra = S[F_RHO * SFA + q0], ua = S[F_U * SFA + q0], va = S[F_V * SFA + q0];
-        const R wa = S[F_W * SFA + q0], pa = S[F_P * SFA + q0];
-#pragma unroll
-        for (int l = 1; l <= NP; ++l) {
-          const int q1 = q0 + l * SA;
-          R f[5];
-          keep_pair<DIR, R>(ra, ua, va, wa, pa, S[F_RHO * SFA + q1], S[F_U * SFA + q1], S[F_V * SFA + q1],
-                            S[F_W * SFA + q1], S[F_P * SFA + q1], K.gamma - R(1), d.keep, f);
-#pragma unroll
-          for (int c = 0; c < 5; ++c) TP[((l - 1) * 5 + c) * ST + a * SA + cc * SCT] = R(acoef<NP>(l)) * f[c];
-        }
-      }
+    if constexpr (TV == 2) {
+      keep_pairs_tile<DIR, R, NP, LT, W, SA, SCS, SCT, SFA>(S, TP, K.gamma - R(1), d.keep);
     } else
     for (int idx = tid; idx < ST; idx += NTHREADS) {
       int a, cc;                            // a in 0..LT-1 <-> position a-NP
@@ -350,7 +362,7 @@ __device__ __forceinline__ void flux_body(const FluxMaps &maps, const Dev &__res
     __syncthreads();
 
     // ---- 3. central flux difference of the thread's points -> RHS ----
-    if (d.keep) {
+    if constexpr (TV == 2) {
       // KEEP: D = 2 sum_l [P_l(a) - P_l(a-l)], P_l the stored a_l f*
 #pragma unroll
       for (int pp = 0; pp < PPT; ++pp) {
@@ -722,20 +734,19 @@ __global__ void __launch_bounds__(WENO_NT) kb_weno(BatchArgs ba) {
 // that unit busy (measured faster than the persistent loop).
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaStream_t st) {
-  static int per_sm[2] = {0, 0};  // resident CTAs per multiprocessor (per instantiation; split form, KEEP)
-  const int kp = d.keep != 0;
-  const size_t smem = flux_smem<DIR, HASW, R, TV, NP>(kp);
-  if (per_sm[kp] == 0) {
+  static int per_sm = 0;  // resident CTAs per multiprocessor (per instantiation)
+  const size_t smem = flux_smem<DIR, HASW, R, TV, NP>(TV == 2);
+  if (per_sm == 0) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flux<DIR, HASW, R, TV, NP>, NTHREADS, smem) !=
             cudaSuccess ||
         b < 1)
       b = 1;
-    per_sm[kp] = b;
+    per_sm = b;
   }
   const TileGrid<DIR, TV, R> tg(d);
   const int ntiles = tg.count();
-  const int cps = d.flux_cps > 0 && d.flux_cps < per_sm[kp] ? d.flux_cps : per_sm[kp];
+  const int cps = d.flux_cps > 0 && d.flux_cps < per_sm ? d.flux_cps : per_sm;
   const int nb = sizeof(R) == 8 ? ntiles : (ntiles < cps * d.nsm ? ntiles : cps * d.nsm);
   k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, smem, st>>>(maps, d, tg, accumulate);
   return cudaGetLastError();
@@ -754,6 +765,7 @@ cudaError_t launch_np(const Dev &d, const FluxMaps &maps, int accumulate, cudaSt
 
 template <int DIR, bool HASW, class R>
 cudaError_t launch_tv(const Dev &d, const FluxMaps (&maps)[2], int accumulate, cudaStream_t st) {
+  if (d.keep) return launch_np<DIR, HASW, R, 2>(d, maps[0], accumulate, st);  // KEEP: the default tile
   return d.tile[DIR] ? launch_np<DIR, HASW, R, 1>(d, maps[1], accumulate, st)
                      : launch_np<DIR, HASW, R, 0>(d, maps[0], accumulate, st);
 }
@@ -775,11 +787,10 @@ cudaError_t launch_weno_one(const Dev &d, cudaStream_t st) {
 
 template <int DIR, bool HASW, class R, int TV, int NP>
 cudaError_t set_attr_one() {
-  // the larger (KEEP) size; a launch passes the size its scheme needs
   cudaError_t e = cudaFuncSetAttribute(k_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)flux_smem<DIR, HASW, R, TV, NP>(true));
+                                       (int)flux_smem<DIR, HASW, R, TV, NP>(TV == 2));
   cudaError_t e2 = cudaFuncSetAttribute(kb_flux<DIR, HASW, R, TV, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)flux_smem<DIR, HASW, R, TV, NP>(true));
+                                        (int)flux_smem<DIR, HASW, R, TV, NP>(TV == 2));
   return e != cudaSuccess ? e : e2;
 }
 
@@ -792,6 +803,8 @@ cudaError_t set_attr() {
   S2_A(false, 1, 1) S2_A(false, 1, 2) S2_A(false, 1, 3) S2_A(false, 1, 4)
   S2_A(true, 0, 1) S2_A(true, 0, 2) S2_A(true, 0, 3) S2_A(true, 0, 4)
   S2_A(true, 1, 1) S2_A(true, 1, 2) S2_A(true, 1, 3) S2_A(true, 1, 4)
+  S2_A(false, 2, 1) S2_A(false, 2, 2) S2_A(false, 2, 3) S2_A(false, 2, 4)
+  S2_A(true, 2, 1) S2_A(true, 2, 2) S2_A(true, 2, 3) S2_A(true, 2, 4)
 #undef S2_A
   return e;
 }
@@ -929,6 +942,7 @@ cudaError_t sel_np(const Dev &d, F &f) {
 
 template <class F, int DIR, class R>
 cudaError_t sel_w(const Dev &d, F &f) {
+  if (d.keep) return d.weno > 0 ? sel_np<F, DIR, true, R, 2>(d, f) : sel_np<F, DIR, false, R, 2>(d, f);
   if (d.weno > 0) return d.tile[DIR] ? sel_np<F, DIR, true, R, 1>(d, f) : sel_np<F, DIR, true, R, 0>(d, f);
   return d.tile[DIR] ? sel_np<F, DIR, false, R, 1>(d, f) : sel_np<F, DIR, false, R, 0>(d, f);
 }
@@ -953,22 +967,21 @@ struct FluxPlan {
   FluxBoxPlan &out;
   template <int DIR, bool HASW, class R, int TV, int NP>
   cudaError_t run() {
-    static int per_sm[2] = {0, 0};  // resident CTAs per multiprocessor of the batched kernel
-    const int kp = d.keep != 0;
-    if (per_sm[kp] == 0) {
+    static int per_sm = 0;  // resident CTAs per multiprocessor of the batched kernel
+    if (per_sm == 0) {
       int b = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kb_flux<DIR, HASW, R, TV, NP>, NTHREADS,
-                                                        flux_smem<DIR, HASW, R, TV, NP>(kp)) != cudaSuccess ||
+                                                        flux_smem<DIR, HASW, R, TV, NP>(TV == 2)) != cudaSuccess ||
           b < 1)
         b = 1;
-      per_sm[kp] = b;
+      per_sm = b;
     }
     const TileGrid<DIR, TV, R> tg(d);
     static_assert(sizeof(tg) <= sizeof(out.tg), "tile grid record");
     memcpy(out.tg, &tg, sizeof(tg));
     out.tg_size = (int)sizeof(tg);
     out.tiles = tg.count();
-    out.per_sm = d.flux_cps > 0 && d.flux_cps < per_sm[kp] ? d.flux_cps : per_sm[kp];
+    out.per_sm = d.flux_cps > 0 && d.flux_cps < per_sm ? d.flux_cps : per_sm;
     out.persistent = sizeof(R) == 4;
     return cudaSuccess;
   }
@@ -976,7 +989,6 @@ struct FluxPlan {
 
 struct FluxBatchLaunch {
   const BatchArgs &ba;
-  bool keep;
   unsigned total;
   const FluxMaps *maps;
   const void *tgs;
@@ -984,7 +996,7 @@ struct FluxBatchLaunch {
   cudaStream_t st;
   template <int DIR, bool HASW, class R, int TV, int NP>
   cudaError_t run() {
-    kb_flux<DIR, HASW, R, TV, NP><<<total, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(keep), st>>>(
+    kb_flux<DIR, HASW, R, TV, NP><<<total, NTHREADS, flux_smem<DIR, HASW, R, TV, NP>(TV == 2), st>>>(
         ba, maps, (const TileGrid<DIR, TV, R> *)tgs, accumulate);
     return cudaGetLastError();
   }
@@ -1029,7 +1041,7 @@ unsigned weno_batch_blocks(const Dev &d, int dir) {
 
 cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total, const FluxMaps *maps,
                               const void *tgs, int dir, int accumulate, cudaStream_t st) {
-  FluxBatchLaunch f{ba, d0.keep != 0, total, maps, tgs, accumulate, st};
+  FluxBatchLaunch f{ba, total, maps, tgs, accumulate, st};
   return flux_select(d0, dir, f);
 }
 

@@ -652,9 +652,9 @@ cudaError_t launch_flux_batch(const Dev &d0, const BatchArgs &ba, unsigned total
 cudaError_t launch_weno_batch(const Dev &d0, const BatchArgs &ba, unsigned total, int dir, cudaStream_t st);
 // z-marching passes of the mixed path: grid of one box (x, y, z blocks)
 void z_pass_grid(const Dev &d, unsigned g[3]);
-// Smallest planes per CTA of the z-marching passes s2_set_tuning accepts
-// (the forcing partials are sized for it).
-constexpr int ZS_MIN = 4, ZS_MAX = 64, ZS_DEFAULT = 12;
+// Planes per CTA of the z-marching passes: compiled for 4, 8, 12, 16 and
+// 24 (the forcing partials are sized for the smallest).
+constexpr int ZS_MIN = 4, ZS_DEFAULT = 12;
 cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
 cudaError_t launch_visc_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);
 cudaError_t launch_apply_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st);

@@ -1538,7 +1538,9 @@ int s2_set_tuning(s2_solver *s, const s2_tuning *t) {
   for (int a = 0; a < 3; ++a)
     if (t->tiles[a] != 0 && t->tiles[a] != 1) return S2_EINVAL;
   if (t->flux_ctas_per_sm < 0 || t->flux_ctas_per_sm > 16) return S2_EINVAL;
-  if (t->z_planes != 0 && (t->z_planes < ZS_MIN || t->z_planes > ZS_MAX)) return S2_EINVAL;
+  if (t->z_planes != 0 && t->z_planes != 4 && t->z_planes != 8 && t->z_planes != 12 && t->z_planes != 16 &&
+      t->z_planes != 24)
+    return S2_EINVAL;
   if (t->weno_ctas_per_sm < 0 || t->weno_ctas_per_sm > 64) return S2_EINVAL;
   DeviceGuard guard(s->device);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
@@ -1753,7 +1755,7 @@ namespace {
 bool same_kernels(const Dev &a, const Dev &b) {
   return a.mixed == b.mixed && a.npc == b.npc && a.npv == b.npv && a.weno == b.weno && a.kd.tp == b.kd.tp &&
          a.tile[0] == b.tile[0] && a.tile[1] == b.tile[1] && a.tile[2] == b.tile[2] && a.viscous == b.viscous &&
-         a.force == b.force && (a.cfl > 0.0) == (b.cfl > 0.0);
+         a.force == b.force && (a.cfl > 0.0) == (b.cfl > 0.0) && a.zs == b.zs;
 }
 
 void *batch_alloc(s2_solver *s, size_t bytes) {
@@ -1871,7 +1873,7 @@ int group_setup(BatchGroup &g) {
   for (int b = 0; b < n; ++b)
     for (int dir = 0; dir < 3; ++dir) {
       const s2_solver *m = g.members[b];
-      memcpy(host.data() + o_maps[dir] + sizeof(FluxMaps) * b, &m->fmaps[dir][d0.tile[dir] ? 1 : 0],
+      memcpy(host.data() + o_maps[dir] + sizeof(FluxMaps) * b, &m->fmaps[dir][d0.tile[dir] && !d0.keep ? 1 : 0],
              sizeof(FluxMaps));
       memcpy(host.data() + o_tg[dir] + (size_t)fp[dir].tg_size * b, plans[3 * b + dir].tg, fp[dir].tg_size);
     }

@@ -22,6 +22,8 @@
 //
 // Every kernel is instantiated for R = double (FP64 path) and R = float
 // (arithmetic of the mixed path).
+#include <type_traits>
+
 #include "s2_internal.cuh"
 
 namespace s2 {
@@ -371,7 +373,7 @@ __device__ __forceinline__ void zhalo_pos(int h, int &hx, int &hy) {
 // Per-thread addressing of a z-marching tile: the thread's own column and
 // its halo slots, as padded offsets without the z term (valid when inside
 // the padded box; out-of-box slots are never read by an active point).
-template <int NP>
+template <int NP, int ZS>
 struct ZTile {
   int i, j, x0, y0, z0, z1;
   bool active, cvalid;
@@ -383,8 +385,8 @@ struct ZTile {
     const int tid = threadIdx.x;
     x0 = B.x * ZTX;
     y0 = B.y * ZTY;
-    z0 = B.z * d.zs;
-    z1 = min(z0 + d.zs, d.nz);
+    z0 = B.z * ZS;
+    z1 = min(z0 + ZS, d.nz);
     i = x0 + tid % ZTX;
     j = y0 + tid / ZTX;
     active = i < d.nx && j < d.ny;
@@ -418,14 +420,14 @@ struct ZTile {
 
 // z-marching gradient pass: theta = div u (with ghosts at walls) and the
 // sensor test.  NF = 3 staged fields (u, v, w).
-template <int NP>
+template <int NP, int ZS>
 __device__ __forceinline__ void grad_z_body(const Dev &__restrict__ d, const Blk &B) {
   using R = float;
   constexpr int NF = 3, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
   __shared__ R sm[2][NF][SZ];
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
-  const ZTile<NP> t(d, B);
+  const ZTile<NP, ZS> t(d, B);
   const R *src[NF] = {V.u, V.v, V.ww};
   const long long sz = d.sz;
   C5<R> cx, cy, cz;
@@ -497,27 +499,27 @@ __device__ __forceinline__ void grad_z_body(const Dev &__restrict__ d, const Blk
   }
 }
 
-template <int NP>
+template <int NP, int ZS>
 __global__ void __launch_bounds__(NT, 3) k_grad_z(Dev d) {
-  grad_z_body<NP>(d, grid_blk());
+  grad_z_body<NP, ZS>(d, grid_blk());
 }
 
-template <int NP>
+template <int NP, int ZS>
 __global__ void __launch_bounds__(NT, 3) kb_grad_z(BatchArgs ba) {
   S2_BATCH_ENTER(ba, sd, B, b_box);
-  grad_z_body<NP>(sd, B);
+  grad_z_body<NP, ZS>(sd, B);
 }
 
 // z-marching viscous pass (velocity gradients recomputed), plus the WENO
 // corrections.  NF = 5 staged fields (u, v, w, T, theta).
-template <int NP>
+template <int NP, int ZS>
 __device__ __forceinline__ void visc_z_body(const Dev &__restrict__ d, const Blk &B) {
   using R = float;
   constexpr int NF = 5, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
   __shared__ R sm[2][NF][SZ];
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
-  const ZTile<NP> t(d, B);
+  const ZTile<NP, ZS> t(d, B);
   const R *src[NF] = {V.u, V.v, V.ww, V.T, V.div};
   const long long sz = d.sz;
   const int jc = t.active ? t.j : 0;
@@ -640,15 +642,15 @@ __device__ __forceinline__ void visc_z_body(const Dev &__restrict__ d, const Blk
   }
 }
 
-template <int NP>
+template <int NP, int ZS>
 __global__ void __launch_bounds__(NT, 2) k_visc_z(Dev d) {
-  visc_z_body<NP>(d, grid_blk());
+  visc_z_body<NP, ZS>(d, grid_blk());
 }
 
-template <int NP>
+template <int NP, int ZS>
 __global__ void __launch_bounds__(NT, 2) kb_visc_z(BatchArgs ba) {
   S2_BATCH_ENTER(ba, sd, B, b_box);
-  visc_z_body<NP>(sd, B);
+  visc_z_body<NP, ZS>(sd, B);
 }
 
 
@@ -674,6 +676,19 @@ void visc_np(const Dev &d, unsigned nb, cudaStream_t st) {
 
 }  // namespace
 
+// Planes per CTA of the z-marching passes, compiled as template arguments
+// (a loop of compile-time length keeps the z queue in fixed registers).
+template <int NPV, class F>
+void z_launch(F f, int zs) {
+  switch (zs) {
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    case 16: f(std::integral_constant<int, 16>()); break;
+    case 24: f(std::integral_constant<int, 24>()); break;
+    default: f(std::integral_constant<int, 12>()); break;
+  }
+}
+
 static dim3 zgrid(const Dev &d) {
   return dim3((d.nx + ZTX - 1) / ZTX, (d.ny + ZTY - 1) / ZTY, (d.nz + d.zs - 1) / d.zs);
 }
@@ -682,10 +697,10 @@ cudaError_t launch_grad(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
   if (d.mixed) {
     switch (d.npv) {
-      case 1: k_grad_z<1><<<zgrid(d), NT, 0, st>>>(d); break;
-      case 2: k_grad_z<2><<<zgrid(d), NT, 0, st>>>(d); break;
-      case 3: k_grad_z<3><<<zgrid(d), NT, 0, st>>>(d); break;
-      default: k_grad_z<4><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 1: z_launch<1>([&](auto zs) { k_grad_z<1, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      case 2: z_launch<2>([&](auto zs) { k_grad_z<2, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      case 3: z_launch<3>([&](auto zs) { k_grad_z<3, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      default: z_launch<4>([&](auto zs) { k_grad_z<4, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
     }
   } else {
     grad_np<double>(d, nb, st);
@@ -721,10 +736,10 @@ void z_pass_grid(const Dev &d, unsigned g[3]) {
 cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
   if (d0.mixed) {
     switch (d0.npv) {
-      case 1: kb_grad_z<1><<<total, NT, 0, st>>>(ba); break;
-      case 2: kb_grad_z<2><<<total, NT, 0, st>>>(ba); break;
-      case 3: kb_grad_z<3><<<total, NT, 0, st>>>(ba); break;
-      default: kb_grad_z<4><<<total, NT, 0, st>>>(ba); break;
+      case 1: z_launch<1>([&](auto zs) { kb_grad_z<1, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      case 2: z_launch<2>([&](auto zs) { kb_grad_z<2, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      case 3: z_launch<3>([&](auto zs) { kb_grad_z<3, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      default: z_launch<4>([&](auto zs) { kb_grad_z<4, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
     }
   } else {
     switch (d0.npv) {
@@ -740,10 +755,10 @@ cudaError_t launch_grad_batch(const Dev &d0, const BatchArgs &ba, unsigned total
 cudaError_t launch_visc_batch(const Dev &d0, const BatchArgs &ba, unsigned total, cudaStream_t st) {
   if (d0.mixed) {
     switch (d0.npv) {
-      case 1: kb_visc_z<1><<<total, NT, 0, st>>>(ba); break;
-      case 2: kb_visc_z<2><<<total, NT, 0, st>>>(ba); break;
-      case 3: kb_visc_z<3><<<total, NT, 0, st>>>(ba); break;
-      default: kb_visc_z<4><<<total, NT, 0, st>>>(ba); break;
+      case 1: z_launch<1>([&](auto zs) { kb_visc_z<1, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      case 2: z_launch<2>([&](auto zs) { kb_visc_z<2, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      case 3: z_launch<3>([&](auto zs) { kb_visc_z<3, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
+      default: z_launch<4>([&](auto zs) { kb_visc_z<4, decltype(zs)::value><<<total, NT, 0, st>>>(ba); }, d0.zs); break;
     }
   } else {
     switch (d0.npv) {
@@ -766,10 +781,10 @@ cudaError_t launch_visc(const Dev &d, cudaStream_t st) {
   unsigned nb = (unsigned)((d.n + NT - 1) / NT);
   if (d.mixed) {
     switch (d.npv) {
-      case 1: k_visc_z<1><<<zgrid(d), NT, 0, st>>>(d); break;
-      case 2: k_visc_z<2><<<zgrid(d), NT, 0, st>>>(d); break;
-      case 3: k_visc_z<3><<<zgrid(d), NT, 0, st>>>(d); break;
-      default: k_visc_z<4><<<zgrid(d), NT, 0, st>>>(d); break;
+      case 1: z_launch<1>([&](auto zs) { k_visc_z<1, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      case 2: z_launch<2>([&](auto zs) { k_visc_z<2, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      case 3: z_launch<3>([&](auto zs) { k_visc_z<3, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
+      default: z_launch<4>([&](auto zs) { k_visc_z<4, decltype(zs)::value><<<zgrid(d), NT, 0, st>>>(d); }, d.zs); break;
     }
   } else {
     visc_np<double>(d, nb, st);

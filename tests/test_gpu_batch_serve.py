@@ -203,14 +203,14 @@ def test_launch_knobs_give_identical_results(s2, precision):
     ref = run(chan)
     for knobs in (dict(flux_ctas_per_sm=1, weno_ctas_per_sm=4), dict(flux_ctas_per_sm=3, weno_ctas_per_sm=32)):
         assert np.array_equal(ref, run(chan, **knobs)), knobs
-    zc = run(chan, z_planes=7)
+    zc = run(chan, z_planes=8)
     if precision == "fp64":
         assert np.array_equal(ref, zc)
     else:
         assert field_err(zc, ref) < 1e-6
     box = W.isotropic(24, mach_t=0.6, seed=3, weno_order=5)
     refb = run(box)
-    for knobs in (dict(z_planes=4, flux_ctas_per_sm=2), dict(z_planes=48, weno_ctas_per_sm=8), dict(z_planes=7)):
+    for knobs in (dict(z_planes=4, flux_ctas_per_sm=2), dict(z_planes=24, weno_ctas_per_sm=8), dict(z_planes=16)):
         assert np.array_equal(refb, run(box, **knobs)), knobs
 
 
