@@ -23,9 +23,10 @@ The reference arm times the plain CPU oracle on the host cores.
 
 Beside the headline: the 256 x 128 x 128 channel (Re_tau ~ 220) in both
 precisions (`channel256`), the same with a thermally perfect gas
-(`thermally_perfect`), and a continuous-batching serving run of the serving
-workload for the p50/p99 batched step latency (`serving`).  The last keys
-of the line repeat the mixed-precision figures.
+(`thermally_perfect`), the work-list batch against the member-branch graph
+on many small boxes (`batching`), and a continuous-batching serving run of
+the serving workload (256 requests) for the p50/p99 batched step latency
+(`serving`).  The last keys of the line repeat the mixed-precision figures.
 """
 from __future__ import annotations
 
@@ -64,8 +65,8 @@ ALG_FLOPS_FLUX_DIFFERENCE = 47.0 / 3  # flux difference per point and direction
 FP64_PEAK_GFLOPS = 152 * 4 * 2.070
 # DRAM bytes per interior point of one launch of the FP64 viscous kernel
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum, 256 x 128 x 128
-# channel; profiles/channel256x128x128_fp64_kernels_dram.md).
-FP64_DRAM_BYTES = {"visc": 207.4}
+# channel, scaled by the points of a launch; profiles/channel256x128x128_fp64_visc_full.md).
+FP64_DRAM_BYTES = {"visc": 207.8}
 # Mixed path: algorithmic HBM bytes per interior point of one launch
 # (single-precision primitives and RHS, double-precision state; each field
 # read or written once, halos not counted):
@@ -79,8 +80,8 @@ MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68
 # and write the state and the RK register, 4 x 40 B.
 METHOD_BYTES_PER_POINT_STEP = 480.0
 # DRAM bytes per interior point of one launch of the mixed kernels (ncu,
-# 256 x 128 x 128 channel, current kernels; profiles/channel256x128x128_mixed_kernels_dram.md).
-MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.3, "update": 110.6}
+# 256 x 128 x 128 channel, first stage; profiles/channel256x128x128_mixed_kernels_full.md).
+MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.8, "update": 110.1}
 # Thermally perfect gas of the side measurement: a synthetic polynomial of
 # the NASA 9-coefficient form, c_p/R = sum_{l=-2..4} a_l T^l (reference
 # units of T), whose gamma falls from 1.45 at T = 0.5 through 1.40 at T = 1
@@ -112,6 +113,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=256,
                     help="requests of the serving run (p50/p99 batched step latency); 0 skips it")
     ap.add_argument("--small", action="store_true", help="headline on the 256x128x128 channel (quick checks)")
+    ap.add_argument("--no-batch", dest="batch", action="store_false", help="skip the batching comparison")
     return ap.parse_args()
 
 
@@ -374,6 +376,42 @@ def mixed_roofline(case, prof, step_ms):
             "frac_per_kernel": kfrac}
 
 
+def batch_leg(s2, steps=10):
+    """Many small boxes batched: ms per batch step of the work-list batch
+    (one launch per kernel for all boxes) and of the member-branch graph,
+    for 64 Taylor-Green boxes of 24^3 (hybrid WENO5) and for one box of each
+    serving size 32^3 .. 128^3, in mixed precision."""
+    import time
+    from paper_2304_05494_gb300 import workloads as W
+    out = {}
+    for name, sizes in (("64x24^3", [24] * 64), ("32^3..128^3", [32, 48, 64, 96, 128])):
+        cases = [W.taylor_green(n, mach=0.3, seed=10 + i) for i, n in enumerate(sizes)]
+        for c in cases:
+            c.weno_order, c.threshold = 5, 0.2
+        res = {}
+        for mode in ("branches", "worklist"):
+            solvers = []
+            for c in cases:
+                sv = s2.Solver.from_case(c, precision="mixed")
+                sv.set_state(c.w0)
+                solvers.append(sv)
+            with s2.Batch(solvers, mode=mode) as b:
+                b.step(2)
+                b.sync()
+                best = 1e9
+                for _ in range(3):
+                    t0 = time.perf_counter()
+                    b.step(steps)
+                    b.sync()
+                    best = min(best, time.perf_counter() - t0)
+                res[mode] = {"ms_per_step": best / steps * 1e3, "launches_per_step": b.launches_per_step}
+            for sv in solvers:
+                sv.close()
+        res["speedup"] = res["branches"]["ms_per_step"] / res["worklist"]["ms_per_step"]
+        out[name] = res
+    return out
+
+
 def ms_per_step(prof, steps):
     return {k: round(v[0] / steps, 4) for k, v in prof.items() if v[1]}
 
@@ -491,6 +529,11 @@ def our_arm(args):
             tp[prec] = {"value": c2.points * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
                         "status_ok": ok}
 
+    # ---- batching: work-list batch against member branches -------------
+    batching = None
+    if args.batch and world == 1:
+        batching = batch_leg(s2)
+
     # ---- serving: continuous batching at 80 % of capacity ----------------
     serving = None
     if args.serve_requests > 0 and world == 1:
@@ -515,7 +558,7 @@ def our_arm(args):
                "config": dict(config_of(case), parallelism="replicas" if world > 1 else "single"),
                "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                "weno_frac": weno_frac, "state_finite": finite, "channel256": side, "thermally_perfect": tp,
-               "serving": serving, "mixed": mixed}
+               "batching": batching, "serving": serving, "mixed": mixed}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(case)
         # the mixed-precision headline figures again, last on the line

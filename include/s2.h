@@ -322,8 +322,9 @@ void s2_destroy(s2_solver *s);
  * device memory, and the persistent single-precision flux grids are
  * shared out over the boxes by their tile counts.  A step costs the same
  * ~40 launches for 1 box or 100.  Members of S2_BATCH_SOLO_POINTS points
- * or more fill enough of the GPU on their own and keep their own launch
- * sequence.  Groups and such members run as concurrent branches of the
+ * or more fill enough of the GPU on their own, and groups of fewer than
+ * S2_BATCH_MIN_GROUP members save too few launches: those keep their own
+ * launch sequence (S2_BATCH_WORKLIST_ALL puts every member in a group).  Groups and such members run as concurrent branches of the
  * step graph.  Branch mode (S2_BATCH_BRANCHES): every member's own
  * launch sequence is a concurrent branch.  Either way each box's
  * arithmetic is exactly that of its solo run (results identical bit for
@@ -343,6 +344,7 @@ void s2_destroy(s2_solver *s);
 #define S2_BATCH_BRANCHES 1
 #define S2_BATCH_WORKLIST_ALL 2   /* work list for every member, whatever its size */
 #define S2_BATCH_SOLO_POINTS 262144 /* 64^3 */
+#define S2_BATCH_MIN_GROUP 4        /* smaller groups keep their members' own launches */
 typedef struct s2_batch s2_batch;
 int s2_batch_create(s2_solver *const *members, int count, void *stream, s2_batch **out);
 int s2_batch_create_ex(s2_solver *const *members, int count, void *stream, int mode, s2_batch **out);

@@ -2081,6 +2081,15 @@ int s2_batch_create_ex(s2_solver *const *members, int count, void *stream, int m
       }
       g->members.push_back(s);
     }
+    if (mode == S2_BATCH_WORKLIST) {
+      // a group of a few boxes saves few launches: its members keep their own
+      std::vector<BatchGroup> kept;
+      for (BatchGroup &g : b->groups) {
+        if ((int)g.members.size() >= S2_BATCH_MIN_GROUP) kept.push_back(g);
+        else b->solo.insert(b->solo.end(), g.members.begin(), g.members.end());
+      }
+      b->groups.swap(kept);
+    }
     for (BatchGroup &g : b->groups)
       if (rc == S2_OK) rc = group_setup(g);
   }

@@ -84,14 +84,15 @@ def test_worklist_batch_of_uneven_boxes_matches_solo_runs(s2, precision):
     kernels run as one group (each kernel one launch for all of them, the
     work list giving every CTA its box and tile); every member equals its
     solo run bit for bit, and the whole step costs the launches of one box.
-    A member with another scheme forms a second group."""
+    A member with another scheme (too few for a group of its own) keeps its
+    own launch sequence."""
     box = W.Case(name="smooth28x20x12", nx=28, ny=20, nz=12, lx=2 * np.pi, ly=2 * np.pi, lz=2 * np.pi,
                  w0=W.smooth_periodic(28, 20, 12, seed=7, mach=0.5, amp_u=0.4, amp_s=0.1), mach=0.5, re=300.0)
     cases = [W.taylor_green(24, seed=3), W.taylor_green(32, mach=0.4, re=800.0, seed=4),
              W.isotropic(20, mach_t=0.6, seed=6, weno_order=5), box]
     for c in cases:
         c.weno_order, c.threshold, c.cfl, c.dt_every = 5, 0.1, 0.8, 2
-    odd = W.channel(40, 24, 16, seed=9)  # walls and forcing: its own group
+    odd = W.channel(40, 24, 16, seed=9)  # walls and forcing: another kernel set
     kw = dict(precision=precision)
     solvers = []
     for c in cases + [odd]:
@@ -108,7 +109,7 @@ def test_worklist_batch_of_uneven_boxes_matches_solo_runs(s2, precision):
     for c, g in zip(cases + [odd], got):
         assert np.array_equal(g, solo(s2, c, 3, **kw)), c.name
     # the branch graph launches every member's kernels; the work list one
-    # set per group (two groups here)
+    # set for the group and the odd member's own
     solvers = [s2.Solver.from_case(c, **kw) for c in cases + [odd]]
     with s2.Batch(solvers, mode="branches") as b:
         n_branch = b.launches_per_step
