@@ -289,10 +289,14 @@ def reference_arm(args):
 
 
 class Timer:
-    """Device time of a region on one stream (CUDA events), max over ranks."""
+    """Device time of a region on one stream (CUDA events), max over ranks.
 
-    def __init__(self, torch, dist, world, stream):
-        self.torch, self.dist, self.world, self.stream = torch, dist, world, stream
+    The ranks are independent replicas: the only collectives are the
+    barriers around the timed region and the max of the times (on the
+    device for NCCL, on the host for gloo)."""
+
+    def __init__(self, torch, dist, world, stream, device="cuda"):
+        self.torch, self.dist, self.world, self.stream, self.device = torch, dist, world, stream, device
 
     def barrier(self):
         if self.world > 1:
@@ -312,10 +316,17 @@ class Timer:
 
     def max(self, v):
         if self.world > 1:
-            t = self.torch.tensor([v], device="cuda", dtype=self.torch.float64)
+            t = self.torch.tensor([v], device=self.device, dtype=self.torch.float64)
             self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
             v = float(t.item())
         return v
+
+
+def whole_job_rate(points, steps, world, ms):
+    """Point-steps per second of the whole job: every rank advances its own
+    replica of `points` points by `steps` steps; `ms` is the slowest rank's
+    time."""
+    return points * steps * world / (ms * 1e-3)
 
 
 def per_launch(prof, name):
@@ -446,7 +457,7 @@ def our_arm(args):
     t_max = T.run(lambda: sv.step(args.steps))
     clk = clocks.stop()
     launches = sv.stats()["launches"] - launches0
-    value = case.points * args.steps * world / (t_max * 1e-3)
+    value = whole_job_rate(case.points, args.steps, world, t_max)
     prof = sv.profile(args.profile_steps)
     weno_frac = sv.stats()["weno_frac"]
     roofline = fp64_roofline(case, prof, args.profile_steps, weno_frac, t_max / args.steps, fma)
@@ -467,7 +478,7 @@ def our_arm(args):
         sv.step(1)
         sv.get_state(wout)
     t_e2e = T.max(time.perf_counter() - t0)
-    e2e = {"value": case.points * args.e2e_steps * world / t_e2e, "unit": UNIT,
+    e2e = {"value": whole_job_rate(case.points, args.e2e_steps, world, t_e2e * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": case.w0.nbytes, "d2h_bytes_per_step": case.w0.nbytes}
     finite = bool(np.isfinite(wout[:, ::64]).all())
     del pinned_in, pinned_out, win, wout
@@ -498,7 +509,7 @@ def our_arm(args):
         del wm, wd
     sm.close()
     sv.close()
-    mixed = {"value": case.points * args.steps * world / (ms_m * 1e-3), "unit": UNIT,
+    mixed = {"value": whole_job_rate(case.points, args.steps, world, ms_m), "unit": UNIT,
              "ms_per_step": ms_m / args.steps, "dtype": "f32 flux / f64 state", "roofline": mroof,
              "err_vs_fp64": err, "energy_rel_diff_vs_fp64": energy_drift, "err_steps": args.err_steps}
 
@@ -514,7 +525,7 @@ def our_arm(args):
             s.sync()
             ms = T.run(lambda: s.step(args.steps))
             s.close()
-            side[prec] = {"value": c2.points * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps}
+            side[prec] = {"value": whole_job_rate(c2.points, args.steps, world, ms), "ms_per_step": ms / args.steps}
         # thermally perfect gas (Sec. 2: c_p(T) from a NASA-form polynomial):
         # the same flow, converted with this gas's e(T) on the device
         tp = {"gas": "synthetic NASA 9-coefficient form, a_-2..a_4 = %s" % TP_GAS, "workload": "channel 256x128x128"}
@@ -526,7 +537,7 @@ def our_arm(args):
             ms = T.run(lambda: s.step(args.steps))
             ok = s.stats()["status"] == 0
             s.close()
-            tp[prec] = {"value": c2.points * args.steps * world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            tp[prec] = {"value": whole_job_rate(c2.points, args.steps, world, ms), "ms_per_step": ms / args.steps,
                         "status_ok": ok}
 
     # ---- batching: work-list batch against member branches -------------
