@@ -565,6 +565,20 @@ __device__ __forceinline__ bool dt_due(const Dev &d) {
 // mbarrier.
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Per-thread asynchronous copies of single words into shared memory
+// (cp.async, cached in L1): the z-marching passes fetch the next plane's
+// halo, and the viscous pass its point's RHS and viscosity, while the
+// current plane is computed, without holding the values in registers.
+// A thread's own copies are complete after cp_async_wait_all; a barrier
+// then makes them visible to the CTA.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }

@@ -511,12 +511,16 @@ __global__ void __launch_bounds__(NT, 3) kb_grad_z(BatchArgs ba) {
 }
 
 // z-marching viscous pass (velocity gradients recomputed), plus the WENO
-// corrections.  NF = 5 staged fields (u, v, w, T, theta).
+// corrections.  NF = 5 staged fields (u, v, w, T, theta).  The next
+// plane's halo and the point's RHS and viscosity arrive by cp.async while
+// the current plane is computed (the plane's centre values come from the
+// column queue in registers).
 template <int NP, int ZS>
 __device__ __forceinline__ void visc_z_body(const Dev &__restrict__ d, const Blk &B) {
   using R = float;
   constexpr int NF = 5, NQ = 2 * NP + 1, SZ = ZGeom<NP>::SIZE, SX = ZGeom<NP>::SX, HPT = ZGeom<NP>::HPT;
   __shared__ R sm[2][NF][SZ];
+  __shared__ R pre[2][NV + 1][NT];  // the thread's RHS (NV) and mu, by plane parity
   const View<R> V = view<R>(d);
   const Consts<R> &K = consts<R>(d);
   const ZTile<NP, ZS> t(d, B);
@@ -533,44 +537,54 @@ __device__ __forceinline__ void visc_z_body(const Dev &__restrict__ d, const Blk
   }
   const R ry = __ldg(V.ry + jc);
   const R c0 = by.c[0] + K.b0xz;
-  R q[NF][NQ], pf[NF], hr[NF][HPT];
+  const int tid = threadIdx.x;
+  // asynchronous part of plane kk into buffer bb: its halo, the point's RHS and mu
+  auto fetch = [&](int kk, int bb) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int s = 0; s < HPT; ++s)
+        if (t.hoff[s] >= 0) cp_async4(&sm[bb][f][t.hoff[s]], src[f] + t.hbase[s] + kk * sz);
+    if (t.active) {
+      const long long qk = ((long long)kk * d.ny + t.j) * d.nx + t.i;
+#pragma unroll
+      for (int f = 0; f < NV; ++f) cp_async4(&pre[bb][f][tid], V.fl + f * d.n + qk);
+      cp_async4(&pre[bb][NV][tid], V.mu + qk);
+    }
+    cp_async_commit();
+  };
+  R q[NF][NQ], pf[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
 #pragma unroll
     for (int m = 0; m < NQ - 1; ++m) q[f][m] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 - NP + m) * sz) : R(0);
     pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (t.z0 + NP) * sz) : R(0);
-#pragma unroll
-    for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + t.z0 * sz) : R(0);
   }
+  fetch(t.z0, 0);
   const int c = t.centre();
   R fsum = R(0);  // the column's R_rho u, for the bulk forcing
   for (int k = t.z0; k < t.z1; ++k) {
     const int b = (k - t.z0) & 1;
     const long long qi = ((long long)k * d.ny + t.j) * d.nx + t.i;  // interior index
-    R Rv[NV], mu = R(0);
-    if (t.active) {
-      mu = __ldg(V.mu + qi);
-#pragma unroll
-      for (int f = 0; f < NV; ++f) Rv[f] = V.fl[f * d.n + qi];
-    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       q[f][NQ - 1] = pf[f];
       sm[b][f][c] = q[f][NP];
-#pragma unroll
-      for (int s = 0; s < HPT; ++s)
-        if (t.hoff[s] >= 0) sm[b][f][t.hoff[s]] = hr[f][s];
     }
+    cp_async_wait_all();
+    // every thread has finished the previous plane (whose buffer the next
+    // fetch overwrites) and this plane's halo is in place
+    __syncthreads();
     if (k + 1 < t.z1) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (k + 1 + NP) * sz) : R(0);
-#pragma unroll
-        for (int s = 0; s < HPT; ++s) hr[f][s] = t.hoff[s] >= 0 ? __ldg(src[f] + t.hbase[s] + (k + 1) * sz) : R(0);
-      }
+      for (int f = 0; f < NF; ++f) pf[f] = t.cvalid ? __ldg(src[f] + t.cbase + (k + 1 + NP) * sz) : R(0);
+      fetch(k + 1, b ^ 1);
     }
-    __syncthreads();
     if (t.active) {
+      R Rv[NV];
+#pragma unroll
+      for (int f = 0; f < NV; ++f) Rv[f] = pre[b][f][tid];
+      const R mu = pre[b][NV][tid];
       // first derivatives (x, y from shared memory, z from the column)
       R gd[NF][3];
 #pragma unroll
