@@ -28,9 +28,10 @@
  *
  * Errors: every int-returning call returns S2_OK (0) or a negative code;
  * s2_strerror names it.  Handles are not thread-safe; each solver issues
- * all its work on one CUDA stream.  No call allocates device memory except
- * s2_create (which allocates everything up front) and s2_batch_create
- * (its work-list tables).
+ * its work on one CUDA stream (s2_stream_states adds two copy streams of
+ * its own, synchronised before it returns).  No call allocates device memory except
+ * s2_create (which allocates everything up front), s2_batch_create (its
+ * work-list tables) and the first s2_stream_states (its staging buffers).
  */
 #ifndef S2_H
 #define S2_H
@@ -218,6 +219,27 @@ int s2_step(s2_solver *s, int n);
 
 /* Wait for the solver's stream; returns the device status. */
 int s2_sync(s2_solver *s);
+
+/* Stream count independent states through the solver (Sec. 3.2,
+ * Listing 3: the state crosses the host link once in and once out, the
+ * steps in between stay on the device).  For j = 0 .. count-1: state j is copied in from
+ * w_in + j*in_stride, advanced by nsteps RK3 steps, and copied out to
+ * w_out + j*out_stride (strides in doubles, >= 0; a stride of 0 reuses one
+ * buffer; layout of each state as s2_set_state).  w_in and w_out may be
+ * host (pinned or pageable) or device memory.  The copy-in of state j+1
+ * and the copy-out of result j run on two streams of the solver beside
+ * the steps of state j, through two device staging buffers of one state
+ * each (allocated at the first call through the s2_device allocator,
+ * released by s2_destroy); pinned host memory lets them overlap.  Each
+ * state starts as after s2_set_state (RK register cleared; the clock runs
+ * on from state to state).  The call returns when every result is in
+ * w_out; w_in must stay unchanged until then, and w_out must not overlap
+ * w_in.  Returns S2_ENONFINITE if any state met an invalid value (its
+ * result and the following ones are still copied out), S2_ENOMEM if the
+ * staging buffers cannot be allocated, S2_EINVAL for a NULL pointer or a
+ * negative count, step count or stride. */
+int s2_stream_states(s2_solver *s, const double *w_in, long long in_stride, double *w_out, long long out_stride,
+                     int count, int nsteps);
 
 /* Flux tile shape per direction: tiles[d] = 0 (64x4 points for x, 32x8
  * for y and z) or 1 (narrower along the direction: 32x8 for x, 16x16 for y

@@ -778,6 +778,11 @@ struct s2_solver {
   // kernel, join before the viscous pass)
   cudaStream_t side;
   cudaEvent_t ev_flux[3], ev_join;
+  // s2_stream_states (set up at its first call): one device staging buffer
+  // per direction, the copy-in and copy-out streams and their events
+  double *stage_in, *stage_out;
+  cudaStream_t cin, cout;
+  cudaEvent_t ev_in_ready, ev_in_free, ev_out_ready, ev_out_free;
 };
 
 namespace {
@@ -803,6 +808,10 @@ void release(s2_solver *s) {
     if (s->ev_flux[a]) cudaEventDestroy(s->ev_flux[a]);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
   if (s->side) cudaStreamDestroy(s->side);
+  for (cudaEvent_t ev : {s->ev_in_ready, s->ev_in_free, s->ev_out_ready, s->ev_out_free})
+    if (ev) cudaEventDestroy(ev);
+  if (s->cin) cudaStreamDestroy(s->cin);
+  if (s->cout) cudaStreamDestroy(s->cout);
   for (void *p : s->blocks) {
     if (s->dev.free) s->dev.free(p, s->dev.ctx);
     else cudaFree(p);
@@ -1530,6 +1539,81 @@ int s2_step(s2_solver *s, int n) {
 int s2_sync(s2_solver *s) {
   if (!s) return S2_EINVAL;
   DeviceGuard guard(s->device);
+  return read_status(s);
+}
+
+namespace {
+
+// Staging buffers (one allocation), streams and events of s2_stream_states.
+int stream_setup(s2_solver *s) {
+  if (s->stage_in) return S2_OK;
+  const size_t n5 = NV * (size_t)s->d.n;
+  // each handle is created once (a failed call leaves the others for s2_destroy)
+  for (cudaStream_t *q : {&s->cin, &s->cout})
+    if (!*q && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess) {
+      *q = nullptr;
+      return S2_ECUDA;
+    }
+  for (cudaEvent_t *ev : {&s->ev_in_ready, &s->ev_in_free, &s->ev_out_ready, &s->ev_out_free})
+    if (!*ev && cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+      *ev = nullptr;
+      return S2_ECUDA;
+    }
+  double *p = (double *)dalloc(s, 2 * n5 * sizeof(double));
+  if (!p) return S2_ENOMEM;
+  s->stage_in = p;
+  s->stage_out = p + n5;
+  return S2_OK;
+}
+
+}  // namespace
+
+int s2_stream_states(s2_solver *s, const double *w_in, long long in_stride, double *w_out, long long out_stride,
+                     int count, int nsteps) {
+  if (!s || !w_in || !w_out || count < 0 || nsteps < 0 || in_stride < 0 || out_stride < 0) return S2_EINVAL;
+  if (count == 0) return S2_OK;
+  DeviceGuard guard(s->device);
+  int rc = stream_setup(s);
+  if (rc != S2_OK) return rc;
+  const size_t n5 = NV * (size_t)s->d.n, bytes = n5 * sizeof(double);
+  cudaStream_t st = s->stream;
+  // copy-in of state j+1 and copy-out of result j-1 overlap the steps of
+  // state j; each staging buffer is handed between its copy stream and the
+  // solver's stream by a pair of events
+  cudaError_t e = cudaMemsetAsync(&s->d.scal->status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->stage_in, w_in, bytes, cudaMemcpyDefault, s->cin);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_in_ready, s->cin);
+  for (int j = 0; j < count && e == cudaSuccess && rc == S2_OK; ++j) {
+    e = cudaStreamWaitEvent(st, s->ev_in_ready, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d.w, s->stage_in, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d.fln, 0, n5 * s->rsize, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_in_free, st);
+    if (e == cudaSuccess && j + 1 < count) {
+      e = cudaStreamWaitEvent(s->cin, s->ev_in_free, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->stage_in, w_in + (j + 1) * in_stride, bytes, cudaMemcpyDefault, s->cin);
+      if (e == cudaSuccess) e = cudaEventRecord(s->ev_in_ready, s->cin);
+    }
+    if (e == cudaSuccess) rc = s2_step(s, nsteps);
+    if (e == cudaSuccess && rc == S2_OK) {
+      e = cudaStreamWaitEvent(st, s->ev_out_free, 0);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(s->stage_out, s->d.w, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaEventRecord(s->ev_out_ready, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cout, s->ev_out_ready, 0);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(w_out + j * out_stride, s->stage_out, bytes, cudaMemcpyDefault, s->cout);
+      if (e == cudaSuccess) e = cudaEventRecord(s->ev_out_free, s->cout);
+    }
+  }
+  // no copy outlives the call, also after an error
+  const cudaError_t e1 = cudaStreamSynchronize(s->cin), e2 = cudaStreamSynchronize(s->cout);
+  if (e != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    return S2_ECUDA;
+  }
+  if (rc != S2_OK) {
+    cudaStreamSynchronize(st);
+    return rc;
+  }
   return read_status(s);
 }
 

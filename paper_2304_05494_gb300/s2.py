@@ -98,6 +98,7 @@ def _load():
     lib.s2_get_primitives.argtypes = [P, P, C.c_int]
     lib.s2_step.argtypes = [P, C.c_int]
     lib.s2_sync.argtypes = [P]
+    lib.s2_stream_states.argtypes = [P, P, C.c_longlong, P, C.c_longlong, C.c_int, C.c_int]
     lib.s2_set_clock.argtypes = [P, C.c_double, C.c_longlong, C.c_double]
     lib.s2_stats.argtypes = [P, C.POINTER(s2_stats_t)]
     lib.s2_rhs.argtypes = [P, P, C.c_int]
@@ -133,7 +134,7 @@ def _load():
     lib.s2_strerror.argtypes = [C.c_int]
     lib.s2_strerror.restype = C.c_char_p
     for f in ("s2_set_state", "s2_get_state", "s2_step", "s2_sync", "s2_set_clock", "s2_stats", "s2_rhs",
-              "s2_get_flags"):
+              "s2_get_flags", "s2_stream_states"):
         getattr(lib, f).restype = C.c_int
     del dp
     return lib
@@ -186,6 +187,12 @@ def s2_set_state(h, w) -> None:
 def s2_get_state(h, out) -> None:
     p, where, _ = _ptr(out)
     _check(_lib.s2_get_state(h, p, where), "s2_get_state")
+
+
+def s2_stream_states(h, w_in, in_stride: int, w_out, out_stride: int, count: int, nsteps: int) -> None:
+    pi, _, _ = _ptr(w_in)
+    po, _, _ = _ptr(w_out)
+    _check(_lib.s2_stream_states(h, pi, in_stride, po, out_stride, count, nsteps), "s2_stream_states")
 
 
 def s2_set_primitives(h, prim) -> None:
@@ -411,6 +418,29 @@ class Solver:
             out = np.empty(self.shape)
         s2_get_state(self.h, self._fits(out))
         return out
+
+    def stream_states(self, w_in, w_out, nsteps: int, count: Optional[int] = None):
+        """Copy in, advance nsteps and copy out count states, the copies
+        overlapping the steps (s2_stream_states).  w_in / w_out: a stack of
+        states (count, 5, nz, ny, nx), or one state (5, nz, ny, nx) used for
+        every j (count then required; w_out then holds the last result)."""
+        strides = []
+        for a in (w_in, w_out):
+            shape = tuple(a.shape)
+            if shape == self.shape:
+                if count is None:
+                    raise ValueError("count is needed when a buffer holds one state")
+                strides.append(0)
+            elif len(shape) == 5 and shape[1:] == self.shape:
+                if count is None:
+                    count = shape[0]
+                if shape[0] < count:
+                    raise ValueError("buffer of %d states for count %d" % (shape[0], count))
+                strides.append(5 * self.n)
+            else:
+                raise ValueError("state stack of shape %s, need (count,) + %s" % (shape, self.shape))
+        s2_stream_states(self.h, w_in, strides[0], w_out, strides[1], count, nsteps)
+        return w_out
 
     def set_primitives(self, prim):
         """State from primitive fields (rho, u, v, w, T), shape (5, nz, ny, nx)."""

@@ -267,6 +267,47 @@ def test_device_pointers_and_stream(s2):
     assert np.array_equal(out.cpu().numpy(), wh)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stream_states_equal_set_step_get(s2, precision):
+    """s2_stream_states, whose copies overlap the steps, gives state by state
+    exactly what s2_set_state / s2_step / s2_get_state give in sequence: a
+    pinned host stack, then one reused input, then device tensors."""
+    c = channel_small(48, 32, 24, seed=5)
+    ins = np.stack([channel_small(48, 32, 24, seed=5 + j).w0 for j in range(3)])
+    nsteps = 4
+    kw = dict(cfl=0.8, dt_every=3, precision=precision)
+    with s2.Solver.from_case(c, **kw) as a:
+        ref = []
+        for j in range(3):
+            a.set_state(ins[j])
+            a.step(nsteps)
+            ref.append(a.get_state())
+        for _ in range(2):
+            a.set_state(ins[0])
+            a.step(nsteps)
+        ref_last = a.get_state()
+        st_a = a.stats()
+    with s2.Solver.from_case(c, **kw) as b:
+        pin_in = torch.from_numpy(ins).pin_memory()
+        pin_out = torch.empty_like(pin_in).pin_memory()
+        b.stream_states(pin_in, pin_out, nsteps)
+        last = np.empty_like(ins[0])
+        b.stream_states(ins[0], last, nsteps, count=2)  # staging buffers reused, stride 0 in and out
+        st_b = b.stats()
+        with pytest.raises(s2.S2Error) as ei:
+            s2.s2_stream_states(b.h, ins, 0, last, 0, -1, nsteps)
+        assert ei.value.code == s2.S2_EINVAL
+    for j in range(3):
+        assert np.array_equal(pin_out[j].numpy(), ref[j]), j
+    assert np.array_equal(last, ref_last)
+    assert st_a["step"] == st_b["step"] == 5 * nsteps and st_a["t"] == st_b["t"]
+    with s2.Solver.from_case(c, **kw) as d:
+        tin = torch.from_numpy(ins).cuda()
+        tout = torch.empty_like(tin)
+        d.stream_states(tin, tout, nsteps)
+    assert np.array_equal(tout.cpu().numpy(), pin_out.numpy())
+
+
 def test_nonfinite_state_reported(s2):
     c = W.taylor_green(16)
     w = c.w0.copy()
