@@ -74,6 +74,7 @@ def test_strerror_and_invalid_arguments(lib):
     assert s2._lib.s2_create(None, None, None, None, None, None, C.byref(h)) == s2.S2_EINVAL
     assert s2._lib.s2_step(None, 1) == s2.S2_EINVAL
     assert s2._lib.s2_stats(None, None) == s2.S2_EINVAL
+    assert s2._lib.s2_stream_states(None, None, 0, None, 0, 1, 1) == s2.S2_EINVAL
     s2._lib.s2_destroy(None)
 
 
@@ -97,3 +98,30 @@ def test_binding_refuses_wrong_state_sizes():
     for bad in (np.zeros((5, 4, 3, 3)), np.zeros(119), np.zeros((4, 4, 3, 2))):
         with pytest.raises(ValueError):
             sv._fits(bad)
+
+
+def test_binding_stream_states_checks_stacks():
+    """Solver.stream_states accepts a stack of states or one reused state,
+    and refuses other shapes or a stack shorter than count, before any
+    library call."""
+    import numpy as np
+    import pytest
+    from paper_2304_05494_gb300 import s2
+    sv = object.__new__(s2.Solver)
+    sv.shape, sv.n, sv.h = (5, 4, 3, 2), 24, None
+    calls = []
+    orig = s2.s2_stream_states
+    s2.s2_stream_states = lambda h, wi, si, wo, so, count, nsteps: calls.append((si, so, count, nsteps))
+    try:
+        sv.stream_states(np.zeros((3, 5, 4, 3, 2)), np.zeros((3, 5, 4, 3, 2)), 2)
+        sv.stream_states(np.zeros((5, 4, 3, 2)), np.zeros((5, 4, 3, 2)), 1, count=4)
+        sv.stream_states(np.zeros((5, 4, 3, 2)), np.zeros((2, 5, 4, 3, 2)), 1, count=2)
+        with pytest.raises(ValueError):
+            sv.stream_states(np.zeros((5, 4, 3, 2)), np.zeros((5, 4, 3, 2)), 1)  # count needed
+        with pytest.raises(ValueError):
+            sv.stream_states(np.zeros((2, 5, 4, 3, 2)), np.zeros((2, 5, 4, 3, 2)), 1, count=3)
+        with pytest.raises(ValueError):
+            sv.stream_states(np.zeros((2, 5, 4, 3, 3)), np.zeros((2, 5, 4, 3, 2)), 1)
+    finally:
+        s2.s2_stream_states = orig
+    assert calls == [(120, 120, 3, 2), (0, 0, 4, 1), (0, 120, 2, 1)]
