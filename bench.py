@@ -80,8 +80,9 @@ MIXED_BYTES = {"prims": 72, "grad": 20, "flux_x": 48, "flux_y": 68, "flux_z": 68
 # and write the state and the RK register, 4 x 40 B.
 METHOD_BYTES_PER_POINT_STEP = 480.0
 # DRAM bytes per interior point of one launch of the mixed kernels (ncu,
-# 256 x 128 x 128 channel, first stage; profiles/channel256x128x128_mixed_kernels_full.md).
-MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.6, "update": 110.1}
+# 256 x 128 x 128 channel, first stage; profiles/channel256x128x128_mixed_kernels_full.md,
+# the viscous pass profiles/channel1024x256x512_launch_list.md).
+MIXED_DRAM_BYTES = {"prims": 63.9, "visc": 65.5, "update": 110.1}
 # Thermally perfect gas of the side measurement: a synthetic polynomial of
 # the NASA 9-coefficient form, c_p/R = sum_{l=-2..4} a_l T^l (reference
 # units of T), whose gamma falls from 1.45 at T = 0.5 through 1.40 at T = 1
