@@ -1,7 +1,9 @@
 """Host-side logic that needs no GPU: serving workload generation, arrival
 process, autotuner choice and cache, and the error bound behind the
-single-precision pre-test of the double-precision sensor decision."""
+single-precision pre-test of the double-precision sensor decision, and the
+roofline arithmetic of the bench line."""
 import numpy as np
+import pytest
 
 from paper_2304_05494_gb300 import autotune, serve
 
@@ -145,3 +147,34 @@ def test_sensor_single_precision_pretest_matches_exact_decision():
         else:
             fallback += 1
     assert decided > 4000 and fallback > 0
+
+
+def test_bench_roofline_arithmetic(monkeypatch):
+    """The bench line's roofline objects from a synthetic per-class profile
+    (total ms and launches per kernel class): achieved = algorithmic bytes
+    (flops) per launch over the mean launch time, the dominant class is the
+    one with the most time, the step fraction uses the method's 480 B per
+    point-step, and the whole-job rate sums the replicas' work."""
+    import bench
+    monkeypatch.setattr(bench, "hbm_peak_gbs", lambda: (6000.0, "measured"))
+
+    class Case:
+        points = 1_000_000
+        nx = ny = nz = 100
+
+    prof = {"prims": (6.0, 6), "visc": (30.0, 6), "update": (12.0, 6), "flux_x": (9.0, 6), "grad": (3.0, 6)}
+    r = bench.mixed_roofline(Case, prof, step_ms=20.0)
+    assert r["kernel"] == "visc" and r["bound"] == "hbm"
+    assert r["per_launch_ms"] == 5.0
+    assert r["achieved"] == pytest.approx(bench.MIXED_BYTES["visc"] * 1e6 / 5e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
+    assert r["step_frac"] == pytest.approx(480.0 * 1e6 / 20e-3 / 1e9 / 6000.0)
+    assert r["frac_per_kernel"]["update"] == round(bench.MIXED_BYTES["update"] * 1e6 / 2e-3 / 1e9 / 6000.0, 3)
+    assert r["traffic"] == pytest.approx(bench.MIXED_DRAM_BYTES["visc"] * 1e6)
+
+    f = bench.fp64_roofline(Case, {"visc": (60.0, 6), "prims": (10.0, 6)}, 2, 0.0, 50.0, 1250.0)
+    assert f["kernel"] == "visc" and f["bound"] == "alu"
+    assert f["achieved"] == pytest.approx(bench.ALG_FLOPS["visc"] * 1e6 / 10e-3 / 1e9)
+    assert f["frac"] == pytest.approx(f["achieved"] / bench.FP64_PEAK_GFLOPS)
+    assert f["frac_of_fma_measured"] == pytest.approx(f["achieved"] / 1250.0)
+    assert bench.whole_job_rate(1e6, 10, 2, 100.0) == pytest.approx(2e8)
