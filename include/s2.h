@@ -254,8 +254,9 @@ int s2_set_tiles(s2_solver *s, const int *tiles);
 /* Launch shape of the kernels, the knobs of the paper's block-shape study
  * (Table 3) and of its translator's configuration (Sec. 3.3), searched by
  * the autotuner (paper_2304_05494_gb300/autotune.py).  tiles: as
- * s2_set_tiles.  flux_ctas_per_sm: CTAs per multiprocessor of the
- * persistent single-precision flux grids (0: as many as fit, up to 16).
+ * s2_set_tiles.  flux_ctas_per_sm[d]: CTAs per multiprocessor of the
+ * persistent single-precision flux grid of direction d (0: as many as
+ * fit, up to 16).
  * z_planes: z-planes each CTA of the mixed path's z-marching gradient and
  * viscous passes walks (0: 12; else 4, 8, 16 or 24, compiled variants).  weno_ctas_per_sm: cap of the
  * WENO kernels' 64-thread CTAs per multiprocessor (0: 16; else 1..64).
@@ -265,7 +266,7 @@ int s2_set_tiles(s2_solver *s, const int *tiles);
  * rounding). */
 typedef struct {
   int tiles[3];
-  int flux_ctas_per_sm;
+  int flux_ctas_per_sm[3];
   int z_planes;
   int weno_ctas_per_sm;
 } s2_tuning;

@@ -10,7 +10,8 @@ library's own CUDA-event trace (s2_profile) per kernel class:
   tile length along the direction against the pencils across), timed per
   direction (flux_x, flux_y, flux_z);
 * single precision: the resident CTAs per multiprocessor of the persistent
-  flux grids (1..4, or all that fit), timed on the three flux classes;
+  flux grid of each direction (1..4, or all that fit), each direction
+  timed on its own flux class;
 * single precision: the z-planes each CTA of the z-marching gradient and
   viscous passes walks (4, 8, 12, 16, 24), timed on grad + visc;
 * the CTAs per multiprocessor of the WENO kernels' grids (4..32), timed on
@@ -78,12 +79,17 @@ def choose(times: dict) -> list:
     return out
 
 
-def _time(sv, w, steps, classes) -> float:
-    """ms per step of the given kernel classes from state w."""
+def _profile(sv, w, steps) -> dict:
+    """Per-class (ms, launches) of `steps` steps from state w."""
     sv.set_state(w)
     sv.set_clock(0.0, 0, 0.0)
     sv.profile(1)  # warm-up (and graph rebuild)
-    prof = sv.profile(steps)
+    return sv.profile(steps)
+
+
+def _time(sv, w, steps, classes) -> float:
+    """ms per step of the given kernel classes from state w."""
+    prof = _profile(sv, w, steps)
     return sum(prof[c][0] for c in classes if c in prof) / steps
 
 
@@ -104,7 +110,16 @@ def tune_solver(sv, w: np.ndarray, steps: int = 3, variants=(0, 1), mixed: Optio
         mixed = getattr(sv, "precision", "fp64") == "mixed"
     searches = []
     if mixed:
-        searches.append(("flux_ctas_per_sm", FLUX_CTAS, _DIRS))
+        # one pass over the values sets the three directions alike; each
+        # direction's grid only changes its own kernel, so each takes the
+        # value that timed best for its own class
+        t = {}
+        for v in FLUX_CTAS:
+            sv.set_tuning(flux_ctas_per_sm=v)
+            prof = _profile(sv, w, steps)
+            t[v] = {d: prof[d][0] / steps for d in _DIRS if d in prof}
+        sv.set_tuning(flux_ctas_per_sm=[min(t, key=lambda v: t[v][d]) for d in _DIRS])
+        times["flux_ctas_per_sm"] = t
         searches.append(("z_planes", Z_PLANES, ("grad", "visc")))
     if weno:
         searches.append(("weno_ctas_per_sm", WENO_CTAS, ("weno",)))

@@ -746,7 +746,7 @@ cudaError_t launch_one(const Dev &d, const FluxMaps &maps, int accumulate, cudaS
   }
   const TileGrid<DIR, TV, R> tg(d);
   const int ntiles = tg.count();
-  const int cps = d.flux_cps > 0 && d.flux_cps < per_sm ? d.flux_cps : per_sm;
+  const int cps = d.flux_cps[DIR] > 0 && d.flux_cps[DIR] < per_sm ? d.flux_cps[DIR] : per_sm;
   const int nb = sizeof(R) == 8 ? ntiles : (ntiles < cps * d.nsm ? ntiles : cps * d.nsm);
   k_flux<DIR, HASW, R, TV, NP><<<nb, NTHREADS, smem, st>>>(maps, d, tg, accumulate);
   return cudaGetLastError();
@@ -981,7 +981,7 @@ struct FluxPlan {
     memcpy(out.tg, &tg, sizeof(tg));
     out.tg_size = (int)sizeof(tg);
     out.tiles = tg.count();
-    out.per_sm = d.flux_cps > 0 && d.flux_cps < per_sm ? d.flux_cps : per_sm;
+    out.per_sm = d.flux_cps[DIR] > 0 && d.flux_cps[DIR] < per_sm ? d.flux_cps[DIR] : per_sm;
     out.persistent = sizeof(R) == 4;
     return cudaSuccess;
   }

@@ -110,7 +110,7 @@ struct Dev {
   int viscous, wall_y, weno, force;
   int mixed;               // 0: FP64 everywhere; 1: FP32 primitives and flux arithmetic, FP64 state
   int tile[3];             // flux tile variant per direction (0 default, 1 narrow)
-  int flux_cps;            // single-precision flux grids: resident CTAs per SM to use (0: all that fit)
+  int flux_cps[3];         // single-precision flux grids, per direction: resident CTAs per SM to use (0: all that fit)
   int zs;                  // planes per CTA of the z-marching passes (mixed path)
   int weno_cps;            // WENO grids: CTAs per SM
   int nsm;                 // multiprocessors of the device

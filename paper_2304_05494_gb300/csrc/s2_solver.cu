@@ -1258,7 +1258,7 @@ int s2_create(const s2_grid *grid, const s2_metrics *metrics, const s2_gas *gas,
   // 256 x 128 x 128 channel)
   d.tile[0] = 0;
   d.tile[1] = d.tile[2] = d.mixed;
-  d.flux_cps = 0;
+  for (int a = 0; a < 3; ++a) d.flux_cps[a] = 0;
   d.zs = ZS_DEFAULT;
   d.weno_cps = 16;
   // scheme constants in both arithmetic types
@@ -1621,7 +1621,8 @@ int s2_set_tuning(s2_solver *s, const s2_tuning *t) {
   if (!s || !t) return S2_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (t->tiles[a] != 0 && t->tiles[a] != 1) return S2_EINVAL;
-  if (t->flux_ctas_per_sm < 0 || t->flux_ctas_per_sm > 16) return S2_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (t->flux_ctas_per_sm[a] < 0 || t->flux_ctas_per_sm[a] > 16) return S2_EINVAL;
   if (t->z_planes != 0 && t->z_planes != 4 && t->z_planes != 8 && t->z_planes != 12 && t->z_planes != 16 &&
       t->z_planes != 24)
     return S2_EINVAL;
@@ -1629,7 +1630,7 @@ int s2_set_tuning(s2_solver *s, const s2_tuning *t) {
   DeviceGuard guard(s->device);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return S2_ECUDA;
   for (int a = 0; a < 3; ++a) s->d.tile[a] = t->tiles[a];
-  s->d.flux_cps = t->flux_ctas_per_sm;
+  for (int a = 0; a < 3; ++a) s->d.flux_cps[a] = t->flux_ctas_per_sm[a];
   s->d.zs = t->z_planes ? t->z_planes : ZS_DEFAULT;
   s->d.weno_cps = t->weno_ctas_per_sm ? t->weno_ctas_per_sm : 16;
   if (s->graph_ready) {
@@ -1642,7 +1643,7 @@ int s2_set_tuning(s2_solver *s, const s2_tuning *t) {
 int s2_get_tuning(const s2_solver *s, s2_tuning *t) {
   if (!s || !t) return S2_EINVAL;
   for (int a = 0; a < 3; ++a) t->tiles[a] = s->d.tile[a];
-  t->flux_ctas_per_sm = s->d.flux_cps;
+  for (int a = 0; a < 3; ++a) t->flux_ctas_per_sm[a] = s->d.flux_cps[a];
   t->z_planes = s->d.zs;
   t->weno_ctas_per_sm = s->d.weno_cps;
   return S2_OK;

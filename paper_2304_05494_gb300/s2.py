@@ -58,7 +58,7 @@ class s2_scheme(C.Structure):
 
 
 class s2_tuning(C.Structure):
-    _fields_ = [("tiles", C.c_int * 3), ("flux_ctas_per_sm", C.c_int), ("z_planes", C.c_int),
+    _fields_ = [("tiles", C.c_int * 3), ("flux_ctas_per_sm", C.c_int * 3), ("z_planes", C.c_int),
                 ("weno_ctas_per_sm", C.c_int)]
 
 
@@ -223,7 +223,9 @@ def s2_set_tiles(h, tiles) -> None:
 
 
 def s2_set_tuning(h, tiles=(0, 0, 0), flux_ctas_per_sm=0, z_planes=0, weno_ctas_per_sm=0) -> None:
-    t = s2_tuning((C.c_int * 3)(*[int(x) for x in tiles]), int(flux_ctas_per_sm), int(z_planes),
+    """flux_ctas_per_sm: one value for the three directions or one per direction."""
+    cps = [flux_ctas_per_sm] * 3 if np.isscalar(flux_ctas_per_sm) else list(flux_ctas_per_sm)
+    t = s2_tuning((C.c_int * 3)(*[int(x) for x in tiles]), (C.c_int * 3)(*[int(x) for x in cps]), int(z_planes),
                   int(weno_ctas_per_sm))
     _check(_lib.s2_set_tuning(h, C.byref(t)), "s2_set_tuning")
 
@@ -231,7 +233,7 @@ def s2_set_tuning(h, tiles=(0, 0, 0), flux_ctas_per_sm=0, z_planes=0, weno_ctas_
 def s2_get_tuning(h) -> dict:
     t = s2_tuning()
     _check(_lib.s2_get_tuning(h, C.byref(t)), "s2_get_tuning")
-    return {"tiles": list(t.tiles), "flux_ctas_per_sm": t.flux_ctas_per_sm, "z_planes": t.z_planes,
+    return {"tiles": list(t.tiles), "flux_ctas_per_sm": list(t.flux_ctas_per_sm), "z_planes": t.z_planes,
             "weno_ctas_per_sm": t.weno_ctas_per_sm}
 
 

@@ -172,7 +172,7 @@ def test_autotuner_caches_a_choice(s2, tmp_path):
     with s2.Solver.from_case(c, precision="mixed") as sv:
         t = autotune.tuning_for(sv, c.w0, (c.nx, c.ny, c.nz), "mixed", 5, path=path, steps=2)
         assert all(x in (0, 1) for x in t["tiles"])
-        assert t["flux_ctas_per_sm"] in autotune.FLUX_CTAS and t["z_planes"] in autotune.Z_PLANES
+        assert all(x in autotune.FLUX_CTAS for x in t["flux_ctas_per_sm"]) and t["z_planes"] in autotune.Z_PLANES
         assert t["weno_ctas_per_sm"] in autotune.WENO_CTAS
         assert sv.get_tuning() == t
         sv.step(1)  # the solver still runs after tuning
@@ -202,7 +202,7 @@ def test_launch_knobs_give_identical_results(s2, precision):
 
     chan = W.channel(40, 36, 30, seed=2)
     ref = run(chan)
-    for knobs in (dict(flux_ctas_per_sm=1, weno_ctas_per_sm=4), dict(flux_ctas_per_sm=3, weno_ctas_per_sm=32)):
+    for knobs in (dict(flux_ctas_per_sm=1, weno_ctas_per_sm=4), dict(flux_ctas_per_sm=[3, 0, 2], weno_ctas_per_sm=32)):
         assert np.array_equal(ref, run(chan, **knobs)), knobs
     zc = run(chan, z_planes=8)
     if precision == "fp64":
