@@ -308,6 +308,29 @@ def test_stream_states_equal_set_step_get(s2, precision):
     assert np.array_equal(tout.cpu().numpy(), pin_out.numpy())
 
 
+def test_stream_states_reports_an_invalid_state(s2):
+    """A non-positive density in one streamed state makes the call return
+    S2_ENONFINITE; every result is still copied out (the one before it equal
+    to a sequential step), and the next call starts with a clear status."""
+    c = W.taylor_green(16)
+    bad = c.w0.copy()
+    bad[0, 3, 4, 5] = -1.0
+    ins = np.stack([c.w0, bad, c.w0])
+    outs = np.full_like(ins, np.nan)
+    with s2.Solver.from_case(c, cfl=0.0, dt_fixed=1e-3) as a:
+        a.set_state(c.w0)
+        a.step(1)
+        ref = a.get_state()
+    with s2.Solver.from_case(c, cfl=0.0, dt_fixed=1e-3) as sv:
+        with pytest.raises(s2.S2Error) as ei:
+            sv.stream_states(ins, outs, 1)
+        assert ei.value.code == s2.S2_ENONFINITE
+        assert np.array_equal(outs[0], ref)
+        assert not np.isnan(outs[2]).all()
+        again = np.empty_like(ins[:1])
+        sv.stream_states(ins[:1], again, 1)
+
+
 def test_nonfinite_state_reported(s2):
     c = W.taylor_green(16)
     w = c.w0.copy()
